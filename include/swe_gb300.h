@@ -1,0 +1,190 @@
+/*
+ * swe_gb300.h -- C ABI of the GB300 (sm_103a) Parareal/MGRIT shallow-water hot path.
+ *
+ * Method: arXiv 2306.09497, "Parallel-in-time integration of the shallow water
+ * equations on the rotating sphere using Parareal and MGRIT".
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Spectral coefficients: complex128 stored as interleaved (re, im) doubles,
+ *   triangular truncation T_M, m-major: for m = 0..M the entries n = m..M are
+ *   contiguous, so coefficient (m, n) sits at m(M+1) - m(m-1)/2 + (n - m);
+ *   NC(M) = (M+1)(M+2)/2 complex values per field.  Associated Legendre
+ *   functions are normalised to unit square integral over mu in [-1, 1], with
+ *   no Condon-Shortley phase; a real field is
+ *   f = sum_n f_{0n} P_n^0 + 2 Re sum_{m>=1} sum_n f_{mn} P_n^m(mu) e^{i m lambda}
+ *   (the imaginary part of every m = 0 coefficient is ignored) (§2.2, Eq. 2).
+ * Grid: Gauss-Legendre latitudes ordered north to south, longitudes
+ *   lambda_k = 2 pi k / nlon; fields are [batch][nlat][nlon], longitude fastest.
+ * State vector U = (Phi', xi, delta): geopotential perturbation (the mean
+ *   Phi_bar is a plan constant), vorticity, divergence (§2.1, Eq. 1); a batch of
+ *   S states is [S][3][NC] complex128.  The n = 0 coefficients of xi and delta
+ *   are zero for every flow and are ignored on input.
+ * Memory: every array argument is a DEVICE pointer owned by the caller unless
+ *   the comment says "host".  The library owns its tables and workspace.
+ * Streams: every call is asynchronous on the given stream (NULL = legacy
+ *   default stream) unless its comment says it synchronises.  Calls on one
+ *   plan must not overlap in time (the plan's workspace is shared).
+ * Errors: functions return a swe_status; SWE_OK is 0.  swe_last_error()
+ *   returns a thread-local message describing the last failure.  No C++
+ *   exception crosses this boundary.
+ */
+#ifndef SWE_GB300_H
+#define SWE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SWE_OK = 0,
+    SWE_EINVAL = 1,      /* invalid argument (sizes, pointers, descriptor fields) */
+    SWE_ENOMEM = 2,      /* device allocation failed */
+    SWE_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+    SWE_EUNSTABLE = 4,   /* a non-finite value appeared in the state */
+    SWE_ETIMEOUT = 5,    /* a bounded device-side wait gave up */
+    SWE_ENOTCONV = 6     /* iteration limit reached before the tolerance */
+} swe_status;
+
+typedef enum {
+    SWE_FP64 = 0,          /* every step in double precision */
+    SWE_SPLIT_BF16X3 = 1   /* Legendre GEMM on tcgen05 tensor cores with operands split
+                              into bf16 (hi, lo) pairs and FP32 accumulation; longitude
+                              FFT and grid products in FP32; spectral state, implicit
+                              solve and PinT correction in FP64 */
+} swe_precision;
+
+typedef enum {
+    SWE_IMEX = 0,                /* IMEX Strang splitting, §2.3.1 Eqs. 3-5 */
+    SWE_SLSI_SETTLS = 1,         /* SL-SI-SETTLS two-step, §2.3.2 Eqs. 6-7 */
+    SWE_SLSI_SETTLS_1STEP = 2    /* one-step variant used inside PinT, §3.2.4 */
+} swe_scheme;
+
+/* Spatial discretisation of one truncation (§2.2). nlat must be even,
+ * nlat >= M + 2, nlon > 2(M+1) and nlon = 2^a 3^b. */
+typedef struct {
+    int M, nlat, nlon;
+    double a;        /* sphere radius, m */
+    double omega;    /* rotation rate, 1/s; Coriolis parameter f = 2 omega mu */
+    double g;        /* gravity, m/s^2 (used by diagnostics only) */
+    double phibar;   /* mean geopotential Phi_bar, m^2/s^2 */
+    swe_precision prec;
+} swe_plan_desc;
+
+/* One propagator phi: nsteps steps of length dt of a scheme, each followed by
+ * backward-Euler (hyper)viscosity of order visc_q (even, >= 2) and coefficient
+ * visc_nu >= 0 (§2.3, App. A). */
+typedef struct {
+    int scheme;      /* swe_scheme */
+    double dt;       /* s */
+    int nsteps;
+    int visc_q;
+    double visc_nu;
+} swe_stepper_desc;
+
+typedef struct swe_plan* swe_plan_t;
+typedef struct swe_pint* swe_pint_t;
+
+/* Library version string (static storage). */
+const char* swe_version(void);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* swe_last_error(void);
+
+/* Number of complex coefficients per field for truncation M: (M+1)(M+2)/2. */
+int64_t swe_ncoef(int M);
+
+/* Creates a plan on the current CUDA device: Gauss-Legendre nodes/weights
+ * (Newton iteration), normalised associated Legendre table for n <= M+1 at
+ * the northern Gauss latitudes (three-term recurrence), FFT twiddles.  All
+ * generated on the device in FP64 (§2.2).  Synchronises.  *out receives the
+ * plan; destroy it with swe_plan_destroy. */
+swe_status swe_plan_create(const swe_plan_desc* desc, swe_plan_t* out);
+swe_status swe_plan_destroy(swe_plan_t plan);
+
+/* Copies the Gauss-Legendre nodes mu_j (north to south) and weights w_j into
+ * HOST arrays of nlat doubles.  Synchronises. */
+swe_status swe_plan_gauss(swe_plan_t plan, double* mu_host, double* w_host);
+
+/* Inverse scalar spherical-harmonic transform (§2.2): spec [batch][NC] complex128
+ * -> grid [batch][nlat][nlon].  grid is double for SWE_FP64 plans and float
+ * for split-precision plans. */
+swe_status sht_inverse(swe_plan_t plan, const void* spec, void* grid, int batch, void* stream);
+
+/* Forward scalar transform: grid [batch][nlat][nlon] (double or float as above)
+ * -> spec [batch][NC] complex128, by FFT in longitude and Gauss quadrature in mu. */
+swe_status sht_forward(swe_plan_t plan, const void* grid, void* spec, int batch, void* stream);
+
+/* Nonlinear tendency N(U) = N_A(U) + N_R(U) of Eq. 1 for S states, evaluated
+ * pseudospectrally on the Gaussian grid (the geopotential part in the
+ * equivalent flux form -div(Phi' V)).  U, N: [S][3][NC] complex128. */
+swe_status swe_nonlinear(swe_plan_t plan, const double* U, double* N, int S, void* stream);
+
+/* Linear tendency L U = L_G U + L_C U of Eq. 1 (f = 2 omega mu), exact in
+ * spectral space.  U, LU: [S][3][NC] complex128. */
+swe_status swe_linear(swe_plan_t plan, const double* U, double* LU, int S, void* stream);
+
+/* Solves (I - alpha L) X = R for S right-hand sides, one banded system per
+ * zonal wavenumber m (Eq. 4 / Eq. 7 implicit part).  R, X: [S][3][NC]. */
+swe_status swe_implicit_solve(swe_plan_t plan, double alpha, const double* R, double* X,
+                              int S, void* stream);
+
+/* Balanced initial state: given vorticity xi [S][NC] and a geopotential
+ * increment phi_add [S][NC] (may be NULL), writes U = (Phi', xi, 0) with
+ * Phi' = lap^{-1}([L_C U + N U]_delta) + phi_add, i.e. d(delta)/dt = 0 for the
+ * non-divergent flow (nonlinear balance).  U: [S][3][NC]. */
+swe_status swe_balance(swe_plan_t plan, const double* xi, const double* phi_add, double* U,
+                       int S, void* stream);
+
+/* Propagator phi_f (§3.1): applies the stepper to S independent states at once.
+ * U_in, U_out: [S][3][NC]; may alias.  For the two-step SL-SI-SETTLS scheme
+ * the first step of each state uses the one-step form (§3.2.4). */
+swe_status propagate_F(swe_plan_t plan, const swe_stepper_desc* st, const double* U_in,
+                       double* U_out, int S, void* stream);
+
+/* Coarse propagator phi_c: runs the stepper on the coarse plan.  When the two
+ * plans have different truncations the input is truncated from `fine` to
+ * `coarse` and the result zero-padded back (spatial coarsening, §5.1).
+ * fine may be NULL or equal to coarse.  U_in, U_out use the fine plan's NC. */
+swe_status propagate_G(swe_plan_t coarse, swe_plan_t fine, const swe_stepper_desc* st,
+                       const double* U_in, double* U_out, int S, void* stream);
+
+/* Parallel-in-time problem on [0, S * slice] with S slices. */
+typedef struct {
+    swe_plan_t fine_plan;          /* level-0 spatial plan */
+    swe_plan_t coarse_plan;        /* coarse plan (may equal fine_plan) */
+    swe_stepper_desc fine;         /* phi_f over one slice (nsteps fine steps) */
+    swe_stepper_desc coarse;       /* phi_c over one slice */
+    int S;                         /* number of time slices N */
+    int use_graphs;                /* 1: capture the serial coarse chain in a CUDA graph */
+} swe_pint_desc;
+
+swe_status swe_pint_create(const swe_pint_desc* desc, swe_pint_t* out);
+swe_status swe_pint_destroy(swe_pint_t p);
+
+/* Sets U_0 (device, [3][NC]) and computes the Parareal initial guess
+ * U^0_{n+1} = phi_c(U^0_n), n = 0..S-1 (§3.1). */
+swe_status swe_pint_init(swe_pint_t p, const double* U0, void* stream);
+
+/* Runs up to kmax Parareal iterations (Eq. 9):
+ * U^{k+1}_{n+1} = phi_c(U^{k+1}_n) + phi_f(U^k_n) - phi_c(U^k_n).
+ * After each iteration the FP64 norm max_n ||U^{k+1}_n - U^k_n||_inf /
+ * max_n ||U^{k+1}_n||_inf is written to norm_hist_host[k] (HOST, kmax doubles,
+ * may be NULL); iterations stop early when it falls below tol (tol <= 0: never).
+ * *k_done (HOST) receives the number of iterations run.  Synchronises once per
+ * iteration (norm readback).  Returns SWE_EUNSTABLE if a non-finite value
+ * appeared. */
+swe_status parareal_iterate(swe_pint_t p, int kmax, double tol, int* k_done,
+                            double* norm_hist_host, void* stream);
+
+/* Copies the slice-boundary states U^k_n, n = 0..S, into U_out (device,
+ * [S+1][3][NC]). */
+swe_status swe_pint_solution(swe_pint_t p, double* U_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWE_GB300_H */

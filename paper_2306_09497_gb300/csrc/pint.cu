@@ -1,0 +1,248 @@
+// Parareal (§3.1, Eq. 9) on one GPU: the fine propagator runs on all S slices
+// at once (one batched propagate_F), the coarse chain runs serially (captured
+// once into a CUDA graph and replayed every iteration), and the FP64 correction
+// U^{k+1}_{n+1} = G(U^{k+1}_n) + F(U^k_n) - G(U^k_n) is fused with the
+// per-field convergence norm.
+#include <cstring>
+
+#include "swe_internal.cuh"
+
+struct swe_pint {
+    swe_pint_desc d;
+    int64_t nc = 0;
+    double2* U = nullptr;      // [S+1][3][NC] current iterate
+    double2* Fo = nullptr;     // [S][3][NC]   phi_f(U^k_n)
+    double2* Gold = nullptr;   // [S][3][NC]   phi_c(U^k_n)
+    double2* Gnew = nullptr;   // [3][NC]      phi_c(U^{k+1}_n)
+    unsigned long long* red = nullptr;   // [6] max |dU_f|, max |U_f| (double bits)
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool ready = false;
+};
+
+namespace {
+
+__device__ __forceinline__ double cabs_inf(double2 v) { return fmax(fabs(v.x), fabs(v.y)); }
+
+// Unext <- G + F - Gold ; Gold <- G ; reduce max |Unext_new - Unext_old| and max |Unext_new| per field
+__global__ void k_parareal_correct(const double2* __restrict__ G, const double2* __restrict__ F,
+                                   double2* __restrict__ Gold, double2* __restrict__ Unext, int64_t nc,
+                                   unsigned long long* red, int* flags) {
+    __shared__ double sd[3][8], sv[3][8];
+    double md[3] = {0, 0, 0}, mv[3] = {0, 0, 0};
+    const int64_t n = 3 * nc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 g = G[i], f = F[i], go = Gold[i], uo = Unext[i];
+        double2 u = make_double2(g.x + f.x - go.x, g.y + f.y - go.y);
+        if (!isfinite(u.x) || !isfinite(u.y)) atomicOr(flags, 1);
+        Unext[i] = u;
+        Gold[i] = g;
+        int fld = (int)(i / nc);
+        double dd = cabs_inf(make_double2(u.x - uo.x, u.y - uo.y));
+        double vv = cabs_inf(u);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            if (q == fld) {
+                md[q] = fmax(md[q], dd);
+                mv[q] = fmax(mv[q], vv);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        for (int o = 16; o > 0; o >>= 1) {
+            md[q] = fmax(md[q], __shfl_xor_sync(0xffffffffu, md[q], o));
+            mv[q] = fmax(mv[q], __shfl_xor_sync(0xffffffffu, mv[q], o));
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int q = 0; q < 3; ++q) {
+            sd[q][warp] = md[q];
+            sv[q][warp] = mv[q];
+        }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        int q = threadIdx.x;
+        double a = 0, b = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a = fmax(a, sd[q][w]);
+            b = fmax(b, sv[q][w]);
+        }
+        // non-negative doubles order like their bit patterns
+        atomicMax(&red[q], (unsigned long long)__double_as_longlong(a));
+        atomicMax(&red[3 + q], (unsigned long long)__double_as_longlong(b));
+    }
+}
+
+}  // namespace
+
+extern "C" swe_status swe_pint_create(const swe_pint_desc* d, swe_pint_t* out) {
+    if (!d || !out || !d->fine_plan || !d->coarse_plan || d->S < 1) {
+        swe_set_error("swe_pint_create: invalid descriptor");
+        return SWE_EINVAL;
+    }
+    if (d->coarse_plan->M > d->fine_plan->M) {
+        swe_set_error("swe_pint_create: coarse truncation must not exceed the fine one");
+        return SWE_EINVAL;
+    }
+    swe_pint* p = new swe_pint();
+    p->d = *d;
+    p->nc = d->fine_plan->nc;
+    const size_t st = sizeof(double2) * 3 * p->nc;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p->U, st * (d->S + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p->Fo, st * d->S);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p->Gold, st * d->S);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p->Gnew, st);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p->red, sizeof(unsigned long long) * 6);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        swe_pint_destroy(p);
+        return swe_cuda_status(e, "swe_pint_create");
+    }
+    *out = p;
+    return SWE_OK;
+}
+
+extern "C" swe_status swe_pint_destroy(swe_pint_t p) {
+    if (!p) return SWE_OK;
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->cs) cudaStreamDestroy(p->cs);
+    cudaFree(p->U);
+    cudaFree(p->Fo);
+    cudaFree(p->Gold);
+    cudaFree(p->Gnew);
+    cudaFree(p->red);
+    delete p;
+    return SWE_OK;
+}
+
+static swe_status coarse(swe_pint* p, const double2* in, double2* out) {
+    return propagate_G(p->d.coarse_plan, p->d.fine_plan, &p->d.coarse, (const double*)in, (double*)out, 1, p->cs);
+}
+
+static swe_status join_user_stream(swe_pint* p, cudaStream_t user) {
+    cudaEvent_t ev;
+    SWE_CHECK_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    SWE_CHECK_CUDA(cudaEventRecord(ev, p->cs));
+    SWE_CHECK_CUDA(cudaStreamWaitEvent(user, ev, 0));
+    cudaEventDestroy(ev);
+    return SWE_OK;
+}
+
+static swe_status wait_user_stream(swe_pint* p, cudaStream_t user) {
+    cudaEvent_t ev;
+    SWE_CHECK_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    SWE_CHECK_CUDA(cudaEventRecord(ev, user));
+    SWE_CHECK_CUDA(cudaStreamWaitEvent(p->cs, ev, 0));
+    cudaEventDestroy(ev);
+    return SWE_OK;
+}
+
+extern "C" swe_status swe_pint_init(swe_pint_t p, const double* U0, void* stream) {
+    if (!p || !U0) {
+        swe_set_error("swe_pint_init: invalid argument");
+        return SWE_EINVAL;
+    }
+    cudaStream_t user = (cudaStream_t)stream;
+    SWE_CHECK(wait_user_stream(p, user));
+    const int64_t per = 3 * p->nc;
+    SWE_CHECK_CUDA(cudaMemcpyAsync(p->U, U0, sizeof(double2) * per, cudaMemcpyDeviceToDevice, p->cs));
+    for (int n = 0; n < p->d.S; ++n) {
+        SWE_CHECK(coarse(p, p->U + per * n, p->Gold + per * n));
+        SWE_CHECK_CUDA(cudaMemcpyAsync(p->U + per * (n + 1), p->Gold + per * n, sizeof(double2) * per,
+                                       cudaMemcpyDeviceToDevice, p->cs));
+    }
+    SWE_CHECK(join_user_stream(p, user));
+    return SWE_OK;
+}
+
+// the serial part of one iteration: G chain + corrections (+ norm reduction)
+static swe_status chain(swe_pint* p) {
+    const int64_t per = 3 * p->nc;
+    SWE_CHECK_CUDA(cudaMemsetAsync(p->red, 0, sizeof(unsigned long long) * 6, p->cs));
+    for (int n = 0; n < p->d.S; ++n) {
+        SWE_CHECK(coarse(p, p->U + per * n, p->Gnew));
+        k_parareal_correct<<<(unsigned)((per + 255) / 256 < 1184 ? (per + 255) / 256 : 1184), 256, 0, p->cs>>>(
+            p->Gnew, p->Fo + per * n, p->Gold + per * n, p->U + per * (n + 1), p->nc, p->red,
+            p->d.fine_plan->flags);
+        SWE_CHECK_LAUNCH("k_parareal_correct");
+    }
+    return SWE_OK;
+}
+
+extern "C" swe_status parareal_iterate(swe_pint_t p, int kmax, double tol, int* k_done, double* norm_hist,
+                                       void* stream) {
+    if (!p || kmax < 0) {
+        swe_set_error("parareal_iterate: invalid argument");
+        return SWE_EINVAL;
+    }
+    cudaStream_t user = (cudaStream_t)stream;
+    SWE_CHECK(wait_user_stream(p, user));
+    SWE_CHECK_CUDA(cudaMemsetAsync(p->d.fine_plan->flags, 0, sizeof(int), p->cs));
+    const int S = p->d.S;
+    int k = 0;
+    swe_status status = SWE_OK;
+    for (; k < kmax; ++k) {
+        // fine propagator on every slice at once
+        SWE_CHECK(propagate_F(p->d.fine_plan, &p->d.fine, (const double*)p->U, (double*)p->Fo, S, p->cs));
+        if (p->d.use_graphs) {
+            if (!p->ready) {
+                SWE_CHECK_CUDA(cudaStreamBeginCapture(p->cs, cudaStreamCaptureModeThreadLocal));
+                swe_status s = chain(p);
+                cudaGraph_t g = nullptr;
+                cudaError_t e = cudaStreamEndCapture(p->cs, &g);
+                if (s != SWE_OK) return s;
+                if (e != cudaSuccess) return swe_cuda_status(e, "cudaStreamEndCapture(coarse chain)");
+                p->graph = g;
+                SWE_CHECK_CUDA(cudaGraphInstantiate(&p->gexec, g, 0));
+                p->ready = true;
+            }
+            SWE_CHECK_CUDA(cudaGraphLaunch(p->gexec, p->cs));
+        } else {
+            SWE_CHECK(chain(p));
+        }
+        unsigned long long red[6];
+        SWE_CHECK_CUDA(cudaMemcpyAsync(red, p->red, sizeof(red), cudaMemcpyDeviceToHost, p->cs));
+        int flag = 0;
+        SWE_CHECK_CUDA(cudaMemcpyAsync(&flag, p->d.fine_plan->flags, sizeof(int), cudaMemcpyDeviceToHost, p->cs));
+        SWE_CHECK_CUDA(cudaStreamSynchronize(p->cs));
+        double nrm = 0.0;
+        for (int q = 0; q < 3; ++q) {
+            double dd, vv;
+            memcpy(&dd, &red[q], sizeof(double));
+            memcpy(&vv, &red[3 + q], sizeof(double));
+            if (vv > 0) nrm = fmax(nrm, dd / vv);
+        }
+        if (norm_hist) norm_hist[k] = nrm;
+        if (flag) {
+            swe_set_error("parareal_iterate: non-finite value at iteration %d", k + 1);
+            status = SWE_EUNSTABLE;
+            ++k;
+            break;
+        }
+        if (tol > 0.0 && nrm < tol) {
+            ++k;
+            break;
+        }
+    }
+    if (k_done) *k_done = k;
+    SWE_CHECK(join_user_stream(p, user));
+    return status;
+}
+
+extern "C" swe_status swe_pint_solution(swe_pint_t p, double* U_out, void* stream) {
+    if (!p || !U_out) {
+        swe_set_error("swe_pint_solution: invalid argument");
+        return SWE_EINVAL;
+    }
+    cudaStream_t user = (cudaStream_t)stream;
+    SWE_CHECK(wait_user_stream(p, user));
+    SWE_CHECK_CUDA(cudaMemcpyAsync(U_out, p->U, sizeof(double2) * 3 * p->nc * (p->d.S + 1), cudaMemcpyDeviceToDevice,
+                                   p->cs));
+    SWE_CHECK(join_user_stream(p, user));
+    return SWE_OK;
+}

@@ -1,0 +1,496 @@
+// Spectral-space kernels: operand construction for the transforms, assembly of the
+// nonlinear tendency, the linear operator L = L_G + L_C (Eq. 1, f = 2 Omega mu), the
+// Crank-Nicolson / semi-implicit solve (I - alpha L) X = R (Eqs. 4, 7), backward-Euler
+// viscosity (App. A) and the nonlinear-balance initial state.
+//
+// State layout inside the library ("SoA"): [3][NC][S] complex128, slice fastest,
+// so that every kernel here reads and writes whole 32-slice segments.
+//
+// Spectral identities used (mu = sin(latitude), eps_n^m = sqrt((n^2-m^2)/(4n^2-1))):
+//   mu P_n^m = eps_{n+1}^m P_{n+1}^m + eps_n^m P_{n-1}^m
+//   (1 - mu^2) dP_n^m/dmu = -n eps_{n+1}^m P_{n+1}^m + (n+1) eps_n^m P_{n-1}^m
+// With psi = lap^{-1} xi, chi = lap^{-1} delta, U = u cos(lat), V = v cos(lat):
+//   U_n = (1/a)[i m chi_n + (n-1) eps_n psi_{n-1} - (n+2) eps_{n+1} psi_{n+1}]
+//   V_n = (1/a)[i m psi_n - (n-1) eps_n chi_{n-1} + (n+2) eps_{n+1} chi_{n+1}]   (n <= M+1)
+// and for a vector with components (A, B) = (a_lon, a_lat) cos(lat) whose quadrature
+// projections on P_n^m of A/(1-mu^2), B/(1-mu^2) are Ahat, Bhat (n <= M+1):
+//   div_n  = (1/a)[i m Ahat_n + n eps_{n+1} Bhat_{n+1} - (n+1) eps_n Bhat_{n-1}]
+//   curl_n = (1/a)[i m Bhat_n - n eps_{n+1} Ahat_{n+1} + (n+1) eps_n Ahat_{n-1}]
+// The Coriolis operator follows from -div(fV) = -f delta - (2 Omega/a) V and
+// curl(fV) = f xi - (2 Omega/a) U:
+//   (L_C U)_xi,n    = -2 Omega [p_n delta_{n-1} + q_n delta_{n+1} - i r_n xi_n]
+//   (L_C U)_delta,n =  2 Omega [p_n xi_{n-1}    + q_n xi_{n+1}    + i r_n delta_n]
+//   p_n = (n+1)/n eps_n,  q_n = n/(n+1) eps_{n+1},  r_n = m/(n(n+1)).
+#include "swe_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ double2 c_add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 c_sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 c_scale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 c_mul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 c_imul(double2 a, double s) { return make_double2(-a.y * s, a.x * s); }  // i s a
+__device__ __forceinline__ double2 c_inv(double2 a) {
+    double d = a.x * a.x + a.y * a.y;
+    return make_double2(a.x / d, -a.y / d);
+}
+__device__ __forceinline__ double2 czero() { return make_double2(0.0, 0.0); }
+
+__device__ __forceinline__ double coef_p(int m, int n) { return n >= 1 ? (n + 1.0) / n * eps_nm(m, n) : 0.0; }
+__device__ __forceinline__ double coef_q(int m, int n) { return n >= 1 ? n / (n + 1.0) * eps_nm(m, n + 1) : 0.0; }
+__device__ __forceinline__ double coef_r(int m, int n) { return n >= 1 ? (double)m / ((double)n * (n + 1.0)) : 0.0; }
+
+__device__ __forceinline__ void flag_nonfinite(int* flags, double2 v) {
+    if (!isfinite(v.x) || !isfinite(v.y)) atomicOr(flags, 1);
+}
+
+// ------------------------------------------------------------------ layouts
+__global__ void k_aos_soa(const double2* __restrict__ in, double2* __restrict__ out, int64_t nc, int S) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t total = 3 * nc * S;
+    if (t >= total) return;
+    int s = (int)(t % S);
+    int64_t fr = t / S;          // f * nc + r
+    out[t] = in[(int64_t)s * 3 * nc + fr];
+}
+
+__global__ void k_soa_aos(const double2* __restrict__ in, double2* __restrict__ out, int64_t nc, int S) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t total = 3 * nc * S;
+    if (t >= total) return;
+    int64_t fr = t % (3 * nc);
+    int s = (int)(t / (3 * nc));
+    out[t] = in[fr * S + s];
+}
+
+__global__ void k_pack(const double2* __restrict__ spec, double2* __restrict__ X, const int* __restrict__ row_m, int M,
+                       int64_t nc, int64_t ncx, int B) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= ncx * B) return;
+    int b = (int)(t % B);
+    int64_t rx = t / B;
+    int m = row_m[rx];
+    int n = m + (int)(rx - ex_off(m, M));
+    X[t] = (n <= M) ? spec[(int64_t)b * nc + st_off(m, M) + (n - m)] : czero();
+}
+
+__global__ void k_unpack(const double2* __restrict__ Y, double2* __restrict__ spec, const int* __restrict__ srow_m,
+                         int M, int64_t nc, int B) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nc * B) return;
+    int64_t r = t % nc;
+    int b = (int)(t / nc);
+    int m = srow_m[r];
+    int n = m + (int)(r - st_off(m, M));
+    spec[t] = Y[(ex_off(m, M) + (n - m)) * B + b];
+}
+
+// ------------------------------------------------------------------ nonlinear pre / post
+struct StateView {
+    const double2* a;
+    const double2* b;
+    double beta;
+    int64_t nc;
+    int S;
+    int M;
+    __device__ __forceinline__ double2 get(int f, int m, int n, int s) const {
+        if (n < m || n > M) return czero();
+        if (n == 0 && f > 0) return czero();     // xi_00 = delta_00 = 0
+        int64_t i = ((int64_t)f * nc + st_off(m, M) + (n - m)) * S + s;
+        double2 v = a[i];
+        if (b) v = c_add(v, c_scale(b[i], beta));
+        return v;
+    }
+};
+
+__global__ void k_nl_pre_kernel(StateView U, double2* __restrict__ X, const int* __restrict__ row_m, int64_t ncx,
+                                double a) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int S = U.S, M = U.M;
+    if (t >= ncx * S) return;
+    int s = (int)(t % S);
+    int64_t rx = t / S;
+    int m = row_m[rx];
+    int n = m + (int)(rx - ex_off(m, M));
+    const double a2 = a * a;
+    auto psi = [&](int k) -> double2 {
+        if (k < 1) return czero();
+        return c_scale(U.get(1, m, k, s), -a2 / ((double)k * (k + 1.0)));
+    };
+    auto chi = [&](int k) -> double2 {
+        if (k < 1) return czero();
+        return c_scale(U.get(2, m, k, s), -a2 / ((double)k * (k + 1.0)));
+    };
+    const double en = eps_nm(m, n), en1 = eps_nm(m, n + 1);
+    double2 ps_m = (n - 1 >= m) ? psi(n - 1) : czero();
+    double2 ch_m = (n - 1 >= m) ? chi(n - 1) : czero();
+    double2 ps_p = psi(n + 1), ch_p = chi(n + 1);
+    double2 ps_0 = psi(n), ch_0 = chi(n);
+    const double ia = 1.0 / a;
+    double2 Uh = c_scale(c_add(c_imul(ch_0, (double)m),
+                               c_sub(c_scale(ps_m, (n - 1.0) * en), c_scale(ps_p, (n + 2.0) * en1))),
+                         ia);
+    double2 Vh = c_scale(c_add(c_imul(ps_0, (double)m),
+                               c_sub(c_scale(ch_p, (n + 2.0) * en1), c_scale(ch_m, (n - 1.0) * en))),
+                         ia);
+    double2* row = X + rx * 4 * (int64_t)S + s;
+    row[0] = U.get(0, m, n, s);
+    row[S] = U.get(1, m, n, s);
+    row[2 * S] = Uh;
+    row[3 * S] = Vh;
+}
+
+__global__ void k_nl_post_kernel(const double2* __restrict__ Y, int mode, double dt, const double2* __restrict__ in0,
+                                 const double2* __restrict__ in1, double2* __restrict__ out0,
+                                 double2* __restrict__ out1, const int* __restrict__ srow_m, int M, int64_t nc, int S,
+                                 double a, int* flags) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nc * S) return;
+    int s = (int)(t % S);
+    int64_t r = t / S;
+    int m = srow_m[r];
+    int n = m + (int)(r - st_off(m, M));
+    const int64_t C5 = 5 * (int64_t)S;
+    const double2* y0 = Y + (ex_off(m, M) + (n - m)) * C5 + s;
+    const double2* yp = y0 + C5;                       // n + 1 (<= M + 1 always present)
+    const bool hm = (n - 1 >= m);
+    const double2* ym = y0 - C5;
+    double2 A1 = y0[0], B1 = y0[S], A2 = y0[2 * S], KE = y0[4 * S];
+    double2 A1p = yp[0], B1p = yp[S], B2p = yp[3 * S];
+    double2 A1m = hm ? ym[0] : czero(), B1m = hm ? ym[S] : czero(), B2m = hm ? ym[3 * S] : czero();
+    const double en = eps_nm(m, n), en1 = eps_nm(m, n + 1);
+    const double ia = 1.0 / a;
+    const double cp = n * en1, cm = (n + 1.0) * en;
+    double2 div1 = c_scale(c_add(c_imul(A1, (double)m), c_sub(c_scale(B1p, cp), c_scale(B1m, cm))), ia);
+    double2 curl1 = c_scale(c_add(c_imul(B1, (double)m), c_sub(c_scale(A1m, cm), c_scale(A1p, cp))), ia);
+    double2 div2 = c_scale(c_add(c_imul(A2, (double)m), c_sub(c_scale(B2p, cp), c_scale(B2m, cm))), ia);
+    double2 N[3];
+    N[0] = c_scale(div2, -1.0);
+    N[1] = c_scale(div1, -1.0);
+    N[2] = c_add(curl1, c_scale(KE, (double)n * (n + 1.0) * ia * ia));
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        int64_t i = ((int64_t)f * nc + r) * S + s;
+        flag_nonfinite(flags, N[f]);
+        if (mode == POST_N) {
+            out0[i] = N[f];
+        } else if (mode == POST_STAGE1) {
+            double2 ub = c_scale(N[f], dt);
+            out0[i] = ub;
+            out1[i] = c_add(in0[i], ub);
+        } else {
+            out0[i] = c_add(in0[i], c_scale(c_add(in1[i], c_scale(N[f], dt)), 0.5));
+        }
+    }
+}
+
+// ------------------------------------------------------------------ linear operator
+// mode 0: out = L U ; mode 1: out = U + alpha L U
+__global__ void k_linop(StateView U, double2* __restrict__ out, const int* __restrict__ srow_m, int mode,
+                        double alpha, double a, double omega, double phibar) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int S = U.S, M = U.M;
+    const int64_t nc = U.nc;
+    if (t >= nc * S) return;
+    int s = (int)(t % S);
+    int64_t r = t / S;
+    int m = srow_m[r];
+    int n = m + (int)(r - st_off(m, M));
+    double2 ph = U.get(0, m, n, s), xi = U.get(1, m, n, s), de = U.get(2, m, n, s);
+    double2 xim = U.get(1, m, n - 1, s), xip = U.get(1, m, n + 1, s);
+    double2 dem = U.get(2, m, n - 1, s), dep = U.get(2, m, n + 1, s);
+    const double w2 = 2.0 * omega;
+    const double p = coef_p(m, n), q = coef_q(m, n), rr = coef_r(m, n);
+    double2 L0 = c_scale(de, -phibar);
+    double2 L1 = c_add(c_scale(c_add(c_scale(dem, p), c_scale(dep, q)), -w2), c_imul(xi, w2 * rr));
+    double2 L2 = c_add(c_scale(ph, (double)n * (n + 1.0) / (a * a)),
+                       c_add(c_scale(c_add(c_scale(xim, p), c_scale(xip, q)), w2), c_imul(de, w2 * rr)));
+    double2 o[3] = {L0, L1, L2};
+    if (mode == 1) {
+        o[0] = c_add(ph, c_scale(L0, alpha));
+        o[1] = c_add(xi, c_scale(L1, alpha));
+        o[2] = c_add(de, c_scale(L2, alpha));
+    }
+#pragma unroll
+    for (int f = 0; f < 3; ++f) out[((int64_t)f * nc + r) * S + s] = o[f];
+}
+
+// ------------------------------------------------------------------ implicit solve
+// Eliminating Phi_n = R^Phi_n - alpha Phi_bar delta_n and xi_{n+-1} from (I - alpha L) X = R
+// leaves, for each m and each parity of n - m, a tridiagonal system in delta:
+//   a_k delta_{n-2} + b_k delta_n + c_k delta_{n+2} = rhs_k,   n = m + par + 2k, with c = 2 Omega alpha,
+//   d_j = 1 - i c r_j,  D_n = 1 + alpha^2 Phi_bar n(n+1)/a^2 - i c r_n,
+//   a_k = c^2 p_n p_{n-1}/d_{n-1},  c_k = c^2 q_n q_{n+1}/d_{n+1},
+//   b_k = D_n + c^2 p_n q_{n-1}/d_{n-1} + c^2 q_n p_{n+1}/d_{n+1},
+//   rhs_k = R^delta_n + alpha n(n+1)/a^2 R^Phi_n + c p_n R^xi_{n-1}/d_{n-1} + c q_n R^xi_{n+1}/d_{n+1}
+// (terms with xi_{n+1} only when n+1 <= M), then
+//   xi_n = [R^xi_n - c (p_n delta_{n-1} + q_n delta_{n+1})] / d_n.
+// The Thomas factorisation depends only on (m, n, alpha) and is precomputed:
+//   fac[0] = a_k, fac[1] = 1/(b_k - a_k c'_{k-1}), fac[2] = c'_k, fac[3] = c p_n/d_{n-1},
+//   fac[4] = c q_n/d_{n+1}, fac[5] = 1/d_n, fac[6] = (c p_n, c q_n [n+1<=M]),
+//   fac[7] = (alpha n(n+1)/a^2, alpha Phi_bar).
+__global__ void k_cn_factor(int M, double alpha, double a, double omega, double phibar, double2* __restrict__ fac) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * (M + 1)) return;
+    const int m = t >> 1, par = t & 1;
+    const double c = 2.0 * omega * alpha;
+    auto dd = [&](int j) { return make_double2(1.0, -c * coef_r(m, j)); };
+    double2 cprev = czero();
+    for (int n = m + par; n <= M; n += 2) {
+        const bool hm = (n - 1 >= m), hp = (n + 1 <= M);
+        const double pn = coef_p(m, n), qn = coef_q(m, n);
+        double2 Dn = make_double2(1.0 + alpha * alpha * phibar * n * (n + 1.0) / (a * a), -c * coef_r(m, n));
+        double2 ak = czero(), ck = czero(), Em = czero(), Ep = czero();
+        double2 bk = Dn;
+        if (hm) {
+            double2 idm = c_inv(dd(n - 1));
+            ak = c_scale(idm, c * c * pn * coef_p(m, n - 1));
+            bk = c_add(bk, c_scale(idm, c * c * pn * coef_q(m, n - 1)));
+            Em = c_scale(idm, c * pn);
+        }
+        if (hp) {
+            double2 idp = c_inv(dd(n + 1));
+            ck = c_scale(idp, c * c * qn * coef_q(m, n + 1));
+            bk = c_add(bk, c_scale(idp, c * c * qn * coef_p(m, n + 1)));
+            Ep = c_scale(idp, c * qn);
+        }
+        double2 g = c_inv(c_sub(bk, c_mul(ak, cprev)));
+        double2 cpk = c_mul(ck, g);
+        double2* f = fac + (st_off(m, M) + (n - m)) * 8;
+        f[0] = ak;
+        f[1] = g;
+        f[2] = cpk;
+        f[3] = Em;
+        f[4] = Ep;
+        f[5] = c_inv(dd(n));
+        f[6] = make_double2(c * pn, hp ? c * qn : 0.0);
+        f[7] = make_double2(alpha * n * (n + 1.0) / (a * a), alpha * phibar);
+        cprev = cpk;
+    }
+}
+
+__device__ __forceinline__ double visc_factor(int n, double dt, double nu, int q, double a) {
+    if (nu <= 0.0) return 1.0;
+    double l = (double)n * (n + 1.0) / (a * a);
+    double lq = 1.0;
+    for (int i = 0; i < q / 2; ++i) lq *= l;
+    return 1.0 / (1.0 + dt * nu * lq);
+}
+
+// One thread per (m, parity, slice).  X may alias R: the thread of parity par
+// reads R^Phi, R^delta at n = m+par (mod 2) and R^xi at the other parity, and
+// writes Phi, delta and xi at exactly those positions, each after its last read;
+// the other parity's thread touches the complementary positions.
+__global__ void k_cn_solve(const double2* __restrict__ fac, const double2* R, double2* X, int M, int64_t nc, int S,
+                           double vdt, double vnu, int vq, double a) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)2 * (M + 1) * S) return;
+    const int s = (int)(t % S);
+    const int mp = (int)(t / S);
+    const int m = mp >> 1, par = mp & 1;
+    const int64_t base = st_off(m, M);
+    auto idx = [&](int f, int n) { return ((int64_t)f * nc + base + (n - m)) * S + s; };
+    auto rxi = [&](int n) -> double2 {           // R^xi_n with xi_00 treated as zero
+        if (n < m || n > M || n == 0) return czero();
+        return R[idx(1, n)];
+    };
+    // forward elimination over delta_n, n = m + par + 2k
+    double2 dprev = czero();
+    int nlast = m + par - 2;
+    for (int n = m + par; n <= M; n += 2) {
+        const double2* f = fac + (base + (n - m)) * 8;
+        double2 rp = R[idx(0, n)];
+        double2 rd = (n == 0) ? czero() : R[idx(2, n)];
+        double2 rhs = c_add(rd, c_scale(rp, f[7].x));
+        rhs = c_add(rhs, c_mul(f[3], rxi(n - 1)));
+        rhs = c_add(rhs, c_mul(f[4], rxi(n + 1)));
+        double2 dp = c_mul(c_sub(rhs, c_mul(f[0], dprev)), f[1]);
+        X[idx(2, n)] = dp;
+        dprev = dp;
+        nlast = n;
+    }
+    // back substitution for delta, then Phi_n = R^Phi_n - alpha Phi_bar delta_n
+    double2 dnext = czero();
+    for (int n = nlast; n >= m + par; n -= 2) {
+        const double2* f = fac + (base + (n - m)) * 8;
+        double2 dn = c_sub(X[idx(2, n)], c_mul(f[2], dnext));
+        if (n == 0) dn = czero();
+        dnext = dn;
+        double2 ph = c_sub(R[idx(0, n)], c_scale(dn, f[7].y));
+        X[idx(2, n)] = dn;
+        X[idx(0, n)] = ph;
+    }
+    // xi on the other parity: xi_n = [R^xi_n - c p_n delta_{n-1} - c q_n delta_{n+1}] / d_n
+    for (int n = m + (par ^ 1); n <= M; n += 2) {
+        const double2* f = fac + (base + (n - m)) * 8;
+        double2 dm = (n - 1 >= m) ? X[idx(2, n - 1)] : czero();
+        double2 dpv = (n + 1 <= M) ? X[idx(2, n + 1)] : czero();
+        double2 num = c_sub(rxi(n), c_add(c_scale(dm, f[6].x), c_scale(dpv, f[6].y)));
+        double2 xn = (n == 0) ? czero() : c_mul(num, f[5]);
+        X[idx(1, n)] = c_scale(xn, visc_factor(n, vdt, vnu, vq, a));
+    }
+    // backward-Euler viscosity on delta and Phi (after xi used the unscaled delta)
+    if (vnu > 0.0) {
+        for (int n = m + par; n <= M; n += 2) {
+            double v = visc_factor(n, vdt, vnu, vq, a);
+            X[idx(2, n)] = c_scale(X[idx(2, n)], v);
+            X[idx(0, n)] = c_scale(X[idx(0, n)], v);
+        }
+    }
+}
+
+__global__ void k_balance(const double2* __restrict__ xi, const double2* __restrict__ N,
+                          const double2* __restrict__ add, double2* __restrict__ U, const int* __restrict__ srow_m,
+                          int M, int64_t nc, int S, double a, double omega) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nc * S) return;
+    int s = (int)(t % S);
+    int64_t r = t / S;
+    int m = srow_m[r];
+    int n = m + (int)(r - st_off(m, M));
+    auto X = [&](int k) -> double2 {
+        if (k < m || k > M || k == 0) return czero();
+        return xi[(st_off(m, M) + (k - m)) * S + s];
+    };
+    double2 ph = czero();
+    if (n >= 1) {
+        double2 lc = c_scale(c_add(c_scale(X(n - 1), coef_p(m, n)), c_scale(X(n + 1), coef_q(m, n))), 2.0 * omega);
+        double2 nd = N[(2 * nc + r) * S + s];
+        ph = c_scale(c_add(lc, nd), -a * a / ((double)n * (n + 1.0)));
+    }
+    if (add) ph = c_add(ph, add[r * S + s]);
+    U[(0 * nc + r) * S + s] = ph;
+    U[(1 * nc + r) * S + s] = X(n);
+    U[(2 * nc + r) * S + s] = czero();
+}
+
+__global__ void k_axpy_kernel(double2* __restrict__ y, const double2* __restrict__ x, double a, int64_t n) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n) y[t] = c_add(y[t], c_scale(x[t], a));
+}
+
+// AoS [S][3][NC(Min)] -> AoS [S][3][NC(Mout)]: keep n <= min(Min, Mout), zero the rest
+__global__ void k_trunc(const double2* __restrict__ in, int Min, double2* __restrict__ out, int Mout, int S) {
+    int64_t ncout = nc_state(Mout), ncin = nc_state(Min);
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= 3 * ncout * S) return;
+    int64_t r = t % ncout;
+    int64_t sf = t / ncout;
+    // locate (m, n) of r in the output truncation
+    int m = 0;
+    while (m < Mout && st_off(m + 1, Mout) <= r) ++m;
+    int n = m + (int)(r - st_off(m, Mout));
+    double2 v = czero();
+    if (m <= Min && n <= Min) v = in[sf * ncin + st_off(m, Min) + (n - m)];
+    out[t] = v;
+}
+
+inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+swe_status k_aos_to_soa(const swe_plan* p, const double2* in, double2* out, int S, cudaStream_t st) {
+    k_aos_soa<<<nblk(3 * p->nc * S), 256, 0, st>>>(in, out, p->nc, S);
+    SWE_CHECK_LAUNCH("k_aos_soa");
+    return SWE_OK;
+}
+swe_status k_soa_to_aos(const swe_plan* p, const double2* in, double2* out, int S, cudaStream_t st) {
+    k_soa_aos<<<nblk(3 * p->nc * S), 256, 0, st>>>(in, out, p->nc, S);
+    SWE_CHECK_LAUNCH("k_soa_aos");
+    return SWE_OK;
+}
+swe_status k_pack_scalar(const swe_plan* p, const double2* spec, double2* X, int B, cudaStream_t st) {
+    k_pack<<<nblk(p->ncx * B), 256, 0, st>>>(spec, X, p->row_m, p->M, p->nc, p->ncx, B);
+    SWE_CHECK_LAUNCH("k_pack");
+    return SWE_OK;
+}
+swe_status k_unpack_scalar(const swe_plan* p, const double2* Y, double2* spec, int B, cudaStream_t st) {
+    k_unpack<<<nblk(p->nc * B), 256, 0, st>>>(Y, spec, p->srow_m, p->M, p->nc, B);
+    SWE_CHECK_LAUNCH("k_unpack");
+    return SWE_OK;
+}
+swe_status k_nl_pre(const swe_plan* p, const double2* Ua, const double2* Ub, double beta, double2* X, int S,
+                    cudaStream_t st) {
+    StateView v{Ua, Ub, beta, p->nc, S, p->M};
+    k_nl_pre_kernel<<<nblk(p->ncx * S), 256, 0, st>>>(v, X, p->row_m, p->ncx, p->a);
+    SWE_CHECK_LAUNCH("k_nl_pre");
+    return SWE_OK;
+}
+swe_status k_nl_post(const swe_plan* p, const double2* Y, int mode, double dt, const double2* in0, const double2* in1,
+                     double2* out0, double2* out1, int S, cudaStream_t st) {
+    k_nl_post_kernel<<<nblk(p->nc * S), 256, 0, st>>>(Y, mode, dt, in0, in1, out0, out1, p->srow_m, p->M, p->nc, S,
+                                                     p->a, p->flags);
+    SWE_CHECK_LAUNCH("k_nl_post");
+    return SWE_OK;
+}
+swe_status k_linear(const swe_plan* p, const double2* U, double2* LU, int S, cudaStream_t st) {
+    StateView v{U, nullptr, 0.0, p->nc, S, p->M};
+    k_linop<<<nblk(p->nc * S), 256, 0, st>>>(v, LU, p->srow_m, 0, 0.0, p->a, p->omega, p->phibar);
+    SWE_CHECK_LAUNCH("k_linop");
+    return SWE_OK;
+}
+
+swe_status plan_cn_factor(swe_plan* p, double alpha, const double2** fac, cudaStream_t st) {
+    for (int i = 0; i < p->ncn; ++i)
+        if (p->cn[i].alpha == alpha) {
+            *fac = p->cn[i].fac;
+            return SWE_OK;
+        }
+    int slot = p->ncn < 16 ? p->ncn++ : 15;
+    if (p->ncn == 16 && slot == 15 && p->cn[15].fac) {
+        SWE_CHECK_CUDA(cudaStreamSynchronize(st));
+        cudaFree(p->cn[15].fac);
+        p->cn[15].fac = nullptr;
+    }
+    double2* f;
+    SWE_CHECK_CUDA(cudaMalloc((void**)&f, sizeof(double2) * 8 * p->nc));
+    k_cn_factor<<<nblk(2 * (p->M + 1), 64), 64, 0, st>>>(p->M, alpha, p->a, p->omega, p->phibar, f);
+    SWE_CHECK_LAUNCH("k_cn_factor");
+    p->cn[slot].alpha = alpha;
+    p->cn[slot].fac = f;
+    *fac = f;
+    return SWE_OK;
+}
+
+swe_status k_implicit(swe_plan* p, double alpha, int with_rhs, const double2* in, double2* out, double visc_dt,
+                      double visc_nu, int visc_q, int S, cudaStream_t st) {
+    const double2* fac;
+    SWE_CHECK(plan_cn_factor(p, alpha, &fac, st));
+    const double2* R = in;
+    if (with_rhs) {
+        if (in == out) {
+            swe_set_error("k_implicit: Crank-Nicolson right-hand side needs distinct buffers");
+            return SWE_EINVAL;
+        }
+        StateView v{in, nullptr, 0.0, p->nc, S, p->M};
+        k_linop<<<nblk(p->nc * S), 256, 0, st>>>(v, out, p->srow_m, 1, alpha, p->a, p->omega, p->phibar);
+        SWE_CHECK_LAUNCH("k_linop(rhs)");
+        R = out;
+    }
+    k_cn_solve<<<nblk((int64_t)2 * (p->M + 1) * S, 128), 128, 0, st>>>(fac, R, out, p->M, p->nc, S, visc_dt, visc_nu,
+                                                                    visc_q, p->a);
+    SWE_CHECK_LAUNCH("k_cn_solve");
+    return SWE_OK;
+}
+
+swe_status k_balance_combine(const swe_plan* p, const double2* xi_soa, const double2* N, const double2* phi_add_soa,
+                             double2* U, int S, cudaStream_t st) {
+    k_balance<<<nblk(p->nc * S), 256, 0, st>>>(xi_soa, N, phi_add_soa, U, p->srow_m, p->M, p->nc, S, p->a, p->omega);
+    SWE_CHECK_LAUNCH("k_balance");
+    return SWE_OK;
+}
+
+swe_status k_axpy(double2* y, const double2* x, double a, int64_t n, cudaStream_t st) {
+    k_axpy_kernel<<<nblk(n), 256, 0, st>>>(y, x, a, n);
+    SWE_CHECK_LAUNCH("k_axpy");
+    return SWE_OK;
+}
+
+swe_status k_truncate(const double2* in, int Min, double2* out, int Mout, int S, cudaStream_t st) {
+    k_trunc<<<nblk(3 * nc_state(Mout) * S), 256, 0, st>>>(in, Min, out, Mout, S);
+    SWE_CHECK_LAUNCH("k_trunc");
+    return SWE_OK;
+}

@@ -1,0 +1,151 @@
+// Internal declarations of the GB300 shallow-water library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "../../include/swe_gb300.h"
+
+// ---------------------------------------------------------------------------
+// error plumbing: thread-local message + status codes, no exceptions across the ABI
+void swe_set_error(const char* fmt, ...);
+swe_status swe_cuda_status(cudaError_t e, const char* what);
+
+#define SWE_CHECK_CUDA(call)                                                   \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) return swe_cuda_status(e_, #call);              \
+    } while (0)
+
+#define SWE_CHECK(call)                                                        \
+    do {                                                                       \
+        swe_status s_ = (call);                                                \
+        if (s_ != SWE_OK) return s_;                                           \
+    } while (0)
+
+#define SWE_CHECK_LAUNCH(what)                                                 \
+    do {                                                                       \
+        cudaError_t e_ = cudaGetLastError();                                   \
+        if (e_ != cudaSuccess) return swe_cuda_status(e_, what);               \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// spectral index helpers
+//   "state" rows: (m, n), 0 <= m <= n <= M            -> NC(M) rows
+//   "extended" rows: (m, n), 0 <= m <= M, m <= n <= M+1 -> NCX rows (transform operands)
+__host__ __device__ inline int64_t st_off(int m, int M) {
+    return (int64_t)m * (M + 1) - (int64_t)m * (m - 1) / 2;
+}
+__host__ __device__ inline int64_t ex_off(int m, int M) {
+    return (int64_t)m * (M + 2) - (int64_t)m * (m - 1) / 2;
+}
+__host__ __device__ inline int64_t nc_state(int M) { return (int64_t)(M + 1) * (M + 2) / 2; }
+__host__ __device__ inline int64_t nc_ext(int M) { return (int64_t)(M + 1) * (M + 4) / 2; }
+
+// epsilon_n^m = sqrt((n^2 - m^2) / (4 n^2 - 1)), zero for n <= m
+__host__ __device__ inline double eps_nm(int m, int n) {
+    if (n <= m) return 0.0;
+    double nn = (double)n, mm = (double)m;
+    return sqrt((nn * nn - mm * mm) / (4.0 * nn * nn - 1.0));
+}
+
+// ---------------------------------------------------------------------------
+// CN / implicit-solve factorisation for one alpha (see spectral.cu)
+struct CNFactor {
+    double alpha;
+    double2* fac;   // [NC][8] complex coefficients per (m, n)
+};
+
+struct Workspace {
+    char* base = nullptr;
+    size_t bytes = 0;
+};
+
+struct swe_plan {
+    int M, nlat, nlon, nlat2;
+    double a, omega, g, phibar;
+    swe_precision prec;
+    int device;
+    int64_t nc, ncx;
+    // device tables (FP64)
+    double* mu = nullptr;       // [nlat] north -> south
+    double* w = nullptr;        // [nlat]
+    double* P = nullptr;        // [ncx][nlat2]: P_n^m(mu_j), j in the northern half
+    int* row_m = nullptr;       // [ncx] m of each extended row
+    int* srow_m = nullptr;      // [nc]  m of each state row
+    double2* tw = nullptr;      // [nlon] e^{-2 pi i k / nlon}
+    float2* twf = nullptr;      // FP32 copy
+    int nrad = 0;
+    int rad[32];
+    // split-precision Legendre operands (bf16 hi/lo), built lazily
+    void* Pbf = nullptr;
+    // implicit-solve factor cache
+    CNFactor cn[16];
+    int ncn = 0;
+    // workspace arena
+    Workspace ws;
+    // device flags: [0] non-finite seen
+    int* flags = nullptr;
+};
+
+// ---------------------------------------------------------------------------
+// plan helpers (plan.cu)
+swe_status plan_workspace(swe_plan* p, size_t bytes, char** out);
+swe_status plan_cn_factor(swe_plan* p, double alpha, const double2** fac, cudaStream_t st);
+
+// workspace layout of a nonlinear evaluation / stepper for S columns
+struct NLBuffers {
+    double2* X;     // [ncx][4S]    transform operands (Phi', xi, U, V)
+    void* Fin;      // [M+1][nlat][4S] Fourier coefficients (double2 or float2)
+    void* Fout;     // [M+1][nlat][5S]
+    double2* Y;     // [ncx][5S]    forward-transform results (A1, B1, A2, B2, KE)
+};
+size_t nl_bytes(const swe_plan* p, int S);
+NLBuffers nl_carve(const swe_plan* p, char* base, int S);
+
+// ---------------------------------------------------------------------------
+// kernel launchers (legendre.cu, ring.cu, spectral.cu)
+swe_status leg_inverse(const swe_plan* p, const double2* X, void* F, int C, cudaStream_t st);
+swe_status leg_forward(const swe_plan* p, const void* F, double2* Y, int C, cudaStream_t st);
+
+swe_status ring_inverse(const swe_plan* p, const void* F, void* grid, int C, cudaStream_t st);
+swe_status ring_forward(const swe_plan* p, const void* grid, void* F, int C, cudaStream_t st);
+swe_status ring_nonlinear(const swe_plan* p, const void* Fin, void* Fout, int S, cudaStream_t st);
+
+// state layout conversions: AoS [S][3][NC] <-> SoA [3][NC][S]
+swe_status k_aos_to_soa(const swe_plan* p, const double2* in, double2* out, int S, cudaStream_t st);
+swe_status k_soa_to_aos(const swe_plan* p, const double2* in, double2* out, int S, cudaStream_t st);
+
+// scalar spectral [B][NC] <-> transform operand [ncx][B]
+swe_status k_pack_scalar(const swe_plan* p, const double2* spec, double2* X, int B, cudaStream_t st);
+swe_status k_unpack_scalar(const swe_plan* p, const double2* Y, double2* spec, int B, cudaStream_t st);
+
+// nonlinear pre/post (SoA state, S columns)
+//   X <- operands of U_a + beta * U_b
+swe_status k_nl_pre(const swe_plan* p, const double2* Ua, const double2* Ub, double beta,
+                    double2* X, int S, cudaStream_t st);
+// post modes
+enum { POST_N = 0, POST_STAGE1 = 1, POST_STAGE2 = 2 };
+//   POST_N:      out0 <- N
+//   POST_STAGE1: out0 <- dt N (=Ubar), out1 <- in0 + dt N  (in0 = U*)
+//   POST_STAGE2: out0 <- in0 + (in1 + dt N) / 2            (in0 = U*, in1 = Ubar)
+swe_status k_nl_post(const swe_plan* p, const double2* Y, int mode, double dt, const double2* in0,
+                     const double2* in1, double2* out0, double2* out1, int S, cudaStream_t st);
+
+// implicit solve (SoA). If with_rhs, R = (I + alpha L) U is formed first (Crank-Nicolson).
+// Viscosity factor [1 + dt nu (n(n+1)/a^2)^{q/2}]^{-1} applied to the result if nu > 0.
+swe_status k_implicit(swe_plan* p, double alpha, int with_rhs, const double2* in, double2* out,
+                      double visc_dt, double visc_nu, int visc_q, int S, cudaStream_t st);
+swe_status k_linear(const swe_plan* p, const double2* U, double2* LU, int S, cudaStream_t st);
+swe_status k_balance_combine(const swe_plan* p, const double2* xi_soa, const double2* N,
+                             const double2* phi_add_soa, double2* U, int S, cudaStream_t st);
+swe_status k_axpy(double2* y, const double2* x, double a, int64_t n, cudaStream_t st);
+swe_status k_truncate(const double2* in, int Min, double2* out, int Mout, int S, cudaStream_t st);
+
+// stepper (stepper.cu), SoA state with S columns; U updated in place
+swe_status stepper_run(swe_plan* p, const swe_stepper_desc* sd, double2* U, int S, cudaStream_t st);
+size_t stepper_bytes(const swe_plan* p, int S);
+swe_status nonlinear_soa(swe_plan* p, const double2* Ua, const double2* Ub, double beta,
+                         double2* N, int S, char* ws, cudaStream_t st);

@@ -1,0 +1,220 @@
+"""Thin ctypes binding of ``libswe_gb300.so`` (C ABI in ``include/swe_gb300.h``).
+
+Argument marshalling only: every computation runs in the CUDA library.  Device
+arrays are passed as torch tensors (their data pointers) or raw integer
+addresses; streams default to torch's current CUDA stream.  There is no CPU
+fallback: if the library is missing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from typing import Optional
+
+from .build import lib_path
+
+SWE_OK, SWE_EINVAL, SWE_ENOMEM, SWE_ECUDA, SWE_EUNSTABLE, SWE_ETIMEOUT, SWE_ENOTCONV = range(7)
+SWE_FP64, SWE_SPLIT_BF16X3 = 0, 1
+SWE_IMEX, SWE_SLSI_SETTLS, SWE_SLSI_SETTLS_1STEP = 0, 1, 2
+
+STATUS_NAMES = {0: "SWE_OK", 1: "SWE_EINVAL", 2: "SWE_ENOMEM", 3: "SWE_ECUDA", 4: "SWE_EUNSTABLE",
+                5: "SWE_ETIMEOUT", 6: "SWE_ENOTCONV"}
+
+# Every symbol include/swe_gb300.h declares (checked by the CPU test suite).
+EXPORTED = [
+    "swe_version", "swe_last_error", "swe_ncoef", "swe_plan_create", "swe_plan_destroy", "swe_plan_gauss",
+    "sht_inverse", "sht_forward", "swe_nonlinear", "swe_linear", "swe_implicit_solve", "swe_balance",
+    "propagate_F", "propagate_G", "swe_pint_create", "swe_pint_destroy", "swe_pint_init", "parareal_iterate",
+    "swe_pint_solution",
+]
+
+
+class SWEError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class PlanDesc(ct.Structure):
+    _fields_ = [("M", ct.c_int), ("nlat", ct.c_int), ("nlon", ct.c_int), ("a", ct.c_double),
+                ("omega", ct.c_double), ("g", ct.c_double), ("phibar", ct.c_double), ("prec", ct.c_int)]
+
+
+class StepperDesc(ct.Structure):
+    _fields_ = [("scheme", ct.c_int), ("dt", ct.c_double), ("nsteps", ct.c_int), ("visc_q", ct.c_int),
+                ("visc_nu", ct.c_double)]
+
+
+class PintDesc(ct.Structure):
+    _fields_ = [("fine_plan", ct.c_void_p), ("coarse_plan", ct.c_void_p), ("fine", StepperDesc),
+                ("coarse", StepperDesc), ("S", ct.c_int), ("use_graphs", ct.c_int)]
+
+
+_lib = None
+
+
+def load(path: Optional[str] = None) -> ct.CDLL:
+    """Load the CUDA library (built in-tree by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    lib = ct.CDLL(path)
+    vp, i, d = ct.c_void_p, ct.c_int, ct.c_double
+    sigs = {
+        "swe_version": ([], ct.c_char_p),
+        "swe_last_error": ([], ct.c_char_p),
+        "swe_ncoef": ([i], ct.c_int64),
+        "swe_plan_create": ([ct.POINTER(PlanDesc), ct.POINTER(vp)], i),
+        "swe_plan_destroy": ([vp], i),
+        "swe_plan_gauss": ([vp, vp, vp], i),
+        "sht_inverse": ([vp, vp, vp, i, vp], i),
+        "sht_forward": ([vp, vp, vp, i, vp], i),
+        "swe_nonlinear": ([vp, vp, vp, i, vp], i),
+        "swe_linear": ([vp, vp, vp, i, vp], i),
+        "swe_implicit_solve": ([vp, d, vp, vp, i, vp], i),
+        "swe_balance": ([vp, vp, vp, vp, i, vp], i),
+        "propagate_F": ([vp, ct.POINTER(StepperDesc), vp, vp, i, vp], i),
+        "propagate_G": ([vp, vp, ct.POINTER(StepperDesc), vp, vp, i, vp], i),
+        "swe_pint_create": ([ct.POINTER(PintDesc), ct.POINTER(vp)], i),
+        "swe_pint_destroy": ([vp], i),
+        "swe_pint_init": ([vp, vp, vp], i),
+        "parareal_iterate": ([vp, i, d, ct.POINTER(i), ct.POINTER(d), vp], i),
+        "swe_pint_solution": ([vp, vp, vp], i),
+    }
+    for name, (args, res) in sigs.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != SWE_OK:
+        raise SWEError(status, load().swe_last_error().decode())
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def ncoef(M: int) -> int:
+    return int(load().swe_ncoef(M))
+
+
+def stepper(scheme=SWE_IMEX, dt=60.0, nsteps=1, visc_q=2, visc_nu=0.0) -> StepperDesc:
+    return StepperDesc(scheme, dt, nsteps, visc_q, visc_nu)
+
+
+class Plan:
+    """A truncation T_M on an nlat x nlon Gaussian grid (swe_plan_create)."""
+
+    def __init__(self, M, nlat, nlon, a=6371.22e3, omega=7.292e-5, g=9.80616, phibar=1.0e5, prec=SWE_FP64):
+        lib = load()
+        self.M, self.nlat, self.nlon, self.prec = M, nlat, nlon, prec
+        self.a, self.omega, self.g, self.phibar = a, omega, g, phibar
+        desc = PlanDesc(M, nlat, nlon, a, omega, g, phibar, prec)
+        h = ct.c_void_p()
+        _check(lib.swe_plan_create(ct.byref(desc), ct.byref(h)))
+        self.h = h
+        self.nc = ncoef(M)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().swe_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def gauss(self):
+        import numpy as np
+        mu = np.empty(self.nlat)
+        w = np.empty(self.nlat)
+        _check(load().swe_plan_gauss(self.h, mu.ctypes.data, w.ctypes.data))
+        return mu, w
+
+    # -- transforms --------------------------------------------------------
+    def sht_inverse(self, spec, grid, batch, stream=None):
+        _check(load().sht_inverse(self.h, _ptr(spec), _ptr(grid), batch, _stream(stream)))
+
+    def sht_forward(self, grid, spec, batch, stream=None):
+        _check(load().sht_forward(self.h, _ptr(grid), _ptr(spec), batch, _stream(stream)))
+
+    # -- operators ---------------------------------------------------------
+    def nonlinear(self, U, N, S, stream=None):
+        _check(load().swe_nonlinear(self.h, _ptr(U), _ptr(N), S, _stream(stream)))
+
+    def linear(self, U, LU, S, stream=None):
+        _check(load().swe_linear(self.h, _ptr(U), _ptr(LU), S, _stream(stream)))
+
+    def implicit_solve(self, alpha, R, X, S, stream=None):
+        _check(load().swe_implicit_solve(self.h, alpha, _ptr(R), _ptr(X), S, _stream(stream)))
+
+    def balance(self, xi, phi_add, U, S, stream=None):
+        _check(load().swe_balance(self.h, _ptr(xi), _ptr(phi_add), _ptr(U), S, _stream(stream)))
+
+    def propagate(self, st: StepperDesc, U_in, U_out, S, stream=None):
+        _check(load().propagate_F(self.h, ct.byref(st), _ptr(U_in), _ptr(U_out), S, _stream(stream)))
+
+    def propagate_G(self, fine: Optional["Plan"], st: StepperDesc, U_in, U_out, S, stream=None):
+        fh = fine.h if fine is not None else None
+        _check(load().propagate_G(self.h, fh, ct.byref(st), _ptr(U_in), _ptr(U_out), S, _stream(stream)))
+
+
+class Parareal:
+    """Parareal on S slices (swe_pint_create / swe_pint_init / parareal_iterate)."""
+
+    def __init__(self, fine_plan: Plan, coarse_plan: Plan, fine: StepperDesc, coarse: StepperDesc, S: int,
+                 use_graphs: bool = True):
+        lib = load()
+        self.fine_plan, self.coarse_plan, self.S = fine_plan, coarse_plan, S
+        desc = PintDesc(fine_plan.h, coarse_plan.h, fine, coarse, S, 1 if use_graphs else 0)
+        h = ct.c_void_p()
+        _check(lib.swe_pint_create(ct.byref(desc), ct.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().swe_pint_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, U0, stream=None):
+        _check(load().swe_pint_init(self.h, _ptr(U0), _stream(stream)))
+
+    def iterate(self, kmax: int, tol: float = 0.0, stream=None):
+        """Returns (iterations run, list of per-iteration convergence norms)."""
+        k = ct.c_int(0)
+        hist = (ct.c_double * max(kmax, 1))()
+        st = load().parareal_iterate(self.h, kmax, tol, ct.byref(k), hist, _stream(stream))
+        norms = [hist[i] for i in range(k.value)]
+        _check(st)
+        return k.value, norms
+
+    def solution(self, U_out, stream=None):
+        _check(load().swe_pint_solution(self.h, _ptr(U_out), _stream(stream)))

@@ -1,0 +1,90 @@
+"""Parareal on the GPU against the serial oracle (§3.1): the T31 workload of 8 slices over 12 h."""
+import numpy as np
+import pytest
+
+from oracle import pint
+from oracle.sphere import Sphere
+from oracle.swe import SWE, to_dense, to_packed
+from paper_2306_09497_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.float64).copy()).cuda()
+
+
+def _relL2(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("use_graphs", [True, False])
+def test_parareal_t31_matches_oracle_and_serial_fine(use_graphs):
+    from paper_2306_09497_gb300 import swe
+    M, nlat, nlon = 31, 48, 96
+    S = 8
+    slice_len = 12 * 3600.0 / S          # 5400 s
+    fine = swe.stepper(swe.SWE_IMEX, 120.0, 45)          # 45 x 120 s
+    coarse = swe.stepper(swe.SWE_IMEX, 1080.0, 5)        # 5 x 1080 s (1200 s nominal)
+    plan = swe.Plan(M, nlat, nlon)
+    s = Sphere(M, nlat, nlon)
+    sw = SWE(s)
+    xi, noise = inputs.initial_fields(M, 1)
+    xd = s.unpack(xi)
+    U0 = (sw.balanced_geopotential(xd) + s.unpack(noise), xd, np.zeros_like(xd))
+    # GPU: balanced init computed by the library itself
+    U0g = torch.empty(1, 3, plan.nc * 2, dtype=torch.float64, device="cuda")
+    plan.balance(_dev(xi[None]), _dev(noise[None]), U0g, 1)
+    K = 3
+    pr = swe.Parareal(plan, plan, fine, coarse, S, use_graphs=use_graphs)
+    pr.init(U0g)
+    k, norms = pr.iterate(K)
+    assert k == K and len(norms) == K
+    sol = torch.empty(S + 1, 3, plan.nc * 2, dtype=torch.float64, device="cuda")
+    pr.solution(sol)
+    got = sol.cpu().numpy().view(np.complex128).reshape(S + 1, 3, -1)
+    f_prop = lambda U: pint.serial(U, lambda X: sw.imex_step(X, 120.0), 45)
+    g_prop = lambda U: pint.serial(U, lambda X: sw.imex_step(X, 1080.0), 5)
+    hist = pint.parareal(U0, f_prop, g_prop, S, K)
+    for n in range(S + 1):
+        ref = to_packed(s, hist[K][n])
+        for f in range(3):
+            assert _relL2(got[n, f], ref[f]) < 1e-10
+    # convergence norm decreases and slices n <= K are the serial fine solution
+    assert norms[-1] < norms[0]
+    Uf = U0
+    for n in range(K + 1):
+        ref = to_packed(s, Uf)
+        for f in range(3):
+            assert _relL2(got[n, f], ref[f]) < 1e-10
+        Uf = f_prop(Uf)
+    pr.close()
+    plan.close()
+
+
+def test_parareal_finite_termination_gpu():
+    """After K = N iterations every slice equals the serial fine solution (§3.1)."""
+    from paper_2306_09497_gb300 import swe
+    M, nlat, nlon = 15, 24, 48
+    S = 4
+    plan = swe.Plan(M, nlat, nlon)
+    fine = swe.stepper(swe.SWE_IMEX, 300.0, 6)
+    coarse = swe.stepper(swe.SWE_IMEX, 1800.0, 1, 2, 1e5)
+    U0 = inputs.random_state(M, 1, seed=9)
+    pr = swe.Parareal(plan, plan, fine, coarse, S)
+    pr.init(_dev(U0))
+    pr.iterate(S)
+    sol = torch.empty(S + 1, 3, plan.nc * 2, dtype=torch.float64, device="cuda")
+    pr.solution(sol)
+    # serial fine on the GPU, slice by slice
+    cur = _dev(U0)
+    nxt = torch.empty_like(cur)
+    for n in range(S + 1):
+        a = sol[n].cpu().numpy()
+        b = cur[0].cpu().numpy()
+        assert np.linalg.norm(a - b) <= 1e-13 * np.linalg.norm(b)
+        plan.propagate(fine, cur, nxt, 1)
+        cur, nxt = nxt, cur
+    pr.close()
+    plan.close()
