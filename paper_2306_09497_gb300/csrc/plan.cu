@@ -167,9 +167,10 @@ extern "C" swe_status swe_plan_create(const swe_plan_desc* d, swe_plan_t* out) {
     p->prec = d->prec;
     p->nc = nc_state(d->M);
     p->ncx = nc_ext(d->M);
-    if (!factor_radices(d->nlon, p->rad, &p->nrad)) {
+    // the longitude FFT runs on nlon/2 complex points (two real samples each)
+    if ((d->nlon & 1) || !factor_radices(d->nlon / 2, p->rad, &p->nrad)) {
         delete p;
-        swe_set_error("swe_plan_create: nlon=%d is not of the form 2^a 3^b", d->nlon);
+        swe_set_error("swe_plan_create: nlon=%d is not of the form 2^a 3^b with a >= 1", d->nlon);
         return SWE_EINVAL;
     }
     cudaError_t e = cudaGetDevice(&p->device);

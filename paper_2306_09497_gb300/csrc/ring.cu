@@ -1,8 +1,11 @@
 // Longitude transforms on latitude rings (§2.2, "Fast Fourier"), in shared memory.
 //
-// A real DFT of length N = nlon is done as a complex Stockham FFT (radix 4/3/2)
-// of two real sequences packed as z = a + i b.  Fourier coefficients are kept
-// for m = 0..M only (M + 1 < N / 2).
+// Every real field of length N = nlon gets its own complex Stockham FFT (radix
+// 4/3/2) of length H = N/2 on z_n = x_{2n} + i x_{2n+1}: the spectra of even and
+// odd samples of ONE field are untangled with the twiddles e^{-2 pi i k / N}, so
+// fields of very different magnitude never share a transform (packing two
+// fields into one complex FFT would add the rounding of the larger one to the
+// smaller one).  Fourier coefficients are kept for m = 0..M (M < H).
 //
 //   inverse:  g(lambda_k) = Re F_0 + 2 Re sum_{m>=1} F_m e^{i m lambda_k}
 //   forward:  F_m = (w_j / N) sum_k g(lambda_k) e^{-i m lambda_k}   (Gauss weight folded in)
@@ -31,15 +34,16 @@ template <int S, typename V> __device__ __forceinline__ V cmul_si(V a) {
 }
 
 struct FFTPlan {
-    int n, nrad;
+    int n, nrad;     // transform length (H = nlon / 2) and radices
+    int tws;         // stride into the nlon-point twiddle table (2)
     int rad[32];
 };
 
 // One Stockham pass of radix R over nfft sequences of length N stored at stride `stride`.
-// S = -1 forward, +1 inverse.  tw[k] = e^{-2 pi i k / N}.
+// S = -1 forward, +1 inverse.  tw[k * tws] = e^{-2 pi i k / N}.
 template <typename T, int S>
 __device__ void fft_pass(const typename CT<T>::V* __restrict__ src, typename CT<T>::V* __restrict__ dst, int N, int R,
-                         int Ns, const typename CT<T>::V* __restrict__ tw, int nfft, int stride) {
+                         int Ns, const typename CT<T>::V* __restrict__ tw, int tws, int nfft, int stride) {
     using V = typename CT<T>::V;
     const int nb = N / R;
     const int tstep = N / (Ns * R);
@@ -54,7 +58,7 @@ __device__ void fft_pass(const typename CT<T>::V* __restrict__ src, typename CT<
         V v0 = x[j], v1 = x[j + nb];
         if (R == 2) {
             if (k) {
-                V w1 = tw[k * tstep];
+                V w1 = tw[k * tstep * tws];
                 if (S > 0) w1 = cconj(w1);
                 v1 = cmul(v1, w1);
             }
@@ -63,7 +67,7 @@ __device__ void fft_pass(const typename CT<T>::V* __restrict__ src, typename CT<
         } else if (R == 3) {
             V v2 = x[j + 2 * nb];
             if (k) {
-                V w1 = tw[k * tstep], w2 = tw[(2 * k * tstep) % N];
+                V w1 = tw[k * tstep * tws], w2 = tw[((2 * k * tstep) % N) * tws];
                 if (S > 0) {
                     w1 = cconj(w1);
                     w2 = cconj(w2);
@@ -81,7 +85,7 @@ __device__ void fft_pass(const typename CT<T>::V* __restrict__ src, typename CT<
         } else {   // R == 4
             V v2 = x[j + 2 * nb], v3 = x[j + 3 * nb];
             if (k) {
-                V w1 = tw[k * tstep], w2 = tw[(2 * k * tstep) % N], w3 = tw[(3 * k * tstep) % N];
+                V w1 = tw[k * tstep * tws], w2 = tw[((2 * k * tstep) % N) * tws], w3 = tw[((3 * k * tstep) % N) * tws];
                 if (S > 0) {
                     w1 = cconj(w1);
                     w2 = cconj(w2);
@@ -110,7 +114,7 @@ __device__ typename CT<T>::V* fft_block(typename CT<T>::V* a, typename CT<T>::V*
     int Ns = 1;
     for (int p = 0; p < fp.nrad; ++p) {
         const int R = fp.rad[p];
-        fft_pass<T, S>(src, dst, fp.n, R, Ns, tw, nfft, stride);
+        fft_pass<T, S>(src, dst, fp.n, R, Ns, tw, fp.tws, nfft, stride);
         __syncthreads();
         V* t = src;
         src = dst;
@@ -120,24 +124,34 @@ __device__ typename CT<T>::V* fft_block(typename CT<T>::V* a, typename CT<T>::V*
     return src;
 }
 
-// Hermitian synthesis input for the pair (A, B) of half spectra, m = 0..M.
+// c2r preparation, in place on one sequence z[0..H): on entry z holds the half
+// spectrum X_k (k <= M, zero above, X_0 real part only); on exit
+//   Z_k = (X_k + conj X_{H-k}) + i e^{+2 pi i k/N} (X_k - conj X_{H-k}),  k = 0..H-1,
+// whose inverse H-point DFT is z_n = x_{2n} + i x_{2n+1}.  twN[k] = e^{-2 pi i k / N}.
 template <typename V>
-__device__ __forceinline__ void put_pair(V* z, int N, int m, V A, V B) {
-    if (m == 0) {
-        z[0] = V{A.x, B.x};
-    } else {
-        z[m] = V{A.x - B.y, A.y + B.x};          // A + i B
-        z[N - m] = V{A.x + B.y, B.x - A.y};      // conj(A) + i conj(B)
+__device__ __forceinline__ void c2r_prepare(V* z, int H, int k, const V* twN) {
+    V a = z[k];
+    V b = (k == 0) ? V{0, 0} : z[H - k];
+    V e = cconj(twN[k]);                       // e^{+i theta_k}
+    V s1 = cadd(a, cconj(b)), d1 = csub(a, cconj(b));
+    z[k] = cadd(s1, cmul_si<1>(cmul(e, d1)));
+    if (k > 0 && k < H - k) {
+        V s2 = cadd(b, cconj(a)), d2 = csub(b, cconj(a));
+        V e2 = V{-twN[k].x, -twN[k].y};        // e^{+i theta_{H-k}} = -e^{-i theta_k}
+        z[H - k] = cadd(s2, cmul_si<1>(cmul(e2, d2)));
     }
 }
 
-// Split the spectrum of z = a + i b into the spectra of a and b at mode m, scaled.
+// r2c untangling: X_k = (Z_k + conj Z_{H-k})/2 - (i/2) e^{-2 pi i k/N} (Z_k - conj Z_{H-k}), scaled.
 template <typename T, typename V>
-__device__ __forceinline__ void get_pair(const V* Z, int N, int m, T scale, V& A, V& B) {
-    V zm = Z[m], zn = Z[m == 0 ? 0 : N - m];
-    A = V{(T)0.5 * (zm.x + zn.x) * scale, (T)0.5 * (zm.y - zn.y) * scale};
-    B = V{(T)0.5 * (zm.y + zn.y) * scale, (T)-0.5 * (zm.x - zn.x) * scale};
+__device__ __forceinline__ V r2c_mode(const V* Z, int H, int k, const V* twN, T scale) {
+    V zk = Z[k % H], zn = cconj(Z[(H - k) % H]);
+    V s1 = cadd(zk, zn), d1 = csub(zk, zn);
+    V t = cmul_si<-1>(cmul(twN[k], d1));       // -i e^{-i theta_k} (Z_k - conj Z_{H-k})
+    return V{(T)0.5 * (s1.x + t.x) * scale, (T)0.5 * (s1.y + t.y) * scale};
 }
+
+constexpr int RING_G = 4;   // columns per block in the plain transforms
 
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -145,27 +159,33 @@ __global__ void __launch_bounds__(256) k_ring_inv(const typename CT<T>::V* __res
                                                   int nlat, int C, FFTPlan fp, const typename CT<T>::V* __restrict__ tw) {
     using V = typename CT<T>::V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int H = fp.n;
     V* a = reinterpret_cast<V*>(smem_raw);
-    V* b = a + fp.n;
-    const int N = fp.n;
+    V* b = a + RING_G * H;
     const int j = blockIdx.y;
-    const int c0 = 2 * blockIdx.x;
-    const bool two = (c0 + 1) < C;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) a[k] = V{0, 0};
+    const int c0 = RING_G * blockIdx.x;
+    const int G = min(RING_G, C - c0);
+    for (int k = threadIdx.x; k < RING_G * H; k += blockDim.x) a[k] = V{0, 0};
     __syncthreads();
-    for (int m = threadIdx.x; m <= M; m += blockDim.x) {
-        const V* row = F + ((int64_t)m * nlat + j) * C;
-        V A = row[c0];
-        V B = two ? row[c0 + 1] : V{0, 0};
-        put_pair(a, N, m, A, B);
+    for (int t = threadIdx.x; t < G * (M + 1); t += blockDim.x) {
+        int g = t / (M + 1), m = t - g * (M + 1);
+        V x = F[((int64_t)m * nlat + j) * C + c0 + g];
+        if (m == 0) x.y = 0;
+        a[g * H + m] = x;
     }
     __syncthreads();
-    V* r = fft_block<T, +1>(a, b, fp, tw, 1, N);
-    T* g0 = grid + ((int64_t)c0 * nlat + j) * N;
-    T* g1 = grid + ((int64_t)(c0 + 1) * nlat + j) * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        g0[k] = r[k].x;
-        if (two) g1[k] = r[k].y;
+    for (int t = threadIdx.x; t < G * (H / 2 + 1); t += blockDim.x) {
+        int g = t / (H / 2 + 1), k = t - g * (H / 2 + 1);
+        c2r_prepare(a + g * H, H, k, tw);
+    }
+    __syncthreads();
+    V* r = fft_block<T, +1>(a, b, fp, tw, RING_G, H);
+    for (int t = threadIdx.x; t < G * H; t += blockDim.x) {
+        int g = t / H, n = t - g * H;
+        V z = r[g * H + n];
+        T* row = grid + ((int64_t)(c0 + g) * nlat + j) * (2 * H);
+        row[2 * n] = z.x;
+        row[2 * n + 1] = z.y;
     }
 }
 
@@ -175,24 +195,27 @@ __global__ void __launch_bounds__(256) k_ring_fwd(const T* __restrict__ grid, ty
                                                   const double* __restrict__ w) {
     using V = typename CT<T>::V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int H = fp.n;
     V* a = reinterpret_cast<V*>(smem_raw);
-    V* b = a + fp.n;
-    const int N = fp.n;
+    V* b = a + RING_G * H;
     const int j = blockIdx.y;
-    const int c0 = 2 * blockIdx.x;
-    const bool two = (c0 + 1) < C;
-    const T* g0 = grid + ((int64_t)c0 * nlat + j) * N;
-    const T* g1 = grid + ((int64_t)(c0 + 1) * nlat + j) * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) a[k] = V{g0[k], two ? g1[k] : (T)0};
+    const int c0 = RING_G * blockIdx.x;
+    const int G = min(RING_G, C - c0);
+    for (int t = threadIdx.x; t < RING_G * H; t += blockDim.x) {
+        int g = t / H, n = t - g * H;
+        V z = V{0, 0};
+        if (g < G) {
+            const T* row = grid + ((int64_t)(c0 + g) * nlat + j) * (2 * H);
+            z = V{row[2 * n], row[2 * n + 1]};
+        }
+        a[t] = z;
+    }
     __syncthreads();
-    V* r = fft_block<T, -1>(a, b, fp, tw, 1, N);
-    const T scale = (T)(w[j] / (double)N);
-    for (int m = threadIdx.x; m <= M; m += blockDim.x) {
-        V A, B;
-        get_pair<T>(r, N, m, scale, A, B);
-        V* row = F + ((int64_t)m * nlat + j) * C;
-        row[c0] = A;
-        if (two) row[c0 + 1] = B;
+    V* r = fft_block<T, -1>(a, b, fp, tw, RING_G, H);
+    const T scale = (T)(w[j] / (double)(2 * H));
+    for (int t = threadIdx.x; t < G * (M + 1); t += blockDim.x) {
+        int g = t / (M + 1), m = t - g * (M + 1);
+        F[((int64_t)m * nlat + j) * C + c0 + g] = r2c_mode<T>(r + g * H, H, m, tw, scale);
     }
 }
 
@@ -205,53 +228,53 @@ __global__ void __launch_bounds__(256) k_ring_nl(const typename CT<T>::V* __rest
                                                  const double* __restrict__ mu, const double* __restrict__ w) {
     using V = typename CT<T>::V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = fp.n;
-    V* d = reinterpret_cast<V*>(smem_raw);   // 3 data sequences
-    V* sc = d + 3 * N;                        // 3 scratch sequences
+    const int H = fp.n;
+    V* d = reinterpret_cast<V*>(smem_raw);   // 5 sequences
+    V* sc = d + 5 * H;                        // 5 scratch sequences
     const int s = blockIdx.x;
     const int j = blockIdx.y;
-    for (int k = threadIdx.x; k < 2 * N; k += blockDim.x) d[k] = V{0, 0};
+    for (int k = threadIdx.x; k < 4 * H; k += blockDim.x) d[k] = V{0, 0};
     __syncthreads();
     const int64_t C4 = 4 * (int64_t)S;
-    for (int m = threadIdx.x; m <= M; m += blockDim.x) {
-        const V* row = Fin + ((int64_t)m * nlat + j) * C4 + s;
-        V ph = row[0], xi = row[S], uu = row[2 * S], vv = row[3 * S];
-        put_pair(d, N, m, ph, xi);
-        put_pair(d + N, N, m, uu, vv);
+    for (int t = threadIdx.x; t < 4 * (M + 1); t += blockDim.x) {
+        int f = t / (M + 1), m = t - f * (M + 1);
+        V x = Fin[((int64_t)m * nlat + j) * C4 + (int64_t)f * S + s];
+        if (m == 0) x.y = 0;
+        d[f * H + m] = x;
     }
     __syncthreads();
-    V* r = fft_block<T, +1>(d, sc, fp, tw, 2, N);
+    for (int t = threadIdx.x; t < 4 * (H / 2 + 1); t += blockDim.x) {
+        int f = t / (H / 2 + 1), k = t - f * (H / 2 + 1);
+        c2r_prepare(d + f * H, H, k, tw);
+    }
+    __syncthreads();
+    V* r = fft_block<T, +1>(d, sc, fp, tw, 4, H);
     const double muj = mu[j];
     const T ic2 = (T)(1.0 / ((1.0 - muj) * (1.0 + muj)));
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        V z1 = r[k], z2 = r[N + k];
-        T ph = z1.x, xi = z1.y, U = z2.x, Vv = z2.y;
-        r[k] = V{xi * U * ic2, xi * Vv * ic2};
-        r[N + k] = V{ph * U * ic2, ph * Vv * ic2};
-        r[2 * N + k] = V{(T)0.5 * (U * U + Vv * Vv) * ic2, (T)0};
+    for (int n = threadIdx.x; n < H; n += blockDim.x) {
+        // each complex element carries two grid points (2n, 2n+1) of the same field
+        V ph = r[n], xi = r[H + n], U = r[2 * H + n], Vv = r[3 * H + n];
+        r[n] = V{xi.x * U.x * ic2, xi.y * U.y * ic2};
+        r[H + n] = V{xi.x * Vv.x * ic2, xi.y * Vv.y * ic2};
+        r[2 * H + n] = V{ph.x * U.x * ic2, ph.y * U.y * ic2};
+        r[3 * H + n] = V{ph.x * Vv.x * ic2, ph.y * Vv.y * ic2};
+        r[4 * H + n] = V{(T)0.5 * (U.x * U.x + Vv.x * Vv.x) * ic2, (T)0.5 * (U.y * U.y + Vv.y * Vv.y) * ic2};
     }
     __syncthreads();
     V* other = (r == d) ? sc : d;
-    V* q = fft_block<T, -1>(r, other, fp, tw, 3, N);
-    const T scale = (T)(w[j] / (double)N);
+    V* q = fft_block<T, -1>(r, other, fp, tw, 5, H);
+    const T scale = (T)(w[j] / (double)(2 * H));
     const int64_t C5 = 5 * (int64_t)S;
-    for (int m = threadIdx.x; m <= M; m += blockDim.x) {
-        V a1, b1, a2, b2, ke, zero;
-        get_pair<T>(q, N, m, scale, a1, b1);
-        get_pair<T>(q + N, N, m, scale, a2, b2);
-        get_pair<T>(q + 2 * N, N, m, scale, ke, zero);
-        V* row = Fout + ((int64_t)m * nlat + j) * C5 + s;
-        row[0] = a1;
-        row[S] = b1;
-        row[2 * S] = a2;
-        row[3 * S] = b2;
-        row[4 * S] = ke;
+    for (int t = threadIdx.x; t < 5 * (M + 1); t += blockDim.x) {
+        int f = t / (M + 1), m = t - f * (M + 1);
+        Fout[((int64_t)m * nlat + j) * C5 + (int64_t)f * S + s] = r2c_mode<T>(q + f * H, H, m, tw, scale);
     }
 }
 
 FFTPlan make_fft_plan(const swe_plan* p) {
     FFTPlan fp;
-    fp.n = p->nlon;
+    fp.n = p->nlon / 2;
+    fp.tws = 2;
     fp.nrad = p->nrad;
     for (int i = 0; i < p->nrad; ++i) fp.rad[i] = p->rad[i];
     return fp;
@@ -268,13 +291,13 @@ swe_status set_smem(K kernel, size_t bytes) {
 
 swe_status ring_inverse(const swe_plan* p, const void* F, void* grid, int C, cudaStream_t st) {
     FFTPlan fp = make_fft_plan(p);
-    dim3 g((C + 1) / 2, p->nlat);
+    dim3 g((C + RING_G - 1) / RING_G, p->nlat);
     if (p->prec == SWE_FP64) {
-        size_t sm = 2 * sizeof(double2) * p->nlon;
+        size_t sm = 2 * RING_G * sizeof(double2) * fp.n;
         SWE_CHECK(set_smem(k_ring_inv<double>, sm));
         k_ring_inv<double><<<g, 256, sm, st>>>((const double2*)F, (double*)grid, p->M, p->nlat, C, fp, p->tw);
     } else {
-        size_t sm = 2 * sizeof(float2) * p->nlon;
+        size_t sm = 2 * RING_G * sizeof(float2) * fp.n;
         SWE_CHECK(set_smem(k_ring_inv<float>, sm));
         k_ring_inv<float><<<g, 256, sm, st>>>((const float2*)F, (float*)grid, p->M, p->nlat, C, fp, p->twf);
     }
@@ -284,13 +307,13 @@ swe_status ring_inverse(const swe_plan* p, const void* F, void* grid, int C, cud
 
 swe_status ring_forward(const swe_plan* p, const void* grid, void* F, int C, cudaStream_t st) {
     FFTPlan fp = make_fft_plan(p);
-    dim3 g((C + 1) / 2, p->nlat);
+    dim3 g((C + RING_G - 1) / RING_G, p->nlat);
     if (p->prec == SWE_FP64) {
-        size_t sm = 2 * sizeof(double2) * p->nlon;
+        size_t sm = 2 * RING_G * sizeof(double2) * fp.n;
         SWE_CHECK(set_smem(k_ring_fwd<double>, sm));
         k_ring_fwd<double><<<g, 256, sm, st>>>((const double*)grid, (double2*)F, p->M, p->nlat, C, fp, p->tw, p->w);
     } else {
-        size_t sm = 2 * sizeof(float2) * p->nlon;
+        size_t sm = 2 * RING_G * sizeof(float2) * fp.n;
         SWE_CHECK(set_smem(k_ring_fwd<float>, sm));
         k_ring_fwd<float><<<g, 256, sm, st>>>((const float*)grid, (float2*)F, p->M, p->nlat, C, fp, p->twf, p->w);
     }
@@ -302,12 +325,12 @@ swe_status ring_nonlinear(const swe_plan* p, const void* Fin, void* Fout, int S,
     FFTPlan fp = make_fft_plan(p);
     dim3 g(S, p->nlat);
     if (p->prec == SWE_FP64) {
-        size_t sm = 6 * sizeof(double2) * p->nlon;
+        size_t sm = 10 * sizeof(double2) * fp.n;
         SWE_CHECK(set_smem(k_ring_nl<double>, sm));
         k_ring_nl<double><<<g, 256, sm, st>>>((const double2*)Fin, (double2*)Fout, p->M, p->nlat, S, fp, p->tw, p->mu,
                                               p->w);
     } else {
-        size_t sm = 6 * sizeof(float2) * p->nlon;
+        size_t sm = 10 * sizeof(float2) * fp.n;
         SWE_CHECK(set_smem(k_ring_nl<float>, sm));
         k_ring_nl<float><<<g, 256, sm, st>>>((const float2*)Fin, (float2*)Fout, p->M, p->nlat, S, fp, p->twf, p->mu,
                                              p->w);

@@ -16,7 +16,10 @@ def _dev(a):
 
 
 def _relL2(a, b):
-    return np.linalg.norm(a - b) / np.linalg.norm(b)
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return 0.0 if np.linalg.norm(a) == 0.0 else np.inf
+    return np.linalg.norm(a - b) / nb
 
 
 @pytest.mark.parametrize("use_graphs", [True, False])

