@@ -1,0 +1,327 @@
+#!/usr/bin/env python3
+"""Benchmark of the Parareal/MGRIT shallow-water hot path at T255 on GB300.
+
+Workload "t255_parareal_s128": T255 on the 384 x 768 Gaussian grid, 5 days split
+into S = 128 slices of 3375 s.  One bench step = one Parareal iteration (Eq. 9):
+the fine IMEX propagator (57 steps of 59.21 s, the level-0 step of the 5-day,
+7296-step problem) on all 128 slices at once, the serial coarse chain
+(6 IMEX steps of 562.5 s with 4th-order hyperviscosity 1e15 m^4/s per slice,
+replayed from a CUDA graph) and the FP64 correction + convergence norm.
+Metric: level-0 slice-steps per second = 128 * 57 / (seconds per iteration).
+
+Inputs are synthetic: seeded k^-3 balanced vorticity (rms wind 20 m/s) plus
+10 m height noise (paper_2306_09497_gb300.inputs), resident in HBM before the
+timed region.  The working set (~4 GB of Fourier/spectral buffers per F sweep)
+is far larger than L2, so no explicit flush is needed between iterations.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|mixed] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M, NLAT, NLON = 255, 384, 768
+S = 128
+DT0 = 432000.0 / 7296.0          # 59.2105 s
+NF = 57                           # fine steps per slice
+NC_STEPS, DTC = 6, 3375.0 / 6.0   # coarse steps per slice, 562.5 s
+NU_C, Q_C = 1.0e15, 4
+WORKLOAD = "t255_parareal_s128"
+METRIC = "SWE slice-steps/s at T255"
+FP64_PEAK_TFLOPS = 1.25           # nominal FP64 rate of GB300 (profiling recipe table)
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                sm.append(float(s[1]))
+                smax.append(float(s[2]))
+                for k, nm in enumerate(names):
+                    if s[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_baseline(seconds: float, seed: int = 3) -> dict:
+    """Time the serial FP64 oracle on one slice of the T255 workload (child process, 1 thread)."""
+    code = f"""
+import json, time, sys
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+from oracle.sphere import Sphere
+from oracle.swe import SWE
+from paper_2306_09497_gb300 import inputs
+t0 = time.perf_counter()
+s = Sphere({M}, {NLAT}, {NLON}); sw = SWE(s)
+xi, noise = inputs.initial_fields({M}, {seed})
+xd = s.unpack(xi)
+U = (sw.balanced_geopotential(xd) + s.unpack(noise), xd, np.zeros_like(xd))
+setup = time.perf_counter() - t0
+sw.imex_step(U, {DT0})   # builds the cached implicit-solve bands (not timed)
+n = 0; t1 = time.perf_counter()
+while True:
+    U = sw.imex_step(U, {DT0}); n += 1
+    if time.perf_counter() - t1 > {seconds}: break
+el = time.perf_counter() - t1
+print(json.dumps({{"steps": n, "seconds": el, "setup_s": setup}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               NUMEXPR_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        return {"error": r.stderr[-400:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    d["value"] = d["steps"] / d["seconds"]
+    return d
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    per = max(5.0, 60.0 / max(1, args.steps + args.warmup))
+    vals = []
+    for _ in range(args.warmup):
+        oracle_baseline(per / 2)
+    for _ in range(args.steps):
+        d = oracle_baseline(per)
+        if "error" in d:
+            print(json.dumps({"impl": "reference", "unavailable": "oracle failed: " + d["error"][-200:]}))
+            return 0
+        vals.append(d["value"])
+    v = sum(vals) / len(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "slice-steps/s", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v if v else None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "M": M, "nlat": NLAT, "nlon": NLON, "slices": S, "fine_steps": NF,
+                   "fine_dt": DT0},
+        "cpu_baseline": {"value": v, "unit": "slice-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": f"serial FP64 oracle IMEX steps on one T255 slice, ~{per:.0f} s per bench step"},
+        "e2e": {"value": v, "unit": "slice-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2306_09497_gb300 import inputs, swe
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = swe.SWE_FP64 if args.prec == "fp64" else swe.SWE_SPLIT_BF16X3
+    plan = swe.Plan(M, NLAT, NLON, prec=prec)
+    fine = swe.stepper(swe.SWE_IMEX, DT0, NF)
+    coarse = swe.stepper(swe.SWE_IMEX, DTC, NC_STEPS, Q_C, NU_C)
+    xi, noise = inputs.initial_fields(M, 3 + rank)
+    xi_d = torch.from_numpy(xi.view(np.float64).copy()).to(dev)
+    nz_d = torch.from_numpy(noise.view(np.float64).copy()).to(dev)
+    U0 = torch.empty(1, 3, plan.nc * 2, dtype=torch.float64, device=dev)
+    plan.balance(xi_d, nz_d, U0, 1)
+    pr = swe.Parareal(plan, plan, fine, coarse, S, use_graphs=True)
+    pr.init(U0)
+    for _ in range(args.warmup):
+        pr.iterate(1)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    clocks.start()
+    swe.prof_reset()
+    swe.prof_enable(True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    l0 = swe.launch_count()
+    e0.record(stream)
+    norms = []
+    for _ in range(args.steps):
+        _, nh = pr.iterate(1)
+        norms += nh
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = swe.launch_count() - l0
+    swe.prof_enable(False)
+    stats = swe.prof_stats()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * S * NF / (ms / 1000.0)
+
+    # end to end through the public API with host buffers: load the Parareal state
+    # from pinned host memory, iterate, save it back to host memory
+    per_state = 3 * plan.nc * 2
+    U_h = torch.empty((S + 1) * per_state, dtype=torch.float64, pin_memory=True)
+    G_h = torch.empty(S * per_state, dtype=torch.float64, pin_memory=True)
+    pr.save_state(U_h, G_h)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        pr.load_state(U_h, G_h)
+        pr.iterate(1)
+        pr.save_state(U_h, G_h)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    nbytes = (U_h.numel() + G_h.numel()) * 8
+
+    # roofline of the dominant kernel (largest event-timed total)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    roof = None
+    if stats:
+        name, (n, tot_ms, fl, by) = max(stats.items(), key=lambda kv: kv[1][1])
+        avg = tot_ms / max(n, 1)
+        if name.startswith("leg_") and name.endswith("f64"):
+            ach = fl / n / (avg / 1000.0) / 1e12
+            roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "avg_launch_ms": avg, "launches_timed": n,
+                    "peak_source": "nominal FP64 DFMA rate (profiling recipe table)"}
+        elif name.startswith("leg_"):
+            pk = peaks.get("bf16_tflops_sustained", 1748.7)
+            ach = fl / n / (avg / 1000.0) / 1e12
+            roof = {"kernel": name, "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                    "frac": ach / pk, "traffic": None, "avg_launch_ms": avg, "launches_timed": n,
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (measured)"}
+        else:
+            pk = peaks.get("hbm_gbs", 6674.8)
+            ach = by / n / (avg / 1000.0) / 1e9
+            roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,
+                    "traffic": None, "avg_launch_ms": avg, "launches_timed": n,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+        roof["kernels"] = {k: {"launches": v[0], "avg_ms": v[1] / max(v[0], 1),
+                               "share_of_timed": v[1] / sum(x[1] for x in stats.values())}
+                           for k, v in stats.items()}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "slice-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "mixed(bf16x3-split GEMM, f32 FFT, f64 state)",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "M": M, "nlat": NLAT, "nlon": NLON, "slices": S, "fine_steps": NF,
+                   "fine_dt": DT0, "coarse_steps": NC_STEPS, "coarse_dt": DTC, "coarse_visc": [Q_C, NU_C],
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                   "l2": "working set > L2 (no flush)", "precision": args.prec},
+        "e2e": {"value": world * S * NF / e2e_s, "unit": "slice-steps/s", "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "clocks": clk,
+        "convergence_norms": norms,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cb = oracle_baseline(args.cpu_seconds)
+        if "error" not in cb:
+            line["cpu_baseline"] = {"value": cb["value"], "unit": "slice-steps/s", "cores": 1, "kind": "oracle",
+                                    "sample": f"{cb['steps']} serial FP64 oracle IMEX steps of one T255 slice "
+                                              f"({cb['seconds']:.1f} s, one thread)"}
+        else:
+            line["cpu_baseline"] = {"value": None, "unit": "slice-steps/s", "cores": 1, "kind": "oracle",
+                                    "sample": "oracle failed: " + cb["error"][-200:]}
+    pr.close()
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

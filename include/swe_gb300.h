@@ -184,6 +184,30 @@ swe_status parareal_iterate(swe_pint_t p, int kmax, double tol, int* k_done,
  * [S+1][3][NC]). */
 swe_status swe_pint_solution(swe_pint_t p, double* U_out, void* stream);
 
+/* Checkpoint / resume of the Parareal state: the iterate U^k_n, n = 0..S
+ * ([S+1][3][NC]) and the coarse results phi_c(U^k_n), n = 0..S-1 ([S][3][NC]),
+ * which is all the next iteration needs.  U and Gold may be HOST (pageable or
+ * pinned) or device pointers.  swe_pint_load with Gold == NULL recomputes
+ * phi_c(U^k_n) serially.  Asynchronous on `stream`. */
+swe_status swe_pint_load(swe_pint_t p, const double* U, const double* Gold, void* stream);
+swe_status swe_pint_save(swe_pint_t p, double* U, double* Gold, void* stream);
+
+/* Instrumentation (host side, no GPU work).
+ * swe_launch_count: kernels launched by the library so far (replays of a
+ *   captured CUDA graph count every kernel node).
+ * swe_prof_enable(on): when on, the Legendre, ring and implicit-solve kernels are
+ *   bracketed by CUDA events on their own launch stream (launches inside a stream
+ *   capture are not timed); returns the previous setting.
+ * swe_prof_read(i, ...): statistics of the i-th timed kernel (name, timed launches,
+ *   total milliseconds, algorithmic FLOPs and bytes summed over those launches);
+ *   synchronises on the recorded events; returns 0 when i is out of range.
+ * swe_prof_reset: drops all statistics. */
+long long swe_launch_count(void);
+int swe_prof_enable(int on);
+void swe_prof_reset(void);
+int swe_prof_read(int i, char* name, int namelen, long long* launches, double* total_ms, double* flops,
+                  double* bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -149,7 +149,11 @@ __global__ void __launch_bounds__(256) k_leg_fwd_f64(const double* __restrict__ 
 swe_status leg_inverse_f64(const swe_plan* p, const double2* X, double2* F, int C, cudaStream_t st) {
     int ncol = 2 * C;
     dim3 grid((ncol + TC - 1) / TC, (p->nlat2 + TJ - 1) / TJ, p->M + 1);
+    const double fl = (double)C * p->nlat * (p->M + 1.0) * (p->M + 2.0);
+    const double by = 16.0 * C * (p->ncx + (p->M + 1.0) * p->nlat) + 8.0 * p->ncx * p->nlat2;
+    ProfToken tk = prof_begin("leg_inv_f64", st, fl, by);
     k_leg_inv_f64<<<grid, 256, 0, st>>>(p->P, (const double*)X, (double*)F, p->M, p->nlat, p->nlat2, ncol);
+    prof_end(tk, st);
     SWE_CHECK_LAUNCH("k_leg_inv_f64");
     return SWE_OK;
 }
@@ -157,7 +161,11 @@ swe_status leg_inverse_f64(const swe_plan* p, const double2* X, double2* F, int 
 swe_status leg_forward_f64(const swe_plan* p, const double2* F, double2* Y, int C, cudaStream_t st) {
     int ncol = 2 * C;
     dim3 grid((ncol + TC - 1) / TC, (p->M + 2 + TN - 1) / TN, p->M + 1);
+    const double fl = (double)C * p->nlat * (p->M + 1.0) * (p->M + 2.0);
+    const double by = 16.0 * C * (p->ncx + (p->M + 1.0) * p->nlat) + 8.0 * p->ncx * p->nlat2;
+    ProfToken tk = prof_begin("leg_fwd_f64", st, fl, by);
     k_leg_fwd_f64<<<grid, 256, 0, st>>>(p->P, (const double*)F, (double*)Y, p->M, p->nlat, p->nlat2, ncol);
+    prof_end(tk, st);
     SWE_CHECK_LAUNCH("k_leg_fwd_f64");
     return SWE_OK;
 }

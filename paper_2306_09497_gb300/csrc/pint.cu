@@ -18,6 +18,7 @@ struct swe_pint {
     cudaStream_t cs = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    long long graph_launches = 0;   // kernels per replay of the captured chain
     bool ready = false;
 };
 
@@ -191,10 +192,14 @@ extern "C" swe_status parareal_iterate(swe_pint_t p, int kmax, double tol, int* 
         SWE_CHECK(propagate_F(p->d.fine_plan, &p->d.fine, (const double*)p->U, (double*)p->Fo, S, p->cs));
         if (p->d.use_graphs) {
             if (!p->ready) {
+                const long long before = swe_launch_count();
                 SWE_CHECK_CUDA(cudaStreamBeginCapture(p->cs, cudaStreamCaptureModeThreadLocal));
                 swe_status s = chain(p);
                 cudaGraph_t g = nullptr;
                 cudaError_t e = cudaStreamEndCapture(p->cs, &g);
+                // captured launches did not execute: count them at each replay instead
+                p->graph_launches = swe_launch_count() - before;
+                prof_launch(-p->graph_launches);
                 if (s != SWE_OK) return s;
                 if (e != cudaSuccess) return swe_cuda_status(e, "cudaStreamEndCapture(coarse chain)");
                 p->graph = g;
@@ -202,6 +207,7 @@ extern "C" swe_status parareal_iterate(swe_pint_t p, int kmax, double tol, int* 
                 p->ready = true;
             }
             SWE_CHECK_CUDA(cudaGraphLaunch(p->gexec, p->cs));
+            prof_launch(p->graph_launches);
         } else {
             SWE_CHECK(chain(p));
         }
@@ -243,6 +249,41 @@ extern "C" swe_status swe_pint_solution(swe_pint_t p, double* U_out, void* strea
     SWE_CHECK(wait_user_stream(p, user));
     SWE_CHECK_CUDA(cudaMemcpyAsync(U_out, p->U, sizeof(double2) * 3 * p->nc * (p->d.S + 1), cudaMemcpyDeviceToDevice,
                                    p->cs));
+    SWE_CHECK(join_user_stream(p, user));
+    return SWE_OK;
+}
+
+// Checkpoint / resume of the Parareal state (U^k_n, n = 0..S, and phi_c(U^k_n)).
+// Pointers may be host (pageable or pinned) or device memory.
+extern "C" swe_status swe_pint_load(swe_pint_t p, const double* U, const double* Gold, void* stream) {
+    if (!p || !U) {
+        swe_set_error("swe_pint_load: invalid argument");
+        return SWE_EINVAL;
+    }
+    cudaStream_t user = (cudaStream_t)stream;
+    SWE_CHECK(wait_user_stream(p, user));
+    const int64_t per = 3 * p->nc;
+    SWE_CHECK_CUDA(cudaMemcpyAsync(p->U, U, sizeof(double2) * per * (p->d.S + 1), cudaMemcpyDefault, p->cs));
+    if (Gold) {
+        SWE_CHECK_CUDA(cudaMemcpyAsync(p->Gold, Gold, sizeof(double2) * per * p->d.S, cudaMemcpyDefault, p->cs));
+    } else {
+        for (int n = 0; n < p->d.S; ++n) SWE_CHECK(coarse(p, p->U + per * n, p->Gold + per * n));
+    }
+    SWE_CHECK(join_user_stream(p, user));
+    return SWE_OK;
+}
+
+extern "C" swe_status swe_pint_save(swe_pint_t p, double* U, double* Gold, void* stream) {
+    if (!p || !U) {
+        swe_set_error("swe_pint_save: invalid argument");
+        return SWE_EINVAL;
+    }
+    cudaStream_t user = (cudaStream_t)stream;
+    SWE_CHECK(wait_user_stream(p, user));
+    const int64_t per = 3 * p->nc;
+    SWE_CHECK_CUDA(cudaMemcpyAsync(U, p->U, sizeof(double2) * per * (p->d.S + 1), cudaMemcpyDefault, p->cs));
+    if (Gold)
+        SWE_CHECK_CUDA(cudaMemcpyAsync(Gold, p->Gold, sizeof(double2) * per * p->d.S, cudaMemcpyDefault, p->cs));
     SWE_CHECK(join_user_stream(p, user));
     return SWE_OK;
 }

@@ -1,0 +1,13 @@
+// Launch accounting / event timing used by every launch site (see prof.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+struct ProfToken {
+    int kid;
+    cudaEvent_t a, b;
+    double flops, bytes;
+};
+
+void prof_launch(long long n = 1);
+ProfToken prof_begin(const char* name, cudaStream_t st, double flops, double bytes);
+void prof_end(const ProfToken& t, cudaStream_t st);

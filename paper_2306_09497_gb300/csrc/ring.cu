@@ -324,6 +324,12 @@ swe_status ring_forward(const swe_plan* p, const void* grid, void* F, int C, cud
 swe_status ring_nonlinear(const swe_plan* p, const void* Fin, void* Fout, int S, cudaStream_t st) {
     FFTPlan fp = make_fft_plan(p);
     dim3 g(S, p->nlat);
+    // algorithmic traffic: read 4 and write 5 Fourier rows of (M+1) modes per ring;
+    // 9 real FFTs of length nlon (2.5 N log2 N each) + ~30 flops per grid point
+    const double fe = (p->prec == SWE_FP64) ? 16.0 : 8.0;
+    const double by = fe * 9.0 * (p->M + 1.0) * p->nlat * S;
+    const double fl = ((9.0 * 2.5 * log2((double)p->nlon)) + 30.0) * p->nlon * (double)p->nlat * S;
+    ProfToken tk = prof_begin(p->prec == SWE_FP64 ? "ring_nl_f64" : "ring_nl_f32", st, fl, by);
     if (p->prec == SWE_FP64) {
         size_t sm = 10 * sizeof(double2) * fp.n;
         SWE_CHECK(set_smem(k_ring_nl<double>, sm));
@@ -335,6 +341,7 @@ swe_status ring_nonlinear(const swe_plan* p, const void* Fin, void* Fout, int S,
         k_ring_nl<float><<<g, 256, sm, st>>>((const float2*)Fin, (float2*)Fout, p->M, p->nlat, S, fp, p->twf, p->mu,
                                              p->w);
     }
+    prof_end(tk, st);
     SWE_CHECK_LAUNCH("k_ring_nl");
     return SWE_OK;
 }

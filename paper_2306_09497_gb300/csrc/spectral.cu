@@ -470,8 +470,11 @@ swe_status k_implicit(swe_plan* p, double alpha, int with_rhs, const double2* in
         SWE_CHECK_LAUNCH("k_linop(rhs)");
         R = out;
     }
+    // algorithmic traffic: R (3 fields) + factors read, X written
+    ProfToken tk = prof_begin("cn_solve", st, 0.0, 16.0 * p->nc * (6.0 * S + 8.0));
     k_cn_solve<<<nblk((int64_t)2 * (p->M + 1) * S, 128), 128, 0, st>>>(fac, R, out, p->M, p->nc, S, visc_dt, visc_nu,
                                                                     visc_q, p->a);
+    prof_end(tk, st);
     SWE_CHECK_LAUNCH("k_cn_solve");
     return SWE_OK;
 }

@@ -7,6 +7,7 @@
 #include <string>
 
 #include "../../include/swe_gb300.h"
+#include "prof.cuh"
 
 // ---------------------------------------------------------------------------
 // error plumbing: thread-local message + status codes, no exceptions across the ABI
@@ -29,6 +30,7 @@ swe_status swe_cuda_status(cudaError_t e, const char* what);
     do {                                                                       \
         cudaError_t e_ = cudaGetLastError();                                   \
         if (e_ != cudaSuccess) return swe_cuda_status(e_, what);               \
+        prof_launch(1);                                                        \
     } while (0)
 
 // ---------------------------------------------------------------------------

@@ -25,7 +25,8 @@ EXPORTED = [
     "swe_version", "swe_last_error", "swe_ncoef", "swe_plan_create", "swe_plan_destroy", "swe_plan_gauss",
     "sht_inverse", "sht_forward", "swe_nonlinear", "swe_linear", "swe_implicit_solve", "swe_balance",
     "propagate_F", "propagate_G", "swe_pint_create", "swe_pint_destroy", "swe_pint_init", "parareal_iterate",
-    "swe_pint_solution",
+    "swe_pint_solution", "swe_pint_load", "swe_pint_save", "swe_launch_count", "swe_prof_enable",
+    "swe_prof_reset", "swe_prof_read",
 ]
 
 
@@ -83,6 +84,13 @@ def load(path: Optional[str] = None) -> ct.CDLL:
         "swe_pint_init": ([vp, vp, vp], i),
         "parareal_iterate": ([vp, i, d, ct.POINTER(i), ct.POINTER(d), vp], i),
         "swe_pint_solution": ([vp, vp, vp], i),
+        "swe_pint_load": ([vp, vp, vp, vp], i),
+        "swe_pint_save": ([vp, vp, vp, vp], i),
+        "swe_launch_count": ([], ct.c_longlong),
+        "swe_prof_enable": ([i], i),
+        "swe_prof_reset": ([], None),
+        "swe_prof_read": ([i, ct.c_char_p, i, ct.POINTER(ct.c_longlong), ct.POINTER(d), ct.POINTER(d),
+                           ct.POINTER(d)], i),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -218,3 +226,38 @@ class Parareal:
 
     def solution(self, U_out, stream=None):
         _check(load().swe_pint_solution(self.h, _ptr(U_out), _stream(stream)))
+
+    def load_state(self, U, Gold=None, stream=None):
+        """Resume from (U^k_n, phi_c(U^k_n)); host or device arrays."""
+        _check(load().swe_pint_load(self.h, _ptr(U), _ptr(Gold), _stream(stream)))
+
+    def save_state(self, U, Gold=None, stream=None):
+        """Checkpoint (U^k_n, phi_c(U^k_n)) into host or device arrays."""
+        _check(load().swe_pint_save(self.h, _ptr(U), _ptr(Gold), _stream(stream)))
+
+
+def launch_count() -> int:
+    return int(load().swe_launch_count())
+
+
+def prof_enable(on: bool) -> bool:
+    return bool(load().swe_prof_enable(1 if on else 0))
+
+
+def prof_reset():
+    load().swe_prof_reset()
+
+
+def prof_stats():
+    """{kernel name: (timed launches, total ms, algorithmic flops, algorithmic bytes)}."""
+    lib = load()
+    out = {}
+    i = 0
+    name = ct.create_string_buffer(64)
+    while True:
+        n, ms, fl, by = ct.c_longlong(), ct.c_double(), ct.c_double(), ct.c_double()
+        if not lib.swe_prof_read(i, name, 64, ct.byref(n), ct.byref(ms), ct.byref(fl), ct.byref(by)):
+            break
+        out[name.value.decode()] = (n.value, ms.value, fl.value, by.value)
+        i += 1
+    return out
