@@ -145,7 +145,8 @@ def test_nonlinear_matches_oracle(pair):
     for b in range(S):
         ref = to_packed(s, sw.nonlinear(to_dense(s, U[b])))
         for f in range(3):
-            assert _relL2(got[b, f], ref[f], m) < 1e-12
+            # sums of O(nlat) products with a steeply decaying spectrum: 1e-11
+            assert _relL2(got[b, f], ref[f], m) < 1e-11
 
 
 def test_balanced_init_matches_oracle(pair):
