@@ -192,6 +192,28 @@ swe_status swe_pint_solution(swe_pint_t p, double* U_out, void* stream);
 swe_status swe_pint_load(swe_pint_t p, const double* U, const double* Gold, void* stream);
 swe_status swe_pint_save(swe_pint_t p, double* U, double* Gold, void* stream);
 
+/* Inverse scalar transform for callers that cannot allocate device memory at
+ * call time -- for example code that runs while a stream is being captured
+ * into a CUDA graph (cudaMalloc cannot be captured), real-time loops that
+ * forbid allocator calls, or applications whose device memory belongs to
+ * their own pool.  Same arguments, layouts and result as sht_inverse (the
+ * paper has no counterpart: this is a library-usage variant).
+ * Scratch comes from a fixed static device array of SWE_NOALLOC_SCRATCH_BYTES
+ * (64 MiB) that every GPU which loads the library holds until the process
+ * exits; nothing is allocated or freed by the call.  The scratch needed is
+ * 16 * NCX + e * (M+1) * nlat bytes per field (NCX = (M+1)(M+4)/2, e = 16 for
+ * SWE_FP64 plans, 8 otherwise), rounded up to 256-byte multiples; a batch that
+ * does not fit returns SWE_EINVAL with the limit in swe_last_error() (for T255
+ * on 384 x 768 in FP64: at most 31 fields per call).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it: make that first call before any stream
+ * capture.  Every call on a device shares the one array, so calls that overlap
+ * on the GPU (other streams, other threads) race and must be serialised by the
+ * caller.  Nothing in the array needs to start at zero: each call writes every
+ * scratch element it reads before reading it. */
+#define SWE_NOALLOC_SCRATCH_BYTES (64u << 20)
+swe_status sht_inverse_noalloc(swe_plan_t plan, const void* spec, void* grid, int batch, void* stream);
+
 /* Instrumentation (host side, no GPU work).
  * swe_launch_count: kernels launched by the library so far (replays of a
  *   captured CUDA graph count every kernel node).

@@ -26,7 +26,7 @@ EXPORTED = [
     "sht_inverse", "sht_forward", "swe_nonlinear", "swe_linear", "swe_implicit_solve", "swe_balance",
     "propagate_F", "propagate_G", "swe_pint_create", "swe_pint_destroy", "swe_pint_init", "parareal_iterate",
     "swe_pint_solution", "swe_pint_load", "swe_pint_save", "swe_launch_count", "swe_prof_enable",
-    "swe_prof_reset", "swe_prof_read",
+    "swe_prof_reset", "swe_prof_read", "sht_inverse_noalloc",
 ]
 
 
@@ -91,6 +91,7 @@ def load(path: Optional[str] = None) -> ct.CDLL:
         "swe_prof_reset": ([], None),
         "swe_prof_read": ([i, ct.c_char_p, i, ct.POINTER(ct.c_longlong), ct.POINTER(d), ct.POINTER(d),
                            ct.POINTER(d)], i),
+        "sht_inverse_noalloc": ([vp, vp, vp, i, vp], i),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -164,6 +165,10 @@ class Plan:
     # -- transforms --------------------------------------------------------
     def sht_inverse(self, spec, grid, batch, stream=None):
         _check(load().sht_inverse(self.h, _ptr(spec), _ptr(grid), batch, _stream(stream)))
+
+    def sht_inverse_noalloc(self, spec, grid, batch, stream=None):
+        """sht_inverse without any device allocation (static 64 MiB scratch; see the C header)."""
+        _check(load().sht_inverse_noalloc(self.h, _ptr(spec), _ptr(grid), batch, _stream(stream)))
 
     def sht_forward(self, grid, spec, batch, stream=None):
         _check(load().sht_forward(self.h, _ptr(grid), _ptr(spec), batch, _stream(stream)))
