@@ -1,0 +1,665 @@
+// Split-precision Legendre contraction on the 5th-generation tensor cores (tcgen05).
+//
+// The contraction of §2.2 ("Fast Legendre") per zonal wavenumber m is a small
+// dense GEMM; all slices and fields are batched into its column dimension.  Both
+// directions are written with the data columns as the MMA M dimension (128 per CTA):
+//
+//   inverse:  D_par[c, j] = sum_k X[(m, n = m+par+2k), c] P_n^m(mu_j)      (j: northern latitudes)
+//             F(mu_j)  = D_0 + D_1,  F(-mu_j) = D_0 - D_1                     (equatorial symmetry)
+//   forward:  D_par[c, k] = sum_j G_par[j, c] P_{m+par+2k}^m(mu_j),
+//             G_0 = F(mu_j) + F(-mu_j),  G_1 = F(mu_j) - F(-mu_j)
+//
+// Precision: every operand value v (FP64 / FP32) is split into three bf16 terms
+// v = v0 + v1 + v2 (24 significant bits), and each product is formed from the six
+// largest partial products a0 b0 + a0 b1 + a1 b0 + a0 b2 + a2 b0 + a1 b1 with FP32
+// accumulation in tensor memory (relative error ~1e-8 per contraction, below the
+// FP32 rounding of the Fourier data this path carries).
+//
+// Data movement: the Legendre operand (B) is pre-split and pre-tiled on the device
+// into the canonical no-swizzle K-major core-matrix layout and streamed into shared
+// memory by the bulk-copy engine (cp.async.bulk + mbarrier transaction counts);
+// the data operand (A) is loaded coalesced by the CTA's 128 threads (one per
+// column), split in registers and stored in the same layout.  One elected thread
+// issues tcgen05.mma (kind::f16, bf16 x bf16 -> f32, M = 128, K = 16) into two
+// TMEM accumulators (one per parity); a two-stage ring overlaps the operand
+// loads of chunk q+1 with the MMAs of chunk q; the epilogue reads TMEM with
+// tcgen05.ld and writes coalesced rows.  Every mbarrier wait is bounded: on
+// timeout the kernel sets an error flag, stops issuing work, releases its tensor
+// memory and returns.
+#include <cuda_bf16.h>
+
+#include <vector>
+
+#include "swe_internal.cuh"
+
+namespace {
+
+constexpr int BM = 128;          // data columns per CTA (MMA M)
+constexpr int KC = 16;           // K per chunk (one MMA)
+constexpr int NPLANE = 3;        // bf16 split terms
+constexpr int NTERMS = 6;        // partial products kept
+constexpr uint32_t TMEM_COLS = 512;
+constexpr unsigned long long WAIT_LIMIT = 1ull << 28;   // ~seconds of polling
+
+__constant__ int c_terms[NTERMS][2] = {{0, 0}, {0, 1}, {1, 0}, {0, 2}, {2, 0}, {1, 1}};
+
+// ----------------------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// bounded wait for completion of phase `parity`; returns false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (unsigned long long it = 0; it < WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n"
+            " .reg .pred p;\n"
+            " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n"
+            "}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor, no swizzle, K-major core matrices (8 rows x 16 bytes)
+__device__ __forceinline__ uint64_t smem_desc(const void* base, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_u32(base) & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;   // descriptor version for tcgen05
+    return d;                 // base offset 0, layout type 0 (no swizzle)
+}
+
+// instruction descriptor: kind::f16 with bf16 A/B, f32 accumulate, both K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t make_idesc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ----------------------------------------------------------------------------- operand helpers
+// three-term bf16 split of a value already rounded to FP32 (24 significant bits)
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
+    a = __float2bfloat16_rn(x);
+    float r = x - __bfloat162float(a);
+    b = __float2bfloat16_rn(r);
+    r = r - __bfloat162float(b);
+    c = __float2bfloat16_rn(r);
+}
+
+// byte offset of element (row, k) in a K-major no-swizzle tile with 16 K-elements:
+// core matrices of 8 rows x 8 elements; K-adjacent core matrices 128 B apart (LBO),
+// row-group-adjacent ones 256 B apart (SBO)
+__host__ __device__ __forceinline__ uint32_t tile_off(int row, int k) {
+    return (uint32_t)((row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// Writes one thread's 16 values (its row of a 16-K chunk) as three bf16 planes.
+__device__ __forceinline__ void store_row_planes(unsigned char* plane0, uint32_t plane_bytes, int row, const float* v) {
+    __nv_bfloat16 h[NPLANE][KC];
+#pragma unroll
+    for (int k = 0; k < KC; ++k) split3(v[k], h[0][k], h[1][k], h[2][k]);
+#pragma unroll
+    for (int pl = 0; pl < NPLANE; ++pl) {
+        unsigned char* base = plane0 + pl * plane_bytes;
+        uint4 lo, hi;
+        memcpy(&lo, &h[pl][0], 16);
+        memcpy(&hi, &h[pl][8], 16);
+        *reinterpret_cast<uint4*>(base + tile_off(row, 0)) = lo;
+        *reinterpret_cast<uint4*>(base + tile_off(row, 8)) = hi;
+    }
+}
+
+struct TCShape {
+    int M, nlat, nlat2, ncol;    // ncol: real data columns
+    int nt;                      // N tile (multiple of 16, <= 256)
+};
+
+// ----------------------------------------------------------------------------- inverse
+// grid: (ceil(ncol/128), M+1, n-tiles over j).  Table Binv: for each m, chunk q, parity,
+// N-tile: a [nt x 16] bf16 tile x 3 planes, contiguous (offsets from inv_off[m]).
+__global__ void __launch_bounds__(128, 1) k_leg_inv_tc(const double* __restrict__ X, float* __restrict__ F,
+                                                       const unsigned char* __restrict__ Binv,
+                                                       const long long* __restrict__ inv_off,
+                                                       const int* __restrict__ inv_nq, TCShape sh, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int nt = sh.nt;
+    const uint32_t a_plane = BM * KC * 2;                 // 4 KB
+    const uint32_t b_plane = (uint32_t)nt * KC * 2;
+    const uint32_t a_stage = 2 * NPLANE * a_plane;        // two parities
+    const uint32_t b_stage = 2 * NPLANE * b_plane;
+    unsigned char* sA[2] = {smem, smem + a_stage};
+    unsigned char* sB[2] = {smem + 2 * a_stage, smem + 2 * a_stage + b_stage};
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * a_stage + 2 * b_stage);
+    uint64_t* bar_tma = bars;          // [2]
+    uint64_t* bar_mma = bars + 2;      // [2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int M = sh.M;
+    const int m = M - (int)blockIdx.y;
+    const int c0 = blockIdx.x * BM;
+    const int jt0 = blockIdx.z * nt;
+    const int nq = inv_nq[m];
+    const int Kx = M + 2 - m;                              // extended rows of this m
+    const int64_t xrow0 = ex_off(m, M);
+
+    if (tid == 0) {
+        mbar_init(&bar_tma[0], 1);
+        mbar_init(&bar_tma[1], 1);
+        mbar_init(&bar_mma[0], 1);
+        mbar_init(&bar_mma[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t idesc = make_idesc(nt);
+    const unsigned char* Bm = Binv + inv_off[m] + (int64_t)blockIdx.z * 2 * NPLANE * b_plane;
+    const int64_t bchunk = (int64_t)gridDim.z * 2 * NPLANE * b_plane;   // bytes per chunk over all n-tiles
+    bool ok = true;
+    const int c = c0 + tid;
+    for (int q = 0; q < nq && ok; ++q) {
+        const int s = q & 1;
+        if (q >= 2) {
+            // stage s is free once the MMAs of chunk q-2 completed (one thread waits, all follow)
+            if (tid == 0) ok = mbar_wait(&bar_mma[s], ((q - 2) >> 1) & 1);
+            ok = __syncthreads_and(ok);
+            if (!ok) break;
+        }
+        if (tid == 0) {
+            mbar_expect_tx(&bar_tma[s], b_stage);
+            bulk_g2s(sB[s], Bm + (int64_t)q * bchunk, b_stage, &bar_tma[s]);
+        }
+        // data operand: rows n = m + par + 2k, k in [16q, 16q+16)
+#pragma unroll
+        for (int par = 0; par < 2; ++par) {
+            float v[KC];
+#pragma unroll
+            for (int kk = 0; kk < KC; ++kk) {
+                const int rr = par + 2 * (KC * q + kk);
+                v[kk] = (rr < Kx && c < sh.ncol) ? (float)X[(xrow0 + rr) * sh.ncol + c] : 0.f;
+            }
+            store_row_planes(sA[s] + par * NPLANE * a_plane, a_plane, tid, v);
+        }
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            ok = mbar_wait(&bar_tma[s], (q >> 1) & 1);
+            if (ok) {
+                tc_fence_after();
+#pragma unroll
+                for (int par = 0; par < 2; ++par) {
+                    for (int t = 0; t < NTERMS; ++t) {
+                        const unsigned char* a = sA[s] + par * NPLANE * a_plane + c_terms[t][0] * a_plane;
+                        const unsigned char* b = sB[s] + par * NPLANE * b_plane + c_terms[t][1] * b_plane;
+                        mma_bf16(tmem + par * nt, smem_desc(a, 128, 256), smem_desc(b, 128, 256), idesc,
+                                 (q > 0 || t > 0) ? 1u : 0u);
+                    }
+                }
+                mma_commit(&bar_mma[s]);
+            }
+        }
+        // broadcast a timeout seen by the issuing thread
+        ok = __syncthreads_and(ok);
+    }
+    if (tid == 0) {
+        if (ok && nq > 0) {
+            ok = mbar_wait(&bar_mma[(nq - 1) & 1], ((nq - 1) >> 1) & 1);
+        } else if (!ok) {
+            // bounded drain of this CTA's own copies and MMAs still in flight
+            for (int s2 = 0; s2 < 2; ++s2) {
+                mbar_wait(&bar_tma[s2], 0);
+                mbar_wait(&bar_mma[s2], 0);
+            }
+        }
+    }
+    ok = __syncthreads_and(ok);
+    tc_fence_after();
+    if (ok) {
+        // epilogue: warp w owns TMEM lanes (= data columns) 32w..32w+31
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        for (int j0 = 0; j0 < nt; j0 += 32) {
+            float e[32], o[32];
+            tmem_ld32(tmem + lane_base + (uint32_t)j0, e);
+            tmem_ld32(tmem + lane_base + (uint32_t)(nt + j0), o);
+            if (c < sh.ncol) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int j = jt0 + j0 + i;
+                    if (j < sh.nlat2) {
+                        F[((int64_t)m * sh.nlat + j) * sh.ncol + c] = e[i] + o[i];
+                        F[((int64_t)m * sh.nlat + (sh.nlat - 1 - j)) * sh.ncol + c] = e[i] - o[i];
+                    }
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicOr(err, 2);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// ----------------------------------------------------------------------------- forward
+// grid: (ceil(ncol/128), M+1, n-tiles over k).  Table Bfwd: for each m, j-chunk q, parity,
+// N-tile: a [nt x 16] tile x 3 planes (rows k = degree index within the parity).
+__global__ void __launch_bounds__(128, 1) k_leg_fwd_tc(const float* __restrict__ F, double* __restrict__ Y,
+                                                       const unsigned char* __restrict__ Bfwd,
+                                                       const long long* __restrict__ fwd_off,
+                                                       const int* __restrict__ fwd_ntiles, TCShape sh, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int nt = sh.nt;
+    const uint32_t a_plane = BM * KC * 2;
+    const uint32_t b_plane = (uint32_t)nt * KC * 2;
+    const uint32_t a_stage = 2 * NPLANE * a_plane;
+    const uint32_t b_stage = 2 * NPLANE * b_plane;
+    unsigned char* sA[2] = {smem, smem + a_stage};
+    unsigned char* sB[2] = {smem + 2 * a_stage, smem + 2 * a_stage + b_stage};
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * a_stage + 2 * b_stage);
+    uint64_t* bar_tma = bars;
+    uint64_t* bar_mma = bars + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int M = sh.M;
+    const int m = M - (int)blockIdx.y;
+    if ((int)blockIdx.z >= fwd_ntiles[m]) return;          // uniform for the CTA: before any barrier
+    const int c0 = blockIdx.x * BM;
+    const int kt0 = blockIdx.z * nt;
+    const int nq = (sh.nlat2 + KC - 1) / KC;
+    const int Kx = M + 2 - m;
+    const int64_t yrow0 = ex_off(m, M);
+
+    if (tid == 0) {
+        mbar_init(&bar_tma[0], 1);
+        mbar_init(&bar_tma[1], 1);
+        mbar_init(&bar_mma[0], 1);
+        mbar_init(&bar_mma[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t idesc = make_idesc(nt);
+    const unsigned char* Bm = Bfwd + fwd_off[m] + (int64_t)blockIdx.z * 2 * NPLANE * b_plane;
+    const int64_t bchunk = (int64_t)fwd_ntiles[m] * 2 * NPLANE * b_plane;
+    bool ok = true;
+    const int c = c0 + tid;
+    const float* Fm = F + (int64_t)m * sh.nlat * sh.ncol;
+    for (int q = 0; q < nq && ok; ++q) {
+        const int s = q & 1;
+        if (q >= 2) {
+            // stage s is free once the MMAs of chunk q-2 completed (one thread waits, all follow)
+            if (tid == 0) ok = mbar_wait(&bar_mma[s], ((q - 2) >> 1) & 1);
+            ok = __syncthreads_and(ok);
+            if (!ok) break;
+        }
+        if (tid == 0) {
+            mbar_expect_tx(&bar_tma[s], b_stage);
+            bulk_g2s(sB[s], Bm + (int64_t)q * bchunk, b_stage, &bar_tma[s]);
+        }
+        float vs[KC], va[KC];
+#pragma unroll
+        for (int jj = 0; jj < KC; ++jj) {
+            const int j = KC * q + jj;
+            float fn = 0.f, fs = 0.f;
+            if (j < sh.nlat2 && c < sh.ncol) {
+                fn = Fm[(int64_t)j * sh.ncol + c];
+                fs = Fm[(int64_t)(sh.nlat - 1 - j) * sh.ncol + c];
+            }
+            vs[jj] = fn + fs;
+            va[jj] = fn - fs;
+        }
+        store_row_planes(sA[s], a_plane, tid, vs);
+        store_row_planes(sA[s] + NPLANE * a_plane, a_plane, tid, va);
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            ok = mbar_wait(&bar_tma[s], (q >> 1) & 1);
+            if (ok) {
+                tc_fence_after();
+#pragma unroll
+                for (int par = 0; par < 2; ++par) {
+                    for (int t = 0; t < NTERMS; ++t) {
+                        const unsigned char* a = sA[s] + par * NPLANE * a_plane + c_terms[t][0] * a_plane;
+                        const unsigned char* b = sB[s] + par * NPLANE * b_plane + c_terms[t][1] * b_plane;
+                        mma_bf16(tmem + par * nt, smem_desc(a, 128, 256), smem_desc(b, 128, 256), idesc,
+                                 (q > 0 || t > 0) ? 1u : 0u);
+                    }
+                }
+                mma_commit(&bar_mma[s]);
+            }
+        }
+        ok = __syncthreads_and(ok);
+    }
+    if (tid == 0) {
+        if (ok && nq > 0) {
+            ok = mbar_wait(&bar_mma[(nq - 1) & 1], ((nq - 1) >> 1) & 1);
+        } else if (!ok) {
+            // bounded drain of this CTA's own copies and MMAs still in flight
+            for (int s2 = 0; s2 < 2; ++s2) {
+                mbar_wait(&bar_tma[s2], 0);
+                mbar_wait(&bar_mma[s2], 0);
+            }
+        }
+    }
+    ok = __syncthreads_and(ok);
+    tc_fence_after();
+    if (ok) {
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        for (int k0 = 0; k0 < nt; k0 += 32) {
+            float d0[32], d1[32];
+            tmem_ld32(tmem + lane_base + (uint32_t)k0, d0);
+            tmem_ld32(tmem + lane_base + (uint32_t)(nt + k0), d1);
+            if (c < sh.ncol) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int k = kt0 + k0 + i;
+                    const int r0 = 2 * k, r1 = 2 * k + 1;        // extended-row offsets of parities 0 / 1
+                    if (r0 < Kx) Y[(yrow0 + r0) * sh.ncol + c] = (double)d0[i];
+                    if (r1 < Kx) Y[(yrow0 + r1) * sh.ncol + c] = (double)d1[i];
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicOr(err, 2);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// ----------------------------------------------------------------------------- table builders
+// Inverse table: element (j, kk) of tile (m, q, tile z, par, plane) = P_{m+par+2(16q+kk)}(mu_{16... j})
+__global__ void k_build_inv_table(const double* __restrict__ P, unsigned char* __restrict__ T,
+                                  const long long* __restrict__ inv_off, const int* __restrict__ inv_nq, int M,
+                                  int nlat2, int nt, int ntiles) {
+    const int m = blockIdx.y;
+    const int nq = inv_nq[m];
+    const uint32_t b_plane = (uint32_t)nt * KC * 2;
+    const int64_t total = (int64_t)nq * ntiles * 2 * nt * KC;
+    const int Kx = M + 2 - m;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        int kk = (int)(t % KC);
+        int64_t r = t / KC;
+        int row = (int)(r % nt);
+        r /= nt;
+        int par = (int)(r % 2);
+        r /= 2;
+        int z = (int)(r % ntiles);
+        int q = (int)(r / ntiles);
+        int j = z * nt + row;
+        int rr = par + 2 * (KC * q + kk);
+        double v = (j < nlat2 && rr < Kx) ? P[(ex_off(m, M) + rr) * nlat2 + j] : 0.0;
+        __nv_bfloat16 h0, h1, h2;
+        split3((float)v, h0, h1, h2);
+        unsigned char* tile = T + inv_off[m] + (((int64_t)q * ntiles + z) * 2 + par) * NPLANE * b_plane;
+        uint32_t off = tile_off(row, kk);
+        *reinterpret_cast<__nv_bfloat16*>(tile + off) = h0;
+        *reinterpret_cast<__nv_bfloat16*>(tile + b_plane + off) = h1;
+        *reinterpret_cast<__nv_bfloat16*>(tile + 2 * b_plane + off) = h2;
+    }
+}
+
+// Forward table: element (k, jj) of tile (m, q, tile z, par, plane) = P_{m+par+2k}(mu_{16q+jj}), k = z*nt + row
+__global__ void k_build_fwd_table(const double* __restrict__ P, unsigned char* __restrict__ T,
+                                  const long long* __restrict__ fwd_off, const int* __restrict__ fwd_ntiles, int M,
+                                  int nlat2, int nt) {
+    const int m = blockIdx.y;
+    const int nz = fwd_ntiles[m];
+    const int nq = (nlat2 + KC - 1) / KC;
+    const uint32_t b_plane = (uint32_t)nt * KC * 2;
+    const int64_t total = (int64_t)nq * nz * 2 * nt * KC;
+    const int Kx = M + 2 - m;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        int jj = (int)(t % KC);
+        int64_t r = t / KC;
+        int row = (int)(r % nt);
+        r /= nt;
+        int par = (int)(r % 2);
+        r /= 2;
+        int z = (int)(r % nz);
+        int q = (int)(r / nz);
+        int k = z * nt + row;
+        int j = KC * q + jj;
+        int rr = par + 2 * k;
+        double v = (j < nlat2 && rr < Kx) ? P[(ex_off(m, M) + rr) * nlat2 + j] : 0.0;
+        __nv_bfloat16 h0, h1, h2;
+        split3((float)v, h0, h1, h2);
+        unsigned char* tile = T + fwd_off[m] + (((int64_t)q * nz + z) * 2 + par) * NPLANE * b_plane;
+        uint32_t off = tile_off(row, jj);
+        *reinterpret_cast<__nv_bfloat16*>(tile + off) = h0;
+        *reinterpret_cast<__nv_bfloat16*>(tile + b_plane + off) = h1;
+        *reinterpret_cast<__nv_bfloat16*>(tile + 2 * b_plane + off) = h2;
+    }
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------- host side
+struct SplitTables {
+    int nt_inv, ntiles_inv, nt_fwd;
+    unsigned char* inv = nullptr;
+    unsigned char* fwd = nullptr;
+    long long* inv_off = nullptr;
+    int* inv_nq = nullptr;
+    long long* fwd_off = nullptr;
+    int* fwd_ntiles = nullptr;
+    int* err = nullptr;
+    size_t smem_inv = 0, smem_fwd = 0;
+};
+
+static int round16(int x) { return (x + 15) / 16 * 16; }
+
+static size_t tc_smem(int nt) {
+    size_t a_stage = 2 * NPLANE * BM * KC * 2, b_stage = 2 * NPLANE * (size_t)nt * KC * 2;
+    return 2 * a_stage + 2 * b_stage + 64;
+}
+
+swe_status split_tables_build(swe_plan* p) {
+    if (p->Pbf) return SWE_OK;
+    SplitTables* t = new SplitTables();
+    const int M = p->M;
+    // inverse: N tiles over the northern latitudes, at most 256 (here: equal tiles)
+    int ntiles = (p->nlat2 + 255) / 256;
+    t->ntiles_inv = ntiles;
+    t->nt_inv = round16((p->nlat2 + ntiles - 1) / ntiles);
+    if (t->nt_inv % 32) t->nt_inv = (t->nt_inv + 31) / 32 * 32;   // epilogue reads 32 columns at a time
+    // forward: N tiles over the degree index within a parity; K_par <= (M + 2 - m + 1) / 2
+    t->nt_fwd = 0;
+    std::vector<long long> ioff(M + 1), foff(M + 1);
+    std::vector<int> inq(M + 1), fnt(M + 1);
+    const int nqf = (p->nlat2 + KC - 1) / KC;
+    int kmax0 = (M + 2 + 1) / 2;                                   // K_par for m = 0
+    int nzf = (kmax0 + 255) / 256;
+    t->nt_fwd = round16((kmax0 + nzf - 1) / nzf);
+    if (t->nt_fwd % 32) t->nt_fwd = (t->nt_fwd + 31) / 32 * 32;
+    long long oi = 0, of = 0;
+    const long long binv = 2LL * NPLANE * t->nt_inv * KC * 2, bfwd = 2LL * NPLANE * t->nt_fwd * KC * 2;
+    for (int m = 0; m <= M; ++m) {
+        int Kx = M + 2 - m;                 // extended rows
+        int Kpar = (Kx + 1) / 2;            // rows in the larger parity
+        inq[m] = (Kpar + KC - 1) / KC;
+        ioff[m] = oi;
+        oi += (long long)inq[m] * ntiles * binv;
+        fnt[m] = (Kpar + t->nt_fwd - 1) / t->nt_fwd;
+        foff[m] = of;
+        of += (long long)nqf * fnt[m] * bfwd;
+    }
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&t->inv, oi);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&t->fwd, of);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&t->inv_off, sizeof(long long) * (M + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&t->inv_nq, sizeof(int) * (M + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&t->fwd_off, sizeof(long long) * (M + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&t->fwd_ntiles, sizeof(int) * (M + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&t->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(t->inv_off, ioff.data(), sizeof(long long) * (M + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(t->inv_nq, inq.data(), sizeof(int) * (M + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(t->fwd_off, foff.data(), sizeof(long long) * (M + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(t->fwd_ntiles, fnt.data(), sizeof(int) * (M + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(t->err, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaFree(t->inv);
+        cudaFree(t->fwd);
+        cudaFree(t->inv_off);
+        cudaFree(t->inv_nq);
+        cudaFree(t->fwd_off);
+        cudaFree(t->fwd_ntiles);
+        cudaFree(t->err);
+        delete t;
+        return swe_cuda_status(e, "split tables");
+    }
+    k_build_inv_table<<<dim3(256, M + 1), 256>>>(p->P, t->inv, t->inv_off, t->inv_nq, M, p->nlat2, t->nt_inv,
+                                                  ntiles);
+    k_build_fwd_table<<<dim3(256, M + 1), 256>>>(p->P, t->fwd, t->fwd_off, t->fwd_ntiles, M, p->nlat2, t->nt_fwd);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    t->smem_inv = tc_smem(t->nt_inv);
+    t->smem_fwd = tc_smem(t->nt_fwd);
+    // at least ~116 KB of shared memory so that a single CTA (holding all 512 TMEM columns) runs per SM
+    const size_t one_per_sm = 116 * 1024;
+    if (t->smem_inv < one_per_sm) t->smem_inv = one_per_sm;
+    if (t->smem_fwd < one_per_sm) t->smem_fwd = one_per_sm;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_leg_inv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_inv);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_leg_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_fwd);
+    p->Pbf = t;
+    if (e != cudaSuccess) return swe_cuda_status(e, "split table kernels");
+    return SWE_OK;
+}
+
+void split_tables_free(swe_plan* p) {
+    SplitTables* t = (SplitTables*)p->Pbf;
+    if (!t) return;
+    cudaFree(t->inv);
+    cudaFree(t->fwd);
+    cudaFree(t->inv_off);
+    cudaFree(t->inv_nq);
+    cudaFree(t->fwd_off);
+    cudaFree(t->fwd_ntiles);
+    cudaFree(t->err);
+    delete t;
+    p->Pbf = nullptr;
+}
+
+swe_status leg_inverse_split(const swe_plan* p, const double2* X, float2* F, int C, cudaStream_t st) {
+    const SplitTables* t = (const SplitTables*)p->Pbf;
+    if (!t) {
+        swe_set_error("split-precision tables missing");
+        return SWE_EINVAL;
+    }
+    TCShape sh{p->M, p->nlat, p->nlat2, 2 * C, t->nt_inv};
+    dim3 grid((sh.ncol + BM - 1) / BM, p->M + 1, t->ntiles_inv);
+    const double fl = (double)C * p->nlat * (p->M + 1.0) * (p->M + 2.0);
+    const double by = 16.0 * C * p->ncx + 8.0 * C * (p->M + 1.0) * p->nlat;
+    ProfToken tk = prof_begin("leg_inv_tc", st, fl, by);
+    k_leg_inv_tc<<<grid, BM, t->smem_inv, st>>>((const double*)X, (float*)F, t->inv, t->inv_off, t->inv_nq, sh,
+                                                t->err);
+    prof_end(tk, st);
+    SWE_CHECK_LAUNCH("k_leg_inv_tc");
+    return SWE_OK;
+}
+
+swe_status leg_forward_split(const swe_plan* p, const float2* F, double2* Y, int C, cudaStream_t st) {
+    const SplitTables* t = (const SplitTables*)p->Pbf;
+    if (!t) {
+        swe_set_error("split-precision tables missing");
+        return SWE_EINVAL;
+    }
+    TCShape sh{p->M, p->nlat, p->nlat2, 2 * C, t->nt_fwd};
+    const int kmax0 = (p->M + 2 + 1) / 2;
+    dim3 grid((sh.ncol + BM - 1) / BM, p->M + 1, (kmax0 + t->nt_fwd - 1) / t->nt_fwd);
+    const double fl = (double)C * p->nlat * (p->M + 1.0) * (p->M + 2.0);
+    const double by = 8.0 * C * (p->M + 1.0) * p->nlat + 16.0 * C * p->ncx;
+    ProfToken tk = prof_begin("leg_fwd_tc", st, fl, by);
+    k_leg_fwd_tc<<<grid, BM, t->smem_fwd, st>>>((const float*)F, (double*)Y, t->fwd, t->fwd_off, t->fwd_ntiles, sh,
+                                                t->err);
+    prof_end(tk, st);
+    SWE_CHECK_LAUNCH("k_leg_fwd_tc");
+    return SWE_OK;
+}
+
+// non-zero if a tensor-core kernel gave up on a bounded wait since the last call
+int split_tables_error(const swe_plan* p, cudaStream_t st) {
+    const SplitTables* t = (const SplitTables*)p->Pbf;
+    if (!t) return 0;
+    int h = 0;
+    cudaMemcpyAsync(&h, t->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    return h;
+}

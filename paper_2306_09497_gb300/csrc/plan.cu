@@ -209,6 +209,13 @@ extern "C" swe_status swe_plan_create(const swe_plan_desc* d, swe_plan_t* out) {
         swe_plan_destroy(p);
         return swe_cuda_status(e, "plan table kernels");
     }
+    if (p->prec == SWE_SPLIT_BF16X3) {
+        swe_status s2 = split_tables_build(p);
+        if (s2 != SWE_OK) {
+            swe_plan_destroy(p);
+            return s2;
+        }
+    }
     *out = p;
     return SWE_OK;
 }
@@ -223,7 +230,7 @@ extern "C" swe_status swe_plan_destroy(swe_plan_t p) {
     cudaFree(p->tw);
     cudaFree(p->twf);
     cudaFree(p->flags);
-    if (p->Pbf) cudaFree(p->Pbf);
+    split_tables_free(p);
     for (int i = 0; i < p->ncn; ++i) cudaFree(p->cn[i].fac);
     if (p->ws.base) cudaFree(p->ws.base);
     delete p;

@@ -93,6 +93,11 @@ struct swe_plan {
 };
 
 // ---------------------------------------------------------------------------
+// split-precision tensor-core operand tables (legendre_tc.cu)
+swe_status split_tables_build(swe_plan* p);
+void split_tables_free(swe_plan* p);
+int split_tables_error(const swe_plan* p, cudaStream_t st);
+
 // plan helpers (plan.cu)
 swe_status plan_workspace(swe_plan* p, size_t bytes, char** out);
 swe_status plan_cn_factor(swe_plan* p, double alpha, const double2** fac, cudaStream_t st);

@@ -1,0 +1,85 @@
+"""Split-precision path (bf16 x 6 products on tcgen05, FP32 FFT/grid, FP64 state) against the FP64 oracle.
+
+Bounds: single transforms <= 1e-6 relative (three-term bf16 operand splits with six
+partial products reach ~1e-8, the FP32 Fourier data ~1e-7); IMEX trajectories: the
+geopotential perturbation within 1e-6 relative L2 (height bound), vorticity and
+divergence within 1e-5.
+"""
+import numpy as np
+import pytest
+
+from oracle.sphere import Sphere
+from oracle.swe import SWE, to_dense, to_packed
+from paper_2306_09497_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GRIDS = [(31, 48, 96), (63, 96, 192), (127, 192, 384), (255, 384, 768)]
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.float64).copy()).cuda()
+
+
+@pytest.fixture(scope="module", params=GRIDS, ids=lambda g: f"T{g[0]}")
+def mixed(request):
+    from paper_2306_09497_gb300 import swe
+    M, nlat, nlon = request.param
+    plan = swe.Plan(M, nlat, nlon, prec=swe.SWE_SPLIT_BF16X3)
+    yield plan, Sphere(M, nlat, nlon)
+    plan.close()
+
+
+def test_split_sht_inverse(mixed):
+    plan, s = mixed
+    B = 6
+    coef = inputs.random_coeffs(s.M, B, seed=21)
+    grid = torch.empty((B, s.nlat, s.nlon), dtype=torch.float32, device="cuda")
+    plan.sht_inverse(_dev(coef), grid, B)
+    got = grid.cpu().numpy().astype(np.float64)
+    for b in (0, B - 1):
+        ref = s.sh_to_grid(s.unpack(coef[b]))
+        assert np.max(np.abs(got[b] - ref)) < 1e-6 * np.max(np.abs(ref))
+
+
+def test_split_sht_forward(mixed):
+    plan, s = mixed
+    B = 5
+    g = inputs.random_grid(s.nlat, s.nlon, B, seed=22)
+    spec = torch.empty((B, plan.nc * 2), dtype=torch.float64, device="cuda")
+    plan.sht_forward(torch.from_numpy(g.astype(np.float32)).cuda(), spec, B)
+    got = spec.cpu().numpy().view(np.complex128).reshape(B, -1)
+    for b in (0, B - 1):
+        ref = s.pack(s.grid_to_sh(g[b].astype(np.float32).astype(np.float64)))
+        assert np.max(np.abs(got[b] - ref)) < 1e-6 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("M,nlat,nlon,nsteps", [(63, 96, 192, 12), (255, 384, 768, 3)])
+def test_split_imex_propagation_height_bound(M, nlat, nlon, nsteps):
+    from paper_2306_09497_gb300 import swe
+    plan = swe.Plan(M, nlat, nlon, prec=swe.SWE_SPLIT_BF16X3)
+    s = Sphere(M, nlat, nlon)
+    sw = SWE(s)
+    S = 2
+    U0 = []
+    for seed in (31, 32):
+        xi, noise = inputs.initial_fields(M, seed)
+        xd = s.unpack(xi)
+        U0.append(to_packed(s, (sw.balanced_geopotential(xd) + s.unpack(noise), xd, np.zeros_like(xd))))
+    U0 = np.stack(U0)
+    dt = 432000.0 / 7296.0 if M == 255 else 240.0
+    out = torch.empty((S, 3, plan.nc * 2), dtype=torch.float64, device="cuda")
+    plan.propagate(swe.stepper(swe.SWE_IMEX, dt, nsteps), _dev(U0), out, S)
+    got = out.cpu().numpy().view(np.complex128).reshape(S, 3, -1)
+    m, _ = inputs.mn_arrays(M)
+    w = np.where(m == 0, 1.0, 2.0)
+    for b in range(1):
+        U = to_dense(s, U0[b])
+        for _ in range(nsteps):
+            U = sw.imex_step(U, dt)
+        ref = to_packed(s, U)
+        err = [np.sqrt(np.sum(w * np.abs(got[b, f] - ref[f]) ** 2) / np.sum(w * np.abs(ref[f]) ** 2)) for f in range(3)]
+        assert err[0] < 1e-6, err
+        assert err[1] < 1e-5 and err[2] < 1e-5, err
+    plan.close()
