@@ -39,7 +39,7 @@ constexpr int KC = 16;           // K per chunk (one MMA)
 constexpr int NPLANE = 3;        // bf16 split terms
 constexpr int NTERMS = 6;        // partial products kept
 constexpr uint32_t TMEM_COLS = 512;
-constexpr unsigned long long WAIT_LIMIT = 1ull << 28;   // ~seconds of polling
+constexpr unsigned long long WAIT_LIMIT = 1ull << 22;   // bounded polling (about a second)
 
 __constant__ int c_terms[NTERMS][2] = {{0, 0}, {0, 1}, {1, 0}, {0, 2}, {2, 0}, {1, 1}};
 
