@@ -50,9 +50,11 @@ def test_split_sht_forward(mixed):
     spec = torch.empty((B, plan.nc * 2), dtype=torch.float64, device="cuda")
     plan.sht_forward(torch.from_numpy(g.astype(np.float32)).cuda(), spec, B)
     got = spec.cpu().numpy().view(np.complex128).reshape(B, -1)
+    # white-noise input (no spectral decay): FP32 rounding 2^-24 times the cancellation of
+    # sum |terms| / |result| ~ sqrt(nlat nlon) / few  ->  bound 5e-6 of the largest coefficient
     for b in (0, B - 1):
         ref = s.pack(s.grid_to_sh(g[b].astype(np.float32).astype(np.float64)))
-        assert np.max(np.abs(got[b] - ref)) < 1e-6 * np.max(np.abs(ref))
+        assert np.max(np.abs(got[b] - ref)) < 5e-6 * np.max(np.abs(ref))
 
 
 @pytest.mark.parametrize("M,nlat,nlon,nsteps", [(63, 96, 192, 12), (255, 384, 768, 3)])
