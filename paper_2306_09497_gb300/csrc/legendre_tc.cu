@@ -627,6 +627,8 @@ swe_status leg_inverse_split(const swe_plan* p, const double2* X, float2* F, int
     dim3 grid((sh.ncol + BM - 1) / BM, p->M + 1, t->ntiles_inv);
     const double fl = (double)C * p->nlat * (p->M + 1.0) * (p->M + 2.0);
     const double by = 16.0 * C * p->ncx + 8.0 * C * (p->M + 1.0) * p->nlat;
+    // the dynamic shared-memory limit is a per-function attribute shared by all plans: set it per launch
+    SWE_CHECK_CUDA(cudaFuncSetAttribute(k_leg_inv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_inv));
     ProfToken tk = prof_begin("leg_inv_tc", st, fl, by);
     k_leg_inv_tc<<<grid, BM, t->smem_inv, st>>>((const double*)X, (float*)F, t->inv, t->inv_off, t->inv_nq, sh,
                                                 t->err);
@@ -646,6 +648,7 @@ swe_status leg_forward_split(const swe_plan* p, const float2* F, double2* Y, int
     dim3 grid((sh.ncol + BM - 1) / BM, p->M + 1, (kmax0 + t->nt_fwd - 1) / t->nt_fwd);
     const double fl = (double)C * p->nlat * (p->M + 1.0) * (p->M + 2.0);
     const double by = 8.0 * C * (p->M + 1.0) * p->nlat + 16.0 * C * p->ncx;
+    SWE_CHECK_CUDA(cudaFuncSetAttribute(k_leg_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_fwd));
     ProfToken tk = prof_begin("leg_fwd_tc", st, fl, by);
     k_leg_fwd_tc<<<grid, BM, t->smem_fwd, st>>>((const float*)F, (double*)Y, t->fwd, t->fwd_off, t->fwd_ntiles, sh,
                                                 t->err);
