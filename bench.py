@@ -17,7 +17,12 @@ Inputs are synthetic: seeded k^-3 balanced vorticity (rms wind 20 m/s) plus
 timed region.  The working set (~4 GB of Fourier/spectral buffers per F sweep)
 is far larger than L2, so no explicit flush is needed between iterations.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|mixed] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|fp64] [--no-fp64] [--impl reference]
+
+The headline value is the mixed-precision path (split-bf16 tensor-core Legendre GEMM,
+FP32 FFT and grid products, FP64 spectral state and Parareal correction); the same
+iteration in FP64 plain arithmetic is measured on the same GPU and reported as
+"fp64_plain" with the ratio "mixed_over_fp64".
 """
 from __future__ import annotations
 
@@ -165,19 +170,15 @@ def run_reference(args):
     return 0
 
 
-def run_ours(args):
+def measure(args, prec_name, rank, world, local, with_e2e=True):
+    """One precision: warm-up, timed Parareal iterations, optional host-buffer e2e leg."""
     import numpy as np
     import torch
 
     from paper_2306_09497_gb300 import inputs, swe
 
-    rank, world, local = _env_rank()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", init_method="env://")
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    prec = swe.SWE_FP64 if args.prec == "fp64" else swe.SWE_SPLIT_BF16X3
+    prec = swe.SWE_FP64 if prec_name == "fp64" else swe.SWE_SPLIT_BF16X3
     plan = swe.Plan(M, NLAT, NLON, prec=prec)
     cplan = swe.Plan(MC, NLATC, NLONC, prec=prec)
     fine = swe.stepper(swe.SWE_IMEX, DT0, NF)
@@ -197,7 +198,7 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
 
-    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    clocks = ClockSampler(local)
     clocks.start()
     swe.prof_reset()
     swe.prof_enable(True)
@@ -223,77 +224,102 @@ def run_ours(args):
         t = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
-    value = world * S * NF / (ms / 1000.0)
-
-    # end to end through the public API with host buffers: load the Parareal state
-    # from pinned host memory, iterate, save it back to host memory
-    per_state = 3 * plan.nc * 2
-    U_h = torch.empty((S + 1) * per_state, dtype=torch.float64, pin_memory=True)
-    G_h = torch.empty(S * per_state, dtype=torch.float64, pin_memory=True)
-    pr.save_state(U_h, G_h)
-    torch.cuda.synchronize()
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        pr.load_state(U_h, G_h)
-        pr.iterate(1)
+    res = {"ms": ms, "value": world * S * NF / (ms / 1000.0), "launches": launches, "stats": stats,
+           "clocks": clk, "norms": norms}
+    if with_e2e:
+        # end to end through the public API with host buffers: load the Parareal state
+        # from pinned host memory, iterate, save it back to host memory
+        per_state = 3 * plan.nc * 2
+        U_h = torch.empty((S + 1) * per_state, dtype=torch.float64, pin_memory=True)
+        G_h = torch.empty(S * per_state, dtype=torch.float64, pin_memory=True)
         pr.save_state(U_h, G_h)
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    nbytes = (U_h.numel() + G_h.numel()) * 8
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pr.load_state(U_h, G_h)
+            pr.iterate(1)
+            pr.save_state(U_h, G_h)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        if world > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        res["e2e"] = {"value": world * S * NF / e2e_s, "unit": "slice-steps/s",
+                      "h2d_bytes_per_step": (U_h.numel() + G_h.numel()) * 8,
+                      "d2h_bytes_per_step": (U_h.numel() + G_h.numel()) * 8}
+    pr.close()
+    plan.close()
+    cplan.close()
+    return res
 
-    # roofline of the dominant kernel (largest event-timed total)
+
+def roofline(stats):
+    """Roofline entry of the dominant kernel (largest event-timed total)."""
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    roof = None
-    if stats:
-        name, (n, tot_ms, fl, by) = max(stats.items(), key=lambda kv: kv[1][1])
-        avg = tot_ms / max(n, 1)
-        if name.startswith("leg_") and name.endswith("f64"):
-            ach = fl / n / (avg / 1000.0) / 1e12
-            roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "avg_launch_ms": avg, "launches_timed": n,
-                    "peak_source": "nominal FP64 DFMA rate (profiling recipe table)"}
-        elif name.startswith("leg_"):
-            pk = peaks.get("bf16_tflops_sustained", 1748.7)
-            ach = fl / n / (avg / 1000.0) / 1e12
-            roof = {"kernel": name, "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                    "frac": ach / pk, "traffic": None, "avg_launch_ms": avg, "launches_timed": n,
-                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (measured)"}
-        else:
-            pk = peaks.get("hbm_gbs", 6674.8)
-            ach = by / n / (avg / 1000.0) / 1e9
-            roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,
-                    "traffic": None, "avg_launch_ms": avg, "launches_timed": n,
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
-        roof["kernels"] = {k: {"launches": v[0], "avg_ms": v[1] / max(v[0], 1),
-                               "share_of_timed": v[1] / sum(x[1] for x in stats.values())}
-                           for k, v in stats.items()}
+    if not stats:
+        return None
+    name, (n, tot_ms, fl, by) = max(stats.items(), key=lambda kv: kv[1][1])
+    avg = tot_ms / max(n, 1)
+    if name.startswith("leg_") and name.endswith("f64"):
+        ach = fl / n / (avg / 1000.0) / 1e12
+        roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "peak_source": "nominal FP64 DFMA rate (profiling recipe table)"}
+    elif name.startswith("leg_"):
+        pk = peaks.get("bf16_tflops_sustained", 1748.7)
+        ach = 6.0 * fl / n / (avg / 1000.0) / 1e12   # six bf16 partial products per useful product
+        roof = {"kernel": name, "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (measured)"}
+    else:
+        pk = peaks.get("hbm_gbs", 6674.8)
+        ach = by / n / (avg / 1000.0) / 1e9
+        roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+    roof.update({"traffic": None, "avg_launch_ms": avg, "launches_timed": n})
+    tot = sum(x[1] for x in stats.values())
+    roof["kernels"] = {k: {"launches": v[0], "avg_ms": v[1] / max(v[0], 1), "share_of_timed": v[1] / tot}
+                       for k, v in stats.items()}
+    return roof
 
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    main_prec = args.prec
+    r = measure(args, main_prec, rank, world, local, with_e2e=True)
     line = {
-        "metric": METRIC, "value": value, "unit": "slice-steps/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "mixed(bf16x3-split GEMM, f32 FFT, f64 state)",
+        "metric": METRIC, "value": r["value"], "unit": "slice-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if main_prec == "fp64" else "mixed: bf16 split x6 tensor GEMM, f32 FFT/grid, f64 state",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "M": M, "nlat": NLAT, "nlon": NLON, "slices": S, "fine_steps": NF,
                    "fine_dt": DT0, "coarse_M": MC, "coarse_grid": [NLATC, NLONC], "coarse_steps": NC_STEPS,
                    "coarse_dt": DTC, "coarse_visc": [Q_C, NU_C],
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                   "l2": "working set > L2 (no flush)", "precision": args.prec},
-        "e2e": {"value": world * S * NF / e2e_s, "unit": "slice-steps/s", "h2d_bytes_per_step": nbytes,
-                "d2h_bytes_per_step": nbytes},
-        "gpu_launches": launches,
-        "roofline": roof,
-        "clocks": clk,
-        "convergence_norms": norms,
+                   "l2": "working set > L2 (no flush)", "precision": main_prec},
+        "e2e": r["e2e"],
+        "gpu_launches": r["launches"],
+        "roofline": roofline(r["stats"]),
+        "clocks": r["clocks"],
+        "convergence_norms": r["norms"],
     }
+    if main_prec == "mixed" and not args.no_fp64:
+        f = measure(args, "fp64", rank, world, local, with_e2e=False)
+        line["fp64_plain"] = {"value": f["value"], "unit": "slice-steps/s", "ms_per_step": f["ms"],
+                              "gpu_launches": f["launches"], "roofline": roofline(f["stats"]),
+                              "clocks": f["clocks"], "convergence_norms": f["norms"]}
+        line["mixed_over_fp64"] = r["value"] / f["value"]
     if rank == 0 and world == 1 and not args.no_cpu:
         cb = oracle_baseline(args.cpu_seconds)
         if "error" not in cb:
@@ -303,9 +329,6 @@ def run_ours(args):
         else:
             line["cpu_baseline"] = {"value": None, "unit": "slice-steps/s", "cores": 1, "kind": "oracle",
                                     "sample": "oracle failed: " + cb["error"][-200:]}
-    pr.close()
-    plan.close()
-    cplan.close()
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -319,7 +342,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--prec", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain comparison run")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
