@@ -230,6 +230,7 @@ extern "C" swe_status swe_plan_destroy(swe_plan_t p) {
     cudaFree(p->tw);
     cudaFree(p->twf);
     cudaFree(p->flags);
+    cudaFree(p->thx);
     split_tables_free(p);
     for (int i = 0; i < p->ncn; ++i) cudaFree(p->cn[i].fac);
     if (p->ws.base) cudaFree(p->ws.base);

@@ -1,0 +1,411 @@
+// SL-SI-SETTLS step (§2.3.2, Eqs. 6-7), batched over S states.
+//
+//   (I - dt/2 L) U^{n+1} = [U^n + dt/2 L U^n + dt/2 (2 N_R^n - N_R^{n-1})]_* + dt/2 N_R^n,
+//   followed by backward-Euler viscosity; N_R = (-Phi' delta, 0, 0); "_*" = value at the
+//   departure point x_d of the trajectory arriving at the grid point x_a, from SETTLS:
+//   x_d^{k+1} = x_a - dt/2 [2 V(t_n, x_d^k) - V(t_{n-1}, x_d^k) + V(t_n, x_a)],  x_d^0 = x_a,
+//   two iterations, in 3-D Cartesian coordinates projected back on the unit sphere.
+// Interpolation: bicubic Lagrange in (longitude, Gaussian latitude) with two halo
+// rows beyond each pole (the rows across the pole, shifted by 180 degrees); the
+// velocity is interpolated through its three Cartesian components (smooth scalar
+// fields everywhere on the sphere).  The one-step variant (§3.2.4) replaces the
+// t_{n-1} data by the t_n data; the first step of a chain is always one-step.
+#include "swe_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ double2 c_add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 c_sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 c_scale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 c_imul(double2 a, double s) { return make_double2(-a.y * s, a.x * s); }
+__device__ __forceinline__ double2 czero() { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ double cp_(int m, int n) { return n >= 1 ? (n + 1.0) / n * eps_nm(m, n) : 0.0; }
+__device__ __forceinline__ double cq_(int m, int n) { return n >= 1 ? n / (n + 1.0) * eps_nm(m, n + 1) : 0.0; }
+__device__ __forceinline__ double cr_(int m, int n) { return n >= 1 ? (double)m / ((double)n * (n + 1.0)) : 0.0; }
+
+struct SV {   // SoA spectral state view
+    const double2* u;
+    int64_t nc;
+    int S, M;
+    __device__ __forceinline__ double2 get(int f, int m, int n, int s) const {
+        if (n < m || n > M) return czero();
+        if (n == 0 && f > 0) return czero();
+        return u[((int64_t)f * nc + st_off(m, M) + (n - m)) * S + s];
+    }
+};
+
+// Transform operands, rows (m, n <= M+1), columns f*S + s.
+//   full = 1: f = 0..2 X = U + h L U (h = dt/2), 3 Phi', 4 delta, 5 U_cos, 6 V_cos   (7 fields)
+//   full = 0: f = 0 Phi', 1 delta, 2 U_cos, 3 V_cos                                 (4 fields)
+__global__ void k_sl_operands(SV U, double2* __restrict__ X, const int* __restrict__ row_m, int64_t ncx, int nf,
+                              int full, double h, double a, double omega, double phibar) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int S = U.S, M = U.M;
+    if (t >= ncx * S) return;
+    const int s = (int)(t % S);
+    const int64_t rx = t / S;
+    const int m = row_m[rx];
+    const int n = m + (int)(rx - ex_off(m, M));
+    const double a2 = a * a;
+    auto psi = [&](int k) -> double2 {
+        if (k < 1 || k < m) return czero();
+        return c_scale(U.get(1, m, k, s), -a2 / ((double)k * (k + 1.0)));
+    };
+    auto chi = [&](int k) -> double2 {
+        if (k < 1 || k < m) return czero();
+        return c_scale(U.get(2, m, k, s), -a2 / ((double)k * (k + 1.0)));
+    };
+    const double en = eps_nm(m, n), en1 = eps_nm(m, n + 1), ia = 1.0 / a;
+    double2 Uh = c_scale(c_add(c_imul(chi(n), (double)m),
+                               c_sub(c_scale(psi(n - 1), (n - 1.0) * en), c_scale(psi(n + 1), (n + 2.0) * en1))),
+                         ia);
+    double2 Vh = c_scale(c_add(c_imul(psi(n), (double)m),
+                               c_sub(c_scale(chi(n + 1), (n + 2.0) * en1), c_scale(chi(n - 1), (n - 1.0) * en))),
+                         ia);
+    double2 ph = U.get(0, m, n, s), xi = U.get(1, m, n, s), de = U.get(2, m, n, s);
+    double2* row = X + rx * (int64_t)nf * S + s;
+    if (full) {
+        const double w2 = 2.0 * omega, p = cp_(m, n), q = cq_(m, n), r = cr_(m, n);
+        double2 L0 = c_scale(de, -phibar);
+        double2 L1 = c_add(c_scale(c_add(c_scale(U.get(2, m, n - 1, s), p), c_scale(U.get(2, m, n + 1, s), q)), -w2),
+                           c_imul(xi, w2 * r));
+        double2 L2 = c_add(c_scale(ph, (double)n * (n + 1.0) / a2),
+                           c_add(c_scale(c_add(c_scale(U.get(1, m, n - 1, s), p), c_scale(U.get(1, m, n + 1, s), q)), w2),
+                                 c_imul(de, w2 * r)));
+        row[0] = c_add(ph, c_scale(L0, h));
+        row[S] = c_add(xi, c_scale(L1, h));
+        row[2 * S] = c_add(de, c_scale(L2, h));
+        row[3 * S] = ph;
+        row[4 * S] = de;
+        row[5 * S] = Uh;
+        row[6 * S] = Vh;
+    } else {
+        row[0] = ph;
+        row[S] = de;
+        row[2 * S] = Uh;
+        row[3 * S] = Vh;
+    }
+}
+
+// Cartesian velocity (m/s) and N_R = -Phi' delta on the grid, from fields
+// (Phi', delta, U_cos, V_cos) at field offsets (fp, fd, fu, fv) of a grid block [nf*S][nlat][nlon].
+template <typename T>
+__global__ void k_sl_vel(const T* __restrict__ G, int fp, int fd, int fu, int fv, T* __restrict__ Vc,
+                         T* __restrict__ NR, const double* __restrict__ mu, int S, int nlat, int nlon) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t npt = (int64_t)nlat * nlon;
+    if (t >= npt * S) return;
+    const int s = (int)(t / npt);
+    const int64_t p = t - (int64_t)s * npt;
+    const int j = (int)(p / nlon), k = (int)(p - (int64_t)j * nlon);
+    auto at = [&](int f) { return (double)G[((int64_t)f * S + s) * npt + p]; };
+    const double sinl = mu[j], cosl = sqrt((1.0 - sinl) * (1.0 + sinl));
+    const double u = at(fu) / cosl, v = at(fv) / cosl;
+    double sl, cl;
+    sincospi(2.0 * k / nlon, &sl, &cl);
+    Vc[((int64_t)0 * S + s) * npt + p] = (T)(-u * sl - v * sinl * cl);
+    Vc[((int64_t)1 * S + s) * npt + p] = (T)(u * cl - v * sinl * sl);
+    Vc[((int64_t)2 * S + s) * npt + p] = (T)(v * cosl);
+    NR[(int64_t)s * npt + p] = (T)(-at(fp) * at(fd));
+}
+
+// X_Phi += h (2 N_R^n - N_R^{n-1}) in place (field 0 of the 7-field block)
+template <typename T>
+__global__ void k_sl_xphi(T* __restrict__ G, const T* __restrict__ NRn, const T* __restrict__ NRm, double h, int S,
+                          int64_t npt) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= npt * S) return;
+    G[t] = (T)((double)G[t] + h * (2.0 * (double)NRn[t] - (double)NRm[t]));
+}
+
+struct Stencil {
+    int row[4], shift[4], col0;
+    double wl[4], wx[4];
+};
+
+// bracket + Lagrange weights of the departure point (latd, lond); thx = extended latitudes (nlat+4)
+__device__ __forceinline__ void make_stencil(double latd, double lond, const double* __restrict__ thx, int nlat,
+                                             int nlon, Stencil& st) {
+    // i = (number of extended latitudes >= latd) - 1, clipped to [1, nlat+1]  (thx descending)
+    int lo = 0, hi = nlat + 4;                 // count of entries >= latd lies in [lo, hi]
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (thx[mid] >= latd) lo = mid + 1; else hi = mid;
+    }
+    int i = lo - 1;
+    i = i < 1 ? 1 : (i > nlat + 1 ? nlat + 1 : i);
+    double y[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int e = i - 1 + r;               // extended index 0..nlat+3
+        y[r] = thx[e];
+        int rowi, sh = 0;
+        if (e < 2) {
+            rowi = 1 - e;
+            sh = nlon / 2;
+        } else if (e < nlat + 2) {
+            rowi = e - 2;
+        } else {
+            rowi = nlat - 1 - (e - (nlat + 2));
+            sh = nlon / 2;
+        }
+        st.row[r] = rowi;
+        st.shift[r] = sh;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        double w = 1.0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (q != r) w *= (latd - y[q]) / (y[r] - y[q]);
+        st.wl[r] = w;
+    }
+    const double dl = 2.0 * M_PI / nlon;
+    double x = fmod(lond, 2.0 * M_PI);
+    if (x < 0) x += 2.0 * M_PI;
+    x /= dl;
+    int i0 = (int)floor(x);
+    const double t = x - i0;
+    i0 = ((i0 % nlon) + nlon) % nlon;
+    st.col0 = i0;
+    st.wx[0] = -t * (t - 1.0) * (t - 2.0) / 6.0;
+    st.wx[1] = (t + 1.0) * (t - 1.0) * (t - 2.0) / 2.0;
+    st.wx[2] = -(t + 1.0) * t * (t - 2.0) / 2.0;
+    st.wx[3] = (t + 1.0) * t * (t - 1.0) / 6.0;
+}
+
+template <typename T>
+__device__ __forceinline__ double interp(const T* __restrict__ F, const Stencil& st, int nlon) {
+    double acc = 0.0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const T* row = F + (int64_t)st.row[r] * nlon;
+        double a = 0.0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            int col = st.col0 - 1 + c + st.shift[r];
+            col = ((col % nlon) + nlon) % nlon;
+            a += st.wx[c] * (double)row[col];
+        }
+        acc += st.wl[r] * a;
+    }
+    return acc;
+}
+
+// departure points + gather: R[f*S + s] = X_f(x_d) (+ h N_R^n(x_a) for f = 0)
+template <typename T>
+__global__ void k_sl_depart(const T* __restrict__ G, const T* __restrict__ Vn, const T* __restrict__ Vm,
+                            const T* __restrict__ NRn, T* __restrict__ R, const double* __restrict__ thx, double h,
+                            double a, int S, int nlat, int nlon) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t npt = (int64_t)nlat * nlon;
+    if (t >= npt * S) return;
+    const int s = (int)(t / npt);
+    const int64_t p = t - (int64_t)s * npt;
+    const int j = (int)(p / nlon), k = (int)(p - (int64_t)j * nlon);
+    const double lat = thx[j + 2];
+    double sl, cl, sp, cp;
+    sincospi(2.0 * k / nlon, &sl, &cl);
+    sincos(lat, &sp, &cp);
+    const double xa[3] = {cp * cl, cp * sl, sp};
+    double va[3], vm[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        va[d] = (double)Vn[((int64_t)d * S + s) * npt + p];
+        vm[d] = (double)Vm[((int64_t)d * S + s) * npt + p];
+    }
+    const double sc = h / a;   // (dt/2) / a
+    double latd = lat, lond = 2.0 * M_PI * k / nlon;
+    double vn[3] = {va[0], va[1], va[2]};   // x_d^0 = x_a: grid values
+    Stencil st;
+    for (int it = 0; it < 2; ++it) {
+        if (it > 0) {
+            make_stencil(latd, lond, thx, nlat, nlon, st);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                vn[d] = interp(Vn + ((int64_t)d * S + s) * npt, st, nlon);
+                vm[d] = interp(Vm + ((int64_t)d * S + s) * npt, st, nlon);
+            }
+        }
+        double xd[3], nrm = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            xd[d] = xa[d] - sc * (2.0 * vn[d] - vm[d] + va[d]);
+            nrm += xd[d] * xd[d];
+        }
+        nrm = 1.0 / sqrt(nrm);
+        const double z = fmin(1.0, fmax(-1.0, xd[2] * nrm));
+        latd = asin(z);
+        lond = atan2(xd[1], xd[0]);
+        if (lond < 0) lond += 2.0 * M_PI;
+    }
+    make_stencil(latd, lond, thx, nlat, nlon, st);
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        double v = interp(G + ((int64_t)f * S + s) * npt, st, nlon);
+        if (f == 0) v += h * (double)NRn[(int64_t)s * npt + p];
+        R[((int64_t)f * S + s) * npt + p] = (T)v;
+    }
+}
+
+// forward results Y [ncx][3S] -> SoA state [3][NC][S] (rows n <= M)
+__global__ void k_sl_unpack(const double2* __restrict__ Y, double2* __restrict__ R, const int* __restrict__ srow_m,
+                            int M, int64_t nc, int S) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nc * S) return;
+    const int s = (int)(t % S);
+    const int64_t r = t / S;
+    const int m = srow_m[r];
+    const int n = m + (int)(r - st_off(m, M));
+    const double2* y = Y + (ex_off(m, M) + (n - m)) * 3 * (int64_t)S + s;
+#pragma unroll
+    for (int f = 0; f < 3; ++f) R[((int64_t)f * nc + r) * S + s] = y[(int64_t)f * S];
+}
+
+__global__ void k_thx(const double* __restrict__ mu, double* __restrict__ thx, int nlat) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nlat + 4) return;
+    double v;
+    if (e < 2) v = M_PI - asin(mu[1 - e]);
+    else if (e < nlat + 2) v = asin(mu[e - 2]);
+    else v = -M_PI - asin(mu[nlat - 1 - (e - (nlat + 2))]);
+    thx[e] = v;
+}
+
+inline unsigned nb(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+// workspace of one SL step for S columns (grid fields in the plan's real type)
+size_t sl_bytes(const swe_plan* p, int S) {
+    const size_t rt = (p->prec == SWE_FP64) ? 8 : 4;
+    const size_t fe = (p->prec == SWE_FP64) ? 16 : 8;
+    const size_t npt = (size_t)p->nlat * p->nlon;
+    const size_t four = (size_t)(p->M + 1) * p->nlat;
+    size_t b = 0;
+    b += a256(16 * (size_t)p->ncx * 7 * S);       // X operands
+    b += a256(fe * four * 7 * S);                 // Fourier
+    b += a256(rt * npt * 7 * S);                  // grid fields
+    b += 2 * a256(rt * npt * 3 * S);              // Vc current / previous
+    b += 2 * a256(rt * npt * S);                  // N_R current / previous
+    b += a256(rt * npt * 3 * S);                  // R grid
+    b += a256(rt * npt * 4 * S);                  // grid fields of an explicit previous state
+    b += a256(16 * (size_t)p->ncx * 3 * S);       // forward results
+    b += a256(16 * 3 * (size_t)p->nc * S);        // R spectral
+    return b;
+}
+
+struct SLBuf {
+    double2 *X, *Y, *Rs;
+    void *Fq, *G, *Vc, *Vp, *Nc, *Np, *R, *Gp;
+};
+
+static SLBuf sl_carve(const swe_plan* p, char* c, int S) {
+    const size_t rt = (p->prec == SWE_FP64) ? 8 : 4;
+    const size_t fe = (p->prec == SWE_FP64) ? 16 : 8;
+    const size_t npt = (size_t)p->nlat * p->nlon;
+    const size_t four = (size_t)(p->M + 1) * p->nlat;
+    SLBuf b;
+    b.X = (double2*)c; c += a256(16 * (size_t)p->ncx * 7 * S);
+    b.Fq = c; c += a256(fe * four * 7 * S);
+    b.G = c; c += a256(rt * npt * 7 * S);
+    b.Vc = c; c += a256(rt * npt * 3 * S);
+    b.Vp = c; c += a256(rt * npt * 3 * S);
+    b.Nc = c; c += a256(rt * npt * S);
+    b.Np = c; c += a256(rt * npt * S);
+    b.R = c; c += a256(rt * npt * 3 * S);
+    b.Gp = c; c += a256(rt * npt * 4 * S);
+    b.Y = (double2*)c; c += a256(16 * (size_t)p->ncx * 3 * S);
+    b.Rs = (double2*)c;
+    return b;
+}
+
+static swe_status ensure_thx(swe_plan* p) {
+    if (p->thx) return SWE_OK;
+    SWE_CHECK_CUDA(cudaMalloc((void**)&p->thx, sizeof(double) * (p->nlat + 4)));
+    k_thx<<<nb(p->nlat + 4, 64), 64>>>(p->mu, p->thx, p->nlat);
+    SWE_CHECK_LAUNCH("k_thx");
+    SWE_CHECK_CUDA(cudaDeviceSynchronize());
+    return SWE_OK;
+}
+
+swe_status sl_prepare(swe_plan* p) { return ensure_thx(p); }
+
+template <typename T>
+static swe_status vel_launch(const swe_plan* p, const void* G, int fp, int fd, int fu, int fv, void* Vc, void* NR,
+                             int S, cudaStream_t st) {
+    const int64_t n = (int64_t)p->nlat * p->nlon * S;
+    k_sl_vel<T><<<nb(n), 256, 0, st>>>((const T*)G, fp, fd, fu, fv, (T*)Vc, (T*)NR, p->mu, S, p->nlat, p->nlon);
+    SWE_CHECK_LAUNCH("k_sl_vel");
+    return SWE_OK;
+}
+
+// One SL-SI-SETTLS step on SoA states.  Uprev == nullptr and !have_prev -> one-step form.
+// have_prev: the previous step's velocity / N_R are already in the workspace (chain inside one call).
+// Result written to Uout (may not alias U).
+swe_status sl_step(swe_plan* p, double dt, double nu, int q, const double2* Uprev, bool have_prev, const double2* U,
+                   double2* Uout, int S, char* ws, bool swap_prev, cudaStream_t st) {
+    SWE_CHECK(ensure_thx(p));
+    SLBuf b = sl_carve(p, ws, S);
+    const double h = 0.5 * dt;
+    const bool f64 = (p->prec == SWE_FP64);
+    const int64_t npt = (int64_t)p->nlat * p->nlon;
+    // operands of the current state (7 fields) -> grid
+    SV v{U, p->nc, S, p->M};
+    k_sl_operands<<<nb(p->ncx * S), 256, 0, st>>>(v, b.X, p->row_m, p->ncx, 7, 1, h, p->a, p->omega, p->phibar);
+    SWE_CHECK_LAUNCH("k_sl_operands");
+    SWE_CHECK(leg_inverse(p, b.X, b.Fq, 7 * S, st));
+    SWE_CHECK(ring_inverse(p, b.Fq, b.G, 7 * S, st));
+    // current velocity / N_R
+    if (f64) SWE_CHECK(vel_launch<double>(p, b.G, 3, 4, 5, 6, b.Vc, b.Nc, S, st));
+    else SWE_CHECK(vel_launch<float>(p, b.G, 3, 4, 5, 6, b.Vc, b.Nc, S, st));
+    // previous velocity / N_R
+    const void* Vm = b.Vc;
+    const void* Nm = b.Nc;
+    if (have_prev) {
+        Vm = b.Vp;
+        Nm = b.Np;
+    } else if (Uprev) {
+        // grid fields (Phi', delta, U_cos, V_cos) of the previous state -> previous velocity / N_R
+        SV vp{Uprev, p->nc, S, p->M};
+        k_sl_operands<<<nb(p->ncx * S), 256, 0, st>>>(vp, b.X, p->row_m, p->ncx, 4, 0, h, p->a, p->omega, p->phibar);
+        SWE_CHECK_LAUNCH("k_sl_operands(prev)");
+        SWE_CHECK(leg_inverse(p, b.X, b.Fq, 4 * S, st));
+        SWE_CHECK(ring_inverse(p, b.Fq, b.Gp, 4 * S, st));
+        if (f64) SWE_CHECK(vel_launch<double>(p, b.Gp, 0, 1, 2, 3, b.Vp, b.Np, S, st));
+        else SWE_CHECK(vel_launch<float>(p, b.Gp, 0, 1, 2, 3, b.Vp, b.Np, S, st));
+        Vm = b.Vp;
+        Nm = b.Np;
+    }
+    // X_Phi += h (2 N_R^n - N_R^{n-1})
+    if (f64) {
+        k_sl_xphi<double><<<nb(npt * S), 256, 0, st>>>((double*)b.G, (const double*)b.Nc, (const double*)Nm, h, S, npt);
+    } else {
+        k_sl_xphi<float><<<nb(npt * S), 256, 0, st>>>((float*)b.G, (const float*)b.Nc, (const float*)Nm, h, S, npt);
+    }
+    SWE_CHECK_LAUNCH("k_sl_xphi");
+    if (f64) {
+        k_sl_depart<double><<<nb(npt * S, 128), 128, 0, st>>>((const double*)b.G, (const double*)b.Vc,
+                                                              (const double*)Vm, (const double*)b.Nc, (double*)b.R,
+                                                              p->thx, h, p->a, S, p->nlat, p->nlon);
+    } else {
+        k_sl_depart<float><<<nb(npt * S, 128), 128, 0, st>>>((const float*)b.G, (const float*)b.Vc,
+                                                             (const float*)Vm, (const float*)b.Nc, (float*)b.R,
+                                                             p->thx, h, p->a, S, p->nlat, p->nlon);
+    }
+    SWE_CHECK_LAUNCH("k_sl_depart");
+    SWE_CHECK(ring_forward(p, b.R, b.Fq, 3 * S, st));
+    SWE_CHECK(leg_forward(p, b.Fq, b.Y, 3 * S, st));
+    k_sl_unpack<<<nb(p->nc * S), 256, 0, st>>>(b.Y, b.Rs, p->srow_m, p->M, p->nc, S);
+    SWE_CHECK_LAUNCH("k_sl_unpack");
+    SWE_CHECK(k_implicit(p, h, 0, b.Rs, Uout, dt, nu, q, S, st));
+    if (swap_prev) {
+        // the current velocity / N_R become the previous ones of the next step
+        const size_t rt = f64 ? 8 : 4;
+        SWE_CHECK_CUDA(cudaMemcpyAsync(b.Vp, b.Vc, rt * npt * 3 * S, cudaMemcpyDeviceToDevice, st));
+        SWE_CHECK_CUDA(cudaMemcpyAsync(b.Np, b.Nc, rt * npt * S, cudaMemcpyDeviceToDevice, st));
+    }
+    return SWE_OK;
+}

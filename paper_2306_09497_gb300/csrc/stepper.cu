@@ -22,7 +22,11 @@ swe_status leg_forward(const swe_plan* p, const void* F, double2* Y, int C, cuda
 
 static size_t state_bytes(const swe_plan* p, int S) { return al256(sizeof(double2) * 3 * p->nc * S); }
 
-size_t stepper_bytes(const swe_plan* p, int S) { return 3 * state_bytes(p, S) + nl_bytes(p, S); }
+size_t stepper_bytes(const swe_plan* p, int S) {
+    size_t imex = 3 * state_bytes(p, S) + nl_bytes(p, S);
+    size_t sl = state_bytes(p, S) + sl_bytes(p, S);
+    return imex > sl ? imex : sl;
+}
 
 // N(U_a + beta U_b) -> N (SoA, S columns); ws must hold nl_bytes(p, S)
 swe_status nonlinear_soa(swe_plan* p, const double2* Ua, const double2* Ub, double beta, double2* N, int S, char* ws,
@@ -72,8 +76,8 @@ static swe_status check_stepper(const swe_stepper_desc* sd) {
                       sd->nsteps, sd->dt, sd->visc_nu, sd->visc_q);
         return SWE_EINVAL;
     }
-    if (sd->scheme != SWE_IMEX) {
-        swe_set_error("stepper: scheme %d is not available in this build", sd->scheme);
+    if (sd->scheme != SWE_IMEX && sd->scheme != SWE_SLSI_SETTLS && sd->scheme != SWE_SLSI_SETTLS_1STEP) {
+        swe_set_error("stepper: unknown scheme %d", sd->scheme);
         return SWE_EINVAL;
     }
     return SWE_OK;
@@ -88,6 +92,22 @@ static swe_status run_soa(swe_plan* p, const swe_stepper_desc* sd, double2* U, i
     char* nlws = ws + 3 * sb;
     double2* cur = U;
     double2* oth = T;
+    if (sd->scheme != SWE_IMEX) {
+        // SL-SI-SETTLS: the first step is one-step; later steps of the two-step scheme reuse
+        // the previous step's velocity and N_R (kept in the SL workspace)
+        char* slws = ws + sb;
+        SWE_CHECK(sl_prepare(p));
+        const bool two = (sd->scheme == SWE_SLSI_SETTLS);
+        for (int k = 0; k < sd->nsteps; ++k) {
+            SWE_CHECK(sl_step(p, sd->dt, sd->visc_nu, sd->visc_q, nullptr, two && k > 0, cur, oth, S, slws,
+                              two && k + 1 < sd->nsteps, st));
+            double2* t = cur;
+            cur = oth;
+            oth = t;
+        }
+        if (cur != U) SWE_CHECK_CUDA(cudaMemcpyAsync(U, cur, sizeof(double2) * 3 * p->nc * S, cudaMemcpyDeviceToDevice, st));
+        return SWE_OK;
+    }
     for (int k = 0; k < sd->nsteps; ++k) {
         double2* res;
         SWE_CHECK(imex_step(p, sd->dt, sd->visc_nu, sd->visc_q, cur, oth, Us, Ub, nlws, S, st, &res));

@@ -90,6 +90,8 @@ struct swe_plan {
     Workspace ws;
     // device flags: [0] non-finite seen
     int* flags = nullptr;
+    // extended latitudes for semi-Lagrangian interpolation (built on first use)
+    double* thx = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -150,6 +152,12 @@ swe_status k_balance_combine(const swe_plan* p, const double2* xi_soa, const dou
                              const double2* phi_add_soa, double2* U, int S, cudaStream_t st);
 swe_status k_axpy(double2* y, const double2* x, double a, int64_t n, cudaStream_t st);
 swe_status k_truncate(const double2* in, int Min, double2* out, int Mout, int S, cudaStream_t st);
+
+// semi-Lagrangian step (sl.cu)
+size_t sl_bytes(const swe_plan* p, int S);
+swe_status sl_prepare(swe_plan* p);
+swe_status sl_step(swe_plan* p, double dt, double nu, int q, const double2* Uprev, bool have_prev, const double2* U,
+                   double2* Uout, int S, char* ws, bool swap_prev, cudaStream_t st);
 
 // stepper (stepper.cu), SoA state with S columns; U updated in place
 swe_status stepper_run(swe_plan* p, const swe_stepper_desc* sd, double2* U, int S, cudaStream_t st);
