@@ -64,6 +64,14 @@ __global__ void k_sl_operands(SV U, double2* __restrict__ X, const int* __restri
                          ia);
     double2 ph = U.get(0, m, n, s), xi = U.get(1, m, n, s), de = U.get(2, m, n, s);
     double2* row = X + rx * (int64_t)nf * S + s;
+    if (n > M) {
+        // the extended row n = M+1 carries only the velocity operands; every other field is
+        // truncated at M (the Coriolis coupling of L U would otherwise leak into degree M+1)
+        for (int f = 0; f < nf - 2; ++f) row[(int64_t)f * S] = czero();
+        row[(int64_t)(nf - 2) * S] = Uh;
+        row[(int64_t)(nf - 1) * S] = Vh;
+        return;
+    }
     if (full) {
         const double w2 = 2.0 * omega, p = cp_(m, n), q = cq_(m, n), r = cr_(m, n);
         double2 L0 = c_scale(de, -phibar);
