@@ -159,7 +159,16 @@ class SWE:
         return out
 
     def implicit_solve(self, R, alpha):
-        """Solve (I - alpha L) X = R exactly, one banded system per m."""
+        """Solve (I - alpha L) X = R exactly, one banded system per m.
+
+        The global means of vorticity and divergence (coefficient (0, 0) of xi and
+        delta) vanish for every velocity field on the sphere, so they are not
+        unknowns: a right-hand side built by interpolation (Eq. 7) can carry a small
+        spurious mean, which is projected out here.
+        """
+        R = tuple(x.copy() for x in R)
+        R[1][0, 0] = 0.0
+        R[2][0, 0] = 0.0
         bands = self._band_matrices(alpha)
         M = self.M
         X = [np.zeros_like(R[0]) for _ in range(3)]
