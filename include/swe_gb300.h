@@ -184,6 +184,42 @@ swe_status parareal_iterate(swe_pint_t p, int kmax, double tol, int* k_done,
  * [S+1][3][NC]). */
 swe_status swe_pint_solution(swe_pint_t p, double* U_out, void* stream);
 
+/* MGRIT (§3.2): L levels, coarsening factor cf (Delta t_{l+1} = cf Delta t_l), F(CF)^nu
+ * relaxation, full approximation scheme with injection at C-points, spectral
+ * truncation / zero padding between the levels' truncations (level l+1 may be coarser
+ * in space), and either V-cycles or F-cycles followed by one V-cycle per level
+ * (§3.2.3).  step[l] is ONE time step of level l (nsteps is ignored).  On the coarsest
+ * level the two-step SL-SI-SETTLS scheme keeps its previous state (the serial coarse
+ * solve); relaxations and restriction steps use the one-step form (§3.2.4).
+ * N0 level-0 steps must be divisible by cf^(L-1).  All time points of all levels live in
+ * device memory. */
+typedef struct swe_mgrit* swe_mgrit_t;
+typedef struct {
+    int L;                       /* number of levels, 2..8 */
+    int cf;                      /* coarsening factor >= 2 */
+    int nu;                      /* number of CF relaxations after the first F relaxation */
+    int N0;                      /* level-0 time steps */
+    int cycle;                   /* 0: V-cycle, 1: F-cycle + one V-cycle */
+    swe_plan_t plan[8];          /* spatial plan of each level (truncation non-increasing) */
+    swe_stepper_desc step[8];    /* one step of each level: scheme, dt, viscosity */
+} swe_mgrit_desc;
+
+swe_status swe_mgrit_create(const swe_mgrit_desc* desc, swe_mgrit_t* out);
+swe_status swe_mgrit_destroy(swe_mgrit_t g);
+/* Sets U_0 (device, [3][NC_0]) and builds the initial guess: serial propagation on the
+ * coarsest level, injected to every finer level followed by F-relaxation. */
+swe_status swe_mgrit_init(swe_mgrit_t g, const double* U0, void* stream);
+/* Runs up to ncycles MGRIT iterations; after each, the FP64 per-field norm
+ * max_i ||u_{cf i} - u_{cf i}^{prev}||_inf / max_i ||u_{cf i}||_inf over the level-0
+ * C-points goes to norm_hist_host[k] (HOST, may be NULL); stops when it is below tol
+ * (tol <= 0: never).  *k_done (HOST) = cycles run.  Synchronises once per cycle.
+ * Returns SWE_EUNSTABLE if a non-finite value appeared. */
+swe_status mgrit_cycle(swe_mgrit_t g, int ncycles, double tol, int* k_done, double* norm_hist_host,
+                       void* stream);
+/* Copies the level-0 C-point values u_{cf i}, i = 0..N0/cf, into U_out ([N0/cf+1][3][NC_0],
+ * host or device). */
+swe_status swe_mgrit_cpoints(swe_mgrit_t g, double* U_out, void* stream);
+
 /* Checkpoint / resume of the Parareal state: the iterate U^k_n, n = 0..S
  * ([S+1][3][NC]) and the coarse results phi_c(U^k_n), n = 0..S-1 ([S][3][NC]),
  * which is all the next iteration needs.  U and Gold may be HOST (pageable or

@@ -65,6 +65,27 @@ __global__ void k_soa_aos(const double2* __restrict__ in, double2* __restrict__ 
     out[t] = in[fr * S + s];
 }
 
+// strided variants: state s lives at in + s * stride (stride in complex values)
+__global__ void k_aos_soa_strided(const double2* __restrict__ in, int64_t stride, double2* __restrict__ out,
+                                  int64_t nc, int S) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= 3 * nc * S) return;
+    int s = (int)(t % S);
+    int64_t fr = t / S;
+    out[t] = in[(int64_t)s * stride + fr];
+}
+
+__global__ void k_soa_aos_strided(const double2* __restrict__ in, double2* __restrict__ out, int64_t stride,
+                                  const double2* __restrict__ add, int64_t add_stride, int64_t nc, int S) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= 3 * nc * S) return;
+    int64_t fr = t % (3 * nc);
+    int s = (int)(t / (3 * nc));
+    double2 v = in[fr * S + s];
+    if (add) v = c_add(v, add[(int64_t)s * add_stride + fr]);
+    out[(int64_t)s * stride + fr] = v;
+}
+
 __global__ void k_pack(const double2* __restrict__ spec, double2* __restrict__ X, const int* __restrict__ row_m, int M,
                        int64_t nc, int64_t ncx, int B) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -495,5 +516,19 @@ swe_status k_axpy(double2* y, const double2* x, double a, int64_t n, cudaStream_
 swe_status k_truncate(const double2* in, int Min, double2* out, int Mout, int S, cudaStream_t st) {
     k_trunc<<<nblk(3 * nc_state(Mout) * S), 256, 0, st>>>(in, Min, out, Mout, S);
     SWE_CHECK_LAUNCH("k_trunc");
+    return SWE_OK;
+}
+
+swe_status k_aos_to_soa_strided(const swe_plan* p, const double2* in, int64_t stride, double2* out, int S,
+                                cudaStream_t st) {
+    k_aos_soa_strided<<<nblk(3 * p->nc * S), 256, 0, st>>>(in, stride, out, p->nc, S);
+    SWE_CHECK_LAUNCH("k_aos_soa_strided");
+    return SWE_OK;
+}
+
+swe_status k_soa_to_aos_strided(const swe_plan* p, const double2* in, double2* out, int64_t stride, const double2* add,
+                                int64_t add_stride, int S, cudaStream_t st) {
+    k_soa_aos_strided<<<nblk(3 * p->nc * S), 256, 0, st>>>(in, out, stride, add, add_stride, p->nc, S);
+    SWE_CHECK_LAUNCH("k_soa_aos_strided");
     return SWE_OK;
 }

@@ -167,6 +167,28 @@ static swe_status propagate_impl(swe_plan* p, const swe_stepper_desc* sd, const 
     return SWE_OK;
 }
 
+swe_status propagate_strided(swe_plan* p, const swe_stepper_desc* sd, const double2* in, int64_t in_stride,
+                             double2* out, int64_t out_stride, const double2* add, int64_t add_stride, int S,
+                             cudaStream_t st) {
+    SWE_CHECK(check_stepper(sd));
+    if (S < 1) return SWE_OK;
+    const int cols = chunk_cols(p, S);
+    const size_t sb = state_bytes(p, cols);
+    char* ws;
+    SWE_CHECK(plan_workspace(p, sb + stepper_bytes(p, cols), &ws));
+    double2* Ut = (double2*)ws;
+    char* sws = ws + sb;
+    const int64_t per = 3 * p->nc;
+    for (int s0 = 0; s0 < S; s0 += cols) {
+        const int c = (S - s0) < cols ? (S - s0) : cols;
+        SWE_CHECK(k_aos_to_soa_strided(p, in + per * in_stride * s0, per * in_stride, Ut, c, st));
+        SWE_CHECK(run_soa(p, sd, Ut, c, sws, st));
+        SWE_CHECK(k_soa_to_aos_strided(p, Ut, out + per * out_stride * s0, per * out_stride,
+                                       add ? add + per * add_stride * s0 : nullptr, per * add_stride, c, st));
+    }
+    return SWE_OK;
+}
+
 extern "C" swe_status propagate_F(swe_plan_t p, const swe_stepper_desc* sd, const double* U_in, double* U_out, int S,
                                   void* stream) {
     if (!p) {

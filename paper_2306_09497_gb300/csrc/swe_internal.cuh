@@ -127,6 +127,11 @@ swe_status ring_nonlinear(const swe_plan* p, const void* Fin, void* Fout, int S,
 swe_status k_aos_to_soa(const swe_plan* p, const double2* in, double2* out, int S, cudaStream_t st);
 swe_status k_soa_to_aos(const swe_plan* p, const double2* in, double2* out, int S, cudaStream_t st);
 
+swe_status k_aos_to_soa_strided(const swe_plan* p, const double2* in, int64_t stride, double2* out, int S,
+                                cudaStream_t st);
+swe_status k_soa_to_aos_strided(const swe_plan* p, const double2* in, double2* out, int64_t stride, const double2* add,
+                                int64_t add_stride, int S, cudaStream_t st);
+
 // scalar spectral [B][NC] <-> transform operand [ncx][B]
 swe_status k_pack_scalar(const swe_plan* p, const double2* spec, double2* X, int B, cudaStream_t st);
 swe_status k_unpack_scalar(const swe_plan* p, const double2* Y, double2* spec, int B, cudaStream_t st);
@@ -162,5 +167,10 @@ swe_status sl_step(swe_plan* p, double dt, double nu, int q, const double2* Upre
 // stepper (stepper.cu), SoA state with S columns; U updated in place
 swe_status stepper_run(swe_plan* p, const swe_stepper_desc* sd, double2* U, int S, cudaStream_t st);
 size_t stepper_bytes(const swe_plan* p, int S);
+// S states at in + s*in_stride (AoS, strides in states) advanced by sd; written to out + s*out_stride,
+// plus add + s*add_stride when add != nullptr.  in and out may alias with equal strides.
+swe_status propagate_strided(swe_plan* p, const swe_stepper_desc* sd, const double2* in, int64_t in_stride,
+                             double2* out, int64_t out_stride, const double2* add, int64_t add_stride, int S,
+                             cudaStream_t st);
 swe_status nonlinear_soa(swe_plan* p, const double2* Ua, const double2* Ub, double beta,
                          double2* N, int S, char* ws, cudaStream_t st);

@@ -26,7 +26,8 @@ EXPORTED = [
     "sht_inverse", "sht_forward", "swe_nonlinear", "swe_linear", "swe_implicit_solve", "swe_balance",
     "propagate_F", "propagate_G", "swe_pint_create", "swe_pint_destroy", "swe_pint_init", "parareal_iterate",
     "swe_pint_solution", "swe_pint_load", "swe_pint_save", "swe_launch_count", "swe_prof_enable",
-    "swe_prof_reset", "swe_prof_read", "sht_inverse_noalloc",
+    "swe_prof_reset", "swe_prof_read", "sht_inverse_noalloc", "swe_mgrit_create", "swe_mgrit_destroy",
+    "swe_mgrit_init", "mgrit_cycle", "swe_mgrit_cpoints",
 ]
 
 
@@ -49,6 +50,11 @@ class StepperDesc(ct.Structure):
 class PintDesc(ct.Structure):
     _fields_ = [("fine_plan", ct.c_void_p), ("coarse_plan", ct.c_void_p), ("fine", StepperDesc),
                 ("coarse", StepperDesc), ("S", ct.c_int), ("use_graphs", ct.c_int)]
+
+
+class MgritDesc(ct.Structure):
+    _fields_ = [("L", ct.c_int), ("cf", ct.c_int), ("nu", ct.c_int), ("N0", ct.c_int), ("cycle", ct.c_int),
+                ("plan", ct.c_void_p * 8), ("step", StepperDesc * 8)]
 
 
 _lib = None
@@ -92,6 +98,11 @@ def load(path: Optional[str] = None) -> ct.CDLL:
         "swe_prof_read": ([i, ct.c_char_p, i, ct.POINTER(ct.c_longlong), ct.POINTER(d), ct.POINTER(d),
                            ct.POINTER(d)], i),
         "sht_inverse_noalloc": ([vp, vp, vp, i, vp], i),
+        "swe_mgrit_create": ([ct.POINTER(MgritDesc), ct.POINTER(vp)], i),
+        "swe_mgrit_destroy": ([vp], i),
+        "swe_mgrit_init": ([vp, vp, vp], i),
+        "mgrit_cycle": ([vp, i, d, ct.POINTER(i), ct.POINTER(d), vp], i),
+        "swe_mgrit_cpoints": ([vp, vp, vp], i),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -239,6 +250,48 @@ class Parareal:
     def save_state(self, U, Gold=None, stream=None):
         """Checkpoint (U^k_n, phi_c(U^k_n)) into host or device arrays."""
         _check(load().swe_pint_save(self.h, _ptr(U), _ptr(Gold), _stream(stream)))
+
+
+class MGRIT:
+    """MGRIT over L levels (swe_mgrit_create / swe_mgrit_init / mgrit_cycle)."""
+
+    def __init__(self, plans, steps, N0: int, cf: int, nu: int = 0, cycle: int = 1):
+        L = len(plans)
+        assert len(steps) == L and 2 <= L <= 8
+        desc = MgritDesc()
+        desc.L, desc.cf, desc.nu, desc.N0, desc.cycle = L, cf, nu, N0, cycle
+        for l in range(L):
+            desc.plan[l] = plans[l].h.value
+            desc.step[l] = steps[l]
+        self.plans, self.N0, self.cf = plans, N0, cf
+        h = ct.c_void_p()
+        _check(load().swe_mgrit_create(ct.byref(desc), ct.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().swe_mgrit_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, U0, stream=None):
+        _check(load().swe_mgrit_init(self.h, _ptr(U0), _stream(stream)))
+
+    def cycle(self, ncycles: int, tol: float = 0.0, stream=None):
+        k = ct.c_int(0)
+        hist = (ct.c_double * max(ncycles, 1))()
+        st = load().mgrit_cycle(self.h, ncycles, tol, ct.byref(k), hist, _stream(stream))
+        norms = [hist[i] for i in range(k.value)]
+        _check(st)
+        return k.value, norms
+
+    def cpoints(self, U_out, stream=None):
+        _check(load().swe_mgrit_cpoints(self.h, _ptr(U_out), _stream(stream)))
 
 
 def launch_count() -> int:
