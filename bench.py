@@ -1,7 +1,16 @@
 #!/usr/bin/env python3
 """Benchmark of the Parareal/MGRIT shallow-water hot path at T255 on GB300.
 
-Workload "t255_parareal_s128": T255 on the 384 x 768 Gaussian grid, 5 days split
+Default workload "t255_mgrit3_cf4" (the T255 MGRIT configuration): 5 days of T255 on the
+384 x 768 Gaussian grid in 7296 level-0 IMEX steps of 59.21 s; three MGRIT levels with
+coarsening factor 4 (F-cycle + one V-cycle, F-relaxation); levels 1 and 2 are
+SL-SI-SETTLS (one-step, and two-step on the serial coarsest level) at 236.8 s and
+947.4 s on T127 (192 x 384) with 2nd-order viscosity 1e7 m^2/s (the configured 1e5 m^2/s
+blows up on the coarse levels).  One bench step = one F-cycle; the metric counts the
+level-0 IMEX slice-steps it computes (12768 = relaxations + restriction residual steps)
+per second.
+
+Alternative workload "t255_parareal_s128" (--workload parareal): T255, 5 days split
 into S = 128 slices of 3375 s.  One bench step = one Parareal iteration (Eq. 9):
 the fine IMEX propagator (57 steps of 59.21 s, the level-0 step of the 5-day,
 7296-step problem) on all 128 slices at once, the serial coarse chain
@@ -44,7 +53,13 @@ NF = 57                           # fine steps per slice
 NC_STEPS, DTC = 6, 3375.0 / 6.0   # coarse steps per slice, 562.5 s
 NU_C, Q_C = 1.0e16, 4
 MC, NLATC, NLONC = 127, 192, 384  # coarse truncation (spatial coarsening)
-WORKLOAD = "t255_parareal_s128"
+WORKLOAD_PARAREAL = "t255_parareal_s128"
+WORKLOAD_MGRIT = "t255_mgrit3_cf4"
+# MGRIT (config with SL-SI-SETTLS coarse levels): 7296 level-0 IMEX steps over 5 days,
+# 3 levels, coarsening factor 4, F-cycle + V-cycle, F-relaxation; levels 1-2 SL-SI-SETTLS
+# (one-step / two-step) on T127 with 2nd-order viscosity 1e7 m^2/s (1e5 m^2/s blows up)
+N0_MG, CF_MG, NU_RELAX = 7296, 4, 0
+VISC_SL = (2, 1.0e7)
 METRIC = "SWE slice-steps/s at T255"
 FP64_PEAK_TFLOPS = 1.25           # nominal FP64 rate of GB300 (profiling recipe table)
 
@@ -160,8 +175,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "slice-steps/s", "n_gpus": 0,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v if v else None,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "M": M, "nlat": NLAT, "nlon": NLON, "slices": S, "fine_steps": NF,
-                   "fine_dt": DT0},
+        "config": config_of(args),
         "cpu_baseline": {"value": v, "unit": "slice-steps/s", "cores": 1, "kind": "oracle",
                          "sample": f"serial FP64 oracle IMEX steps on one T255 slice, ~{per:.0f} s per bench step"},
         "e2e": {"value": v, "unit": "slice-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -170,8 +184,8 @@ def run_reference(args):
     return 0
 
 
-def measure(args, prec_name, rank, world, local, with_e2e=True):
-    """One precision: warm-up, timed Parareal iterations, optional host-buffer e2e leg."""
+def _build(args, prec_name, rank, local):
+    """Plans, initial state and the iteration object of the selected workload."""
     import numpy as np
     import torch
 
@@ -181,17 +195,42 @@ def measure(args, prec_name, rank, world, local, with_e2e=True):
     prec = swe.SWE_FP64 if prec_name == "fp64" else swe.SWE_SPLIT_BF16X3
     plan = swe.Plan(M, NLAT, NLON, prec=prec)
     cplan = swe.Plan(MC, NLATC, NLONC, prec=prec)
-    fine = swe.stepper(swe.SWE_IMEX, DT0, NF)
-    coarse = swe.stepper(swe.SWE_IMEX, DTC, NC_STEPS, Q_C, NU_C)
     xi, noise = inputs.initial_fields(M, 3 + rank)
     xi_d = torch.from_numpy(xi.view(np.float64).copy()).to(dev)
     nz_d = torch.from_numpy(noise.view(np.float64).copy()).to(dev)
     U0 = torch.empty(1, 3, plan.nc * 2, dtype=torch.float64, device=dev)
     plan.balance(xi_d, nz_d, U0, 1)
-    pr = swe.Parareal(plan, cplan, fine, coarse, S, use_graphs=True)
-    pr.init(U0)
+    if args.workload == "parareal":
+        fine = swe.stepper(swe.SWE_IMEX, DT0, NF)
+        coarse = swe.stepper(swe.SWE_IMEX, DTC, NC_STEPS, Q_C, NU_C)
+        it = swe.Parareal(plan, cplan, fine, coarse, S, use_graphs=True)
+        it.init(U0)
+        fine_steps = S * NF
+        step_fn = lambda: it.iterate(1)[1]
+    else:
+        steps = [swe.stepper(swe.SWE_IMEX, DT0, 1),
+                 swe.stepper(swe.SWE_SLSI_SETTLS_1STEP, CF_MG * DT0, 1, VISC_SL[0], VISC_SL[1]),
+                 swe.stepper(swe.SWE_SLSI_SETTLS, CF_MG * CF_MG * DT0, 1, VISC_SL[0], VISC_SL[1])]
+        it = swe.MGRIT([plan, cplan, cplan], steps, N0_MG, CF_MG, NU_RELAX, cycle=1)
+        it.init(U0)
+        nc_pts = N0_MG // CF_MG
+        # level-0 steps computed by one F-cycle: F-relaxation before and after the coarse
+        # correction ((cf-1) Nc each) + the residual steps of the restriction (Nc)
+        fine_steps = (2 * (CF_MG - 1) * (1 + NU_RELAX) + 1 + 2 * NU_RELAX) * nc_pts
+        step_fn = lambda: it.cycle(1)[1]
+    return plan, cplan, it, fine_steps, step_fn
+
+
+def measure(args, prec_name, rank, world, local, with_e2e=True):
+    """One precision: warm-up, timed iterations, optional host-buffer e2e leg."""
+    import torch
+
+    from paper_2306_09497_gb300 import swe
+
+    dev = torch.device("cuda", local)
+    plan, cplan, it, fine_steps, step_fn = _build(args, prec_name, rank, local)
     for _ in range(args.warmup):
-        pr.iterate(1)
+        step_fn()
     torch.cuda.synchronize()
 
     def barrier():
@@ -210,8 +249,7 @@ def measure(args, prec_name, rank, world, local, with_e2e=True):
     e0.record(stream)
     norms = []
     for _ in range(args.steps):
-        _, nh = pr.iterate(1)
-        norms += nh
+        norms += step_fn()
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -224,32 +262,53 @@ def measure(args, prec_name, rank, world, local, with_e2e=True):
         t = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
-    res = {"ms": ms, "value": world * S * NF / (ms / 1000.0), "launches": launches, "stats": stats,
-           "clocks": clk, "norms": norms}
+    res = {"ms": ms, "value": world * fine_steps / (ms / 1000.0), "launches": launches, "stats": stats,
+           "clocks": clk, "norms": norms, "fine_steps": fine_steps,
+           "problem_steps_per_s": world * (S * NF if args.workload == "parareal" else N0_MG) / (ms / 1000.0)}
     if with_e2e:
-        # end to end through the public API with host buffers: load the Parareal state
-        # from pinned host memory, iterate, save it back to host memory
-        per_state = 3 * plan.nc * 2
-        U_h = torch.empty((S + 1) * per_state, dtype=torch.float64, pin_memory=True)
-        G_h = torch.empty(S * per_state, dtype=torch.float64, pin_memory=True)
-        pr.save_state(U_h, G_h)
+        # end to end through the public API with host buffers: the iteration's state
+        # comes from pinned host memory and its result goes back to host memory
+        if args.workload == "parareal":
+            per_state = 3 * plan.nc * 2
+            U_h = torch.empty((S + 1) * per_state, dtype=torch.float64, pin_memory=True)
+            G_h = torch.empty(S * per_state, dtype=torch.float64, pin_memory=True)
+            it.save_state(U_h, G_h)
+            nbytes_in = nbytes_out = (U_h.numel() + G_h.numel()) * 8
+
+            def e2e_step():
+                it.load_state(U_h, G_h)
+                it.iterate(1)
+                it.save_state(U_h, G_h)
+        else:
+            U0_h = torch.empty(3 * plan.nc * 2, dtype=torch.float64, pin_memory=True)
+            U0_d = torch.empty(3 * plan.nc * 2, dtype=torch.float64, device=dev)
+            C_h = torch.empty((N0_MG // CF_MG + 1) * 3 * plan.nc * 2, dtype=torch.float64, pin_memory=True)
+            it.cpoints(C_h)
+            U0_h.copy_(C_h[: 3 * plan.nc * 2])
+            nbytes_in = U0_h.numel() * 8
+            nbytes_out = C_h.numel() * 8
+
+            def e2e_step():
+                U0_d.copy_(U0_h, non_blocking=True)
+                it.init(U0_d)
+                it.cycle(1)
+                it.cpoints(C_h)
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            pr.load_state(U_h, G_h)
-            pr.iterate(1)
-            pr.save_state(U_h, G_h)
+            e2e_step()
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.steps
         if world > 1:
             t = torch.tensor([e2e_s], device=dev)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             e2e_s = float(t.item())
-        res["e2e"] = {"value": world * S * NF / e2e_s, "unit": "slice-steps/s",
-                      "h2d_bytes_per_step": (U_h.numel() + G_h.numel()) * 8,
-                      "d2h_bytes_per_step": (U_h.numel() + G_h.numel()) * 8}
-    pr.close()
+        res["e2e"] = {"value": world * fine_steps / e2e_s, "unit": "slice-steps/s",
+                      "h2d_bytes_per_step": nbytes_in, "d2h_bytes_per_step": nbytes_out}
+        if args.workload != "parareal":
+            res["e2e"]["note"] = "each step re-initialises MGRIT from the host initial state and runs one F-cycle"
+    it.close()
     plan.close()
     cplan.close()
     return res
@@ -287,6 +346,17 @@ def roofline(stats):
     return roof
 
 
+def config_of(args):
+    if args.workload == "parareal":
+        return {"workload": WORKLOAD_PARAREAL, "M": M, "nlat": NLAT, "nlon": NLON, "slices": S, "fine_steps": NF,
+                "fine_dt": DT0, "coarse_M": MC, "coarse_grid": [NLATC, NLONC], "coarse_steps": NC_STEPS,
+                "coarse_dt": DTC, "coarse_visc": [Q_C, NU_C], "method": "parareal"}
+    return {"workload": WORKLOAD_MGRIT, "M": M, "nlat": NLAT, "nlon": NLON, "N0": N0_MG, "cf": CF_MG, "levels": 3,
+            "nu_relax": NU_RELAX, "cycle": "F-cycle + V-cycle", "fine": "IMEX dt=%.4f s" % DT0,
+            "coarse": "SL-SI-SETTLS (1-step level 1, 2-step level 2) on T%d %dx%d" % (MC, NLATC, NLONC),
+            "coarse_visc": list(VISC_SL), "method": "mgrit"}
+
+
 def run_ours(args):
     import torch
 
@@ -303,16 +373,15 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f64" if main_prec == "fp64" else "mixed: bf16 split x6 tensor GEMM, f32 FFT/grid, f64 state",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "M": M, "nlat": NLAT, "nlon": NLON, "slices": S, "fine_steps": NF,
-                   "fine_dt": DT0, "coarse_M": MC, "coarse_grid": [NLATC, NLONC], "coarse_steps": NC_STEPS,
-                   "coarse_dt": DTC, "coarse_visc": [Q_C, NU_C],
-                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                   "l2": "working set > L2 (no flush)", "precision": main_prec},
+        "config": dict(config_of(args), parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
+                       l2="working set > L2 (no flush)", precision=main_prec),
         "e2e": r["e2e"],
         "gpu_launches": r["launches"],
         "roofline": roofline(r["stats"]),
         "clocks": r["clocks"],
         "convergence_norms": r["norms"],
+        "fine_steps_per_iteration": r["fine_steps"],
+        "problem_steps_per_s": r["problem_steps_per_s"],
     }
     if main_prec == "mixed" and not args.no_fp64:
         f = measure(args, "fp64", rank, world, local, with_e2e=False)
@@ -343,6 +412,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--workload", default="mgrit", choices=["mgrit", "parareal"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain comparison run")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
