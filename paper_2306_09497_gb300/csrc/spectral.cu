@@ -362,6 +362,108 @@ __global__ void k_cn_solve(const double2* __restrict__ fac, const double2* R, do
     }
 }
 
+// Warp-parallel form of the same solve, for small batches: one warp per (m, parity, slice).
+// Both recurrences are affine, x_k = A_k x_{k-1} + B_k (forward elimination with
+// A = -a_k g_k, B = rhs_k g_k; back substitution, walked from the top degree down, with
+// A = -c'_k, B = d'_k), so each 32-element chunk is an inclusive scan of the maps
+// (A, B) under composition (A2 A1, A2 B1 + B2), continued from the previous chunk's value.
+__device__ __forceinline__ double2 shfl_up2(double2 v, int d) {
+    return make_double2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+}
+
+__device__ __forceinline__ void affine_scan(double2& A, double2& B) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        double2 Ap = shfl_up2(A, d), Bp = shfl_up2(B, d);
+        if (lane >= d) {
+            B = c_add(c_mul(A, Bp), B);
+            A = c_mul(A, Ap);
+        }
+    }
+}
+
+__global__ void k_cn_solve_warp(const double2* __restrict__ fac, const double2* R, double2* X, int M, int64_t nc,
+                                int S, double vdt, double vnu, int vq, double a) {
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= (int64_t)2 * (M + 1) * S) return;          // whole warps exit together
+    const int s = (int)(w % S);
+    const int mp = (int)(w / S);
+    const int m = mp >> 1, par = mp & 1;
+    const int64_t base = st_off(m, M);
+    auto idx = [&](int f, int n) { return ((int64_t)f * nc + base + (n - m)) * S + s; };
+    auto rxi = [&](int n) -> double2 {
+        if (n < m || n > M || n == 0) return czero();
+        return R[idx(1, n)];
+    };
+    const int n0 = m + par;
+    const int K = (n0 <= M) ? (M - n0) / 2 + 1 : 0;
+    // forward elimination: d'_k into X[delta]
+    double2 carry = czero();
+    for (int k0 = 0; k0 < K; k0 += 32) {
+        const int k = k0 + lane;
+        double2 A = czero(), B = czero();
+        if (k < K) {
+            const int n = n0 + 2 * k;
+            const double2* f = fac + (base + (n - m)) * 8;
+            double2 rhs = c_add((n == 0) ? czero() : R[idx(2, n)], c_scale(R[idx(0, n)], f[7].x));
+            rhs = c_add(rhs, c_mul(f[3], rxi(n - 1)));
+            rhs = c_add(rhs, c_mul(f[4], rxi(n + 1)));
+            A = c_scale(c_mul(f[0], f[1]), -1.0);
+            B = c_mul(rhs, f[1]);
+        }
+        affine_scan(A, B);
+        const double2 v = c_add(c_mul(A, carry), B);
+        __syncwarp();
+        if (k < K) X[idx(2, n0 + 2 * k)] = v;
+        carry = make_double2(__shfl_sync(0xffffffffu, v.x, 31), __shfl_sync(0xffffffffu, v.y, 31));
+    }
+    __syncwarp();
+    // back substitution from the top: delta_k = -c'_k delta_{k+1} + d'_k; then Phi
+    carry = czero();
+    for (int k0 = 0; k0 < K; k0 += 32) {
+        const int k = K - 1 - (k0 + lane);
+        double2 A = czero(), B = czero();
+        if (k >= 0) {
+            const int n = n0 + 2 * k;
+            const double2* f = fac + (base + (n - m)) * 8;
+            A = c_scale(f[2], -1.0);
+            B = X[idx(2, n)];
+        }
+        affine_scan(A, B);
+        double2 dn = c_add(c_mul(A, carry), B);
+        carry = make_double2(__shfl_sync(0xffffffffu, dn.x, 31), __shfl_sync(0xffffffffu, dn.y, 31));
+        __syncwarp();
+        if (k >= 0) {
+            const int n = n0 + 2 * k;
+            if (n == 0) dn = czero();
+            const double2* f = fac + (base + (n - m)) * 8;
+            const double2 ph = c_sub(R[idx(0, n)], c_scale(dn, f[7].y));
+            X[idx(2, n)] = dn;
+            X[idx(0, n)] = ph;
+        }
+    }
+    __syncwarp();
+    // xi on the other parity (uses the unscaled delta)
+    for (int n = m + (par ^ 1) + 2 * lane; n <= M; n += 64) {
+        const double2* f = fac + (base + (n - m)) * 8;
+        double2 dm = (n - 1 >= m) ? X[idx(2, n - 1)] : czero();
+        double2 dpv = (n + 1 <= M) ? X[idx(2, n + 1)] : czero();
+        double2 num = c_sub(rxi(n), c_add(c_scale(dm, f[6].x), c_scale(dpv, f[6].y)));
+        double2 xn = (n == 0) ? czero() : c_mul(num, f[5]);
+        X[idx(1, n)] = c_scale(xn, visc_factor(n, vdt, vnu, vq, a));
+    }
+    __syncwarp();
+    if (vnu > 0.0) {
+        for (int n = n0 + 2 * lane; n <= M; n += 64) {
+            const double v = visc_factor(n, vdt, vnu, vq, a);
+            X[idx(2, n)] = c_scale(X[idx(2, n)], v);
+            X[idx(0, n)] = c_scale(X[idx(0, n)], v);
+        }
+    }
+}
+
 __global__ void k_balance(const double2* __restrict__ xi, const double2* __restrict__ N,
                           const double2* __restrict__ add, double2* __restrict__ U, const int* __restrict__ srow_m,
                           int M, int64_t nc, int S, double a, double omega) {
@@ -493,8 +595,14 @@ swe_status k_implicit(swe_plan* p, double alpha, int with_rhs, const double2* in
     }
     // algorithmic traffic: R (3 fields) + factors read, X written
     ProfToken tk = prof_begin("cn_solve", st, 0.0, 16.0 * p->nc * (6.0 * S + 8.0));
-    k_cn_solve<<<nblk((int64_t)2 * (p->M + 1) * S, 128), 128, 0, st>>>(fac, R, out, p->M, p->nc, S, visc_dt, visc_nu,
-                                                                    visc_q, p->a);
+    if (S <= 4) {
+        // small batches (serial coarse chains): one warp per (m, parity, slice), scan-based
+        k_cn_solve_warp<<<nblk((int64_t)2 * (p->M + 1) * S * 32, 128), 128, 0, st>>>(fac, R, out, p->M, p->nc, S,
+                                                                                  visc_dt, visc_nu, visc_q, p->a);
+    } else {
+        k_cn_solve<<<nblk((int64_t)2 * (p->M + 1) * S, 128), 128, 0, st>>>(fac, R, out, p->M, p->nc, S, visc_dt,
+                                                                        visc_nu, visc_q, p->a);
+    }
     prof_end(tk, st);
     SWE_CHECK_LAUNCH("k_cn_solve");
     return SWE_OK;
