@@ -19,8 +19,8 @@
 namespace {
 
 template <typename T> struct CT;
-template <> struct CT<double> { using V = double2; };
-template <> struct CT<float> { using V = float2; };
+template <> struct CT<double> { using V = double2; static constexpr int threads = 256; };
+template <> struct CT<float> { using V = float2; static constexpr int threads = 512; };
 
 template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return V{a.x + b.x, a.y + b.y}; }
 template <typename V> __device__ __forceinline__ V csub(V a, V b) { return V{a.x - b.x, a.y - b.y}; }
@@ -151,6 +151,143 @@ __device__ __forceinline__ V r2c_mode(const V* Z, int H, int k, const V* twN, T 
     return V{(T)0.5 * (s1.x + t.x) * scale, (T)0.5 * (s1.y + t.y) * scale};
 }
 
+// In-place Stockham pass: every thread first loads the inputs of all its butterflies
+// (at most W of them) into registers, the block synchronises, and the outputs are
+// written back into the same buffer.  Needs nfft * N / R <= W * blockDim.x.
+template <typename T, int S, int R, int W>
+__device__ __forceinline__ void fft_pass_inplace(typename CT<T>::V* __restrict__ x, int N, int Ns,
+                                                 const typename CT<T>::V* __restrict__ tw, int tws, int nfft) {
+    using V = typename CT<T>::V;
+    const int nb = N / R;
+    const int tstep = N / (Ns * R);
+    const int total = nb * nfft;
+    V v[W][R];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const int t = threadIdx.x + w * blockDim.x;
+        if (t < total) {
+            const int f = t / nb, j = t - f * nb;
+            const V* xs = x + (int64_t)f * N;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[w][r] = xs[j + r * nb];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const int t = threadIdx.x + w * blockDim.x;
+        if (t < total) {
+            const int f = t / nb, j = t - f * nb;
+            const int k = j % Ns;
+            const int idx = (j / Ns) * Ns * R + k;
+            V* y = x + (int64_t)f * N;
+            if (k) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    V wr = tw[((r * k * tstep) % N) * tws];
+                    if (S > 0) wr = cconj(wr);
+                    v[w][r] = cmul(v[w][r], wr);
+                }
+            }
+            if (R == 2) {
+                y[idx] = cadd(v[w][0], v[w][1]);
+                y[idx + Ns] = csub(v[w][0], v[w][1]);
+            } else if (R == 3) {
+                const T h = (T)0.86602540378443864676;
+                V t1 = cadd(v[w][1], v[w][2]), t2 = csub(v[w][1], v[w][2]);
+                V a = V{v[w][0].x - (T)0.5 * t1.x, v[w][0].y - (T)0.5 * t1.y};
+                V b = cmul_si<S>(V{h * t2.x, h * t2.y});
+                y[idx] = cadd(v[w][0], t1);
+                y[idx + Ns] = cadd(a, b);
+                y[idx + 2 * Ns] = csub(a, b);
+            } else {
+                V a0 = cadd(v[w][0], v[w][2]), a1 = csub(v[w][0], v[w][2]);
+                V b0 = cadd(v[w][1], v[w][3]), b1 = cmul_si<S>(csub(v[w][1], v[w][3]));
+                y[idx] = cadd(a0, b0);
+                y[idx + Ns] = cadd(a1, b1);
+                y[idx + 2 * Ns] = csub(a0, b0);
+                y[idx + 3 * Ns] = csub(a1, b1);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T, int S>
+__device__ __forceinline__ void fft_inplace(typename CT<T>::V* x, const FFTPlan& fp, const typename CT<T>::V* tw,
+                                            int nfft) {
+    int Ns = 1;
+    for (int p = 0; p < fp.nrad; ++p) {
+        const int R = fp.rad[p];
+        if (R == 4) fft_pass_inplace<T, S, 4, 4>(x, fp.n, Ns, tw, fp.tws, nfft);
+        else if (R == 3) fft_pass_inplace<T, S, 3, 6>(x, fp.n, Ns, tw, fp.tws, nfft);
+        else fft_pass_inplace<T, S, 2, 8>(x, fp.n, Ns, tw, fp.tws, nfft);
+        Ns *= R;
+    }
+}
+
+// Grouped fused nonlinear ring: one latitude j, G consecutive slices per block (every
+// (field, m) access touches G contiguous columns).  Shared memory: G x 5 sequences of H.
+template <typename T>
+__global__ void __launch_bounds__(CT<T>::threads) k_ring_nl_g(const typename CT<T>::V* __restrict__ Fin,
+                                                   typename CT<T>::V* __restrict__ Fout, int M, int nlat, int S, int G,
+                                                   FFTPlan fp, const typename CT<T>::V* __restrict__ tw,
+                                                   const double* __restrict__ mu, const double* __restrict__ w) {
+    using V = typename CT<T>::V;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int H = fp.n;
+    V* d = reinterpret_cast<V*>(smem_raw);      // [g][5][H]
+    const int s0 = blockIdx.x * G;
+    const int Gv = min(G, S - s0);
+    const int j = blockIdx.y;
+    for (int k = threadIdx.x; k < G * 5 * H; k += blockDim.x) d[k] = V{0, 0};
+    __syncthreads();
+    const int64_t C4 = 4 * (int64_t)S;
+    for (int t = threadIdx.x; t < 4 * (M + 1) * G; t += blockDim.x) {
+        const int g = t % G;
+        const int fm = t / G;
+        const int f = fm / (M + 1), m = fm - f * (M + 1);
+        if (g < Gv) {
+            V x = Fin[((int64_t)m * nlat + j) * C4 + (int64_t)f * S + s0 + g];
+            if (m == 0) x.y = 0;
+            d[(g * 5 + f) * H + m] = x;
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 4 * G * (H / 2 + 1); t += blockDim.x) {
+        const int q = t / (H / 2 + 1), k = t - q * (H / 2 + 1);
+        const int g = q / 4, f = q - g * 4;
+        c2r_prepare(d + (g * 5 + f) * H, H, k, tw);
+    }
+    __syncthreads();
+    // inverse FFTs of the 4 input sequences of every slice: run over all 5G sequences
+    // (the fifth of each slice is zero and unused)
+    fft_inplace<T, +1>(d, fp, tw, 5 * G);
+    const double muj = mu[j];
+    const T ic2 = (T)(1.0 / ((1.0 - muj) * (1.0 + muj)));
+    for (int t = threadIdx.x; t < G * H; t += blockDim.x) {
+        const int g = t / H, n = t - g * H;
+        V* b = d + (g * 5) * H;
+        V ph = b[n], xi = b[H + n], U = b[2 * H + n], Vv = b[3 * H + n];
+        b[n] = V{xi.x * U.x * ic2, xi.y * U.y * ic2};
+        b[H + n] = V{xi.x * Vv.x * ic2, xi.y * Vv.y * ic2};
+        b[2 * H + n] = V{ph.x * U.x * ic2, ph.y * U.y * ic2};
+        b[3 * H + n] = V{ph.x * Vv.x * ic2, ph.y * Vv.y * ic2};
+        b[4 * H + n] = V{(T)0.5 * (U.x * U.x + Vv.x * Vv.x) * ic2, (T)0.5 * (U.y * U.y + Vv.y * Vv.y) * ic2};
+    }
+    __syncthreads();
+    fft_inplace<T, -1>(d, fp, tw, 5 * G);
+    const T scale = (T)(w[j] / (double)(2 * H));
+    const int64_t C5 = 5 * (int64_t)S;
+    for (int t = threadIdx.x; t < 5 * (M + 1) * G; t += blockDim.x) {
+        const int g = t % G;
+        const int fm = t / G;
+        const int f = fm / (M + 1), m = fm - f * (M + 1);
+        if (g < Gv)
+            Fout[((int64_t)m * nlat + j) * C5 + (int64_t)f * S + s0 + g] = r2c_mode<T>(d + (g * 5 + f) * H, H, m, tw, scale);
+    }
+}
+
 constexpr int RING_G = 4;   // columns per block in the plain transforms
 
 // ---------------------------------------------------------------------------
@@ -168,7 +305,7 @@ __global__ void __launch_bounds__(256) k_ring_inv(const typename CT<T>::V* __res
     for (int k = threadIdx.x; k < RING_G * H; k += blockDim.x) a[k] = V{0, 0};
     __syncthreads();
     for (int t = threadIdx.x; t < G * (M + 1); t += blockDim.x) {
-        int g = t / (M + 1), m = t - g * (M + 1);
+        int m = t / G, g = t - m * G;                 // columns fastest: contiguous loads
         V x = F[((int64_t)m * nlat + j) * C + c0 + g];
         if (m == 0) x.y = 0;
         a[g * H + m] = x;
@@ -214,7 +351,7 @@ __global__ void __launch_bounds__(256) k_ring_fwd(const T* __restrict__ grid, ty
     V* r = fft_block<T, -1>(a, b, fp, tw, RING_G, H);
     const T scale = (T)(w[j] / (double)(2 * H));
     for (int t = threadIdx.x; t < G * (M + 1); t += blockDim.x) {
-        int g = t / (M + 1), m = t - g * (M + 1);
+        int m = t / G, g = t - m * G;                 // columns fastest: contiguous stores
         F[((int64_t)m * nlat + j) * C + c0 + g] = r2c_mode<T>(r + g * H, H, m, tw, scale);
     }
 }
@@ -323,25 +460,31 @@ swe_status ring_forward(const swe_plan* p, const void* grid, void* F, int C, cud
 
 swe_status ring_nonlinear(const swe_plan* p, const void* Fin, void* Fout, int S, cudaStream_t st) {
     FFTPlan fp = make_fft_plan(p);
-    dim3 g(S, p->nlat);
+    const bool f64 = (p->prec == SWE_FP64);
+    const int T = f64 ? CT<double>::threads : CT<float>::threads;
+    // slices per block: largest of 4, 2, 1 with 5 G H <= 16 T (register staging bound of the passes)
+    int G = 4;
+    while (G > 1 && 5 * G * fp.n > 16 * T) G >>= 1;
+    if (G > S) G = S < 4 ? (S < 2 ? 1 : 2) : G;
+    dim3 g((S + G - 1) / G, p->nlat);
     // algorithmic traffic: read 4 and write 5 Fourier rows of (M+1) modes per ring;
     // 9 real FFTs of length nlon (2.5 N log2 N each) + ~30 flops per grid point
-    const double fe = (p->prec == SWE_FP64) ? 16.0 : 8.0;
+    const double fe = f64 ? 16.0 : 8.0;
     const double by = fe * 9.0 * (p->M + 1.0) * p->nlat * S;
     const double fl = ((9.0 * 2.5 * log2((double)p->nlon)) + 30.0) * p->nlon * (double)p->nlat * S;
-    ProfToken tk = prof_begin(p->prec == SWE_FP64 ? "ring_nl_f64" : "ring_nl_f32", st, fl, by);
-    if (p->prec == SWE_FP64) {
-        size_t sm = 10 * sizeof(double2) * fp.n;
-        SWE_CHECK(set_smem(k_ring_nl<double>, sm));
-        k_ring_nl<double><<<g, 256, sm, st>>>((const double2*)Fin, (double2*)Fout, p->M, p->nlat, S, fp, p->tw, p->mu,
-                                              p->w);
+    ProfToken tk = prof_begin(f64 ? "ring_nl_f64" : "ring_nl_f32", st, fl, by);
+    if (f64) {
+        size_t sm = (size_t)G * 5 * sizeof(double2) * fp.n;
+        SWE_CHECK(set_smem(k_ring_nl_g<double>, sm));
+        k_ring_nl_g<double><<<g, T, sm, st>>>((const double2*)Fin, (double2*)Fout, p->M, p->nlat, S, G, fp, p->tw,
+                                              p->mu, p->w);
     } else {
-        size_t sm = 10 * sizeof(float2) * fp.n;
-        SWE_CHECK(set_smem(k_ring_nl<float>, sm));
-        k_ring_nl<float><<<g, 256, sm, st>>>((const float2*)Fin, (float2*)Fout, p->M, p->nlat, S, fp, p->twf, p->mu,
-                                             p->w);
+        size_t sm = (size_t)G * 5 * sizeof(float2) * fp.n;
+        SWE_CHECK(set_smem(k_ring_nl_g<float>, sm));
+        k_ring_nl_g<float><<<g, T, sm, st>>>((const float2*)Fin, (float2*)Fout, p->M, p->nlat, S, G, fp, p->twf,
+                                             p->mu, p->w);
     }
     prof_end(tk, st);
-    SWE_CHECK_LAUNCH("k_ring_nl");
+    SWE_CHECK_LAUNCH("k_ring_nl_g");
     return SWE_OK;
 }
