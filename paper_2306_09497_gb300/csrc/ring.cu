@@ -19,8 +19,8 @@
 namespace {
 
 template <typename T> struct CT;
-template <> struct CT<double> { using V = double2; static constexpr int threads = 256; };
-template <> struct CT<float> { using V = float2; static constexpr int threads = 512; };
+template <> struct CT<double> { using V = double2; };
+template <> struct CT<float> { using V = float2; };
 
 template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return V{a.x + b.x, a.y + b.y}; }
 template <typename V> __device__ __forceinline__ V csub(V a, V b) { return V{a.x - b.x, a.y - b.y}; }
@@ -213,23 +213,25 @@ __device__ __forceinline__ void fft_pass_inplace(typename CT<T>::V* __restrict__
     __syncthreads();
 }
 
-template <typename T, int S>
+// W = butterflies per thread for radix 4 (radix 3: 3W/2, radix 2: 2W)
+template <typename T, int S, int W>
 __device__ __forceinline__ void fft_inplace(typename CT<T>::V* x, const FFTPlan& fp, const typename CT<T>::V* tw,
                                             int nfft) {
     int Ns = 1;
     for (int p = 0; p < fp.nrad; ++p) {
         const int R = fp.rad[p];
-        if (R == 4) fft_pass_inplace<T, S, 4, 4>(x, fp.n, Ns, tw, fp.tws, nfft);
-        else if (R == 3) fft_pass_inplace<T, S, 3, 6>(x, fp.n, Ns, tw, fp.tws, nfft);
-        else fft_pass_inplace<T, S, 2, 8>(x, fp.n, Ns, tw, fp.tws, nfft);
+        if (R == 4) fft_pass_inplace<T, S, 4, W>(x, fp.n, Ns, tw, fp.tws, nfft);
+        else if (R == 3) fft_pass_inplace<T, S, 3, (3 * W + 1) / 2>(x, fp.n, Ns, tw, fp.tws, nfft);
+        else fft_pass_inplace<T, S, 2, 2 * W>(x, fp.n, Ns, tw, fp.tws, nfft);
         Ns *= R;
     }
 }
 
 // Grouped fused nonlinear ring: one latitude j, G consecutive slices per block (every
 // (field, m) access touches G contiguous columns).  Shared memory: G x 5 sequences of H.
-template <typename T>
-__global__ void __launch_bounds__(CT<T>::threads) k_ring_nl_g(const typename CT<T>::V* __restrict__ Fin,
+// NT threads, W radix-4 butterflies per thread and pass: requires 5 G H / 4 <= W NT.
+template <typename T, int NT, int W, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_ring_nl_g(const typename CT<T>::V* __restrict__ Fin,
                                                    typename CT<T>::V* __restrict__ Fout, int M, int nlat, int S, int G,
                                                    FFTPlan fp, const typename CT<T>::V* __restrict__ tw,
                                                    const double* __restrict__ mu, const double* __restrict__ w) {
@@ -262,7 +264,7 @@ __global__ void __launch_bounds__(CT<T>::threads) k_ring_nl_g(const typename CT<
     __syncthreads();
     // inverse FFTs of the 4 input sequences of every slice: run over all 5G sequences
     // (the fifth of each slice is zero and unused)
-    fft_inplace<T, +1>(d, fp, tw, 5 * G);
+    fft_inplace<T, +1, W>(d, fp, tw, 5 * G);
     const double muj = mu[j];
     const T ic2 = (T)(1.0 / ((1.0 - muj) * (1.0 + muj)));
     for (int t = threadIdx.x; t < G * H; t += blockDim.x) {
@@ -276,7 +278,7 @@ __global__ void __launch_bounds__(CT<T>::threads) k_ring_nl_g(const typename CT<
         b[4 * H + n] = V{(T)0.5 * (U.x * U.x + Vv.x * Vv.x) * ic2, (T)0.5 * (U.y * U.y + Vv.y * Vv.y) * ic2};
     }
     __syncthreads();
-    fft_inplace<T, -1>(d, fp, tw, 5 * G);
+    fft_inplace<T, -1, W>(d, fp, tw, 5 * G);
     const T scale = (T)(w[j] / (double)(2 * H));
     const int64_t C5 = 5 * (int64_t)S;
     for (int t = threadIdx.x; t < 5 * (M + 1) * G; t += blockDim.x) {
@@ -356,58 +358,6 @@ __global__ void __launch_bounds__(256) k_ring_fwd(const T* __restrict__ grid, ty
     }
 }
 
-// Fused nonlinear ring: Fin [M+1][nlat][4S] (Phi', xi, U, V), Fout [M+1][nlat][5S]
-// (A1 = xi U/c2, B1 = xi V/c2, A2 = Phi' U/c2, B2 = Phi' V/c2, KE = (U^2+V^2)/(2 c2)), c2 = 1 - mu^2.
-template <typename T>
-__global__ void __launch_bounds__(256) k_ring_nl(const typename CT<T>::V* __restrict__ Fin,
-                                                 typename CT<T>::V* __restrict__ Fout, int M, int nlat, int S,
-                                                 FFTPlan fp, const typename CT<T>::V* __restrict__ tw,
-                                                 const double* __restrict__ mu, const double* __restrict__ w) {
-    using V = typename CT<T>::V;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int H = fp.n;
-    V* d = reinterpret_cast<V*>(smem_raw);   // 5 sequences
-    V* sc = d + 5 * H;                        // 5 scratch sequences
-    const int s = blockIdx.x;
-    const int j = blockIdx.y;
-    for (int k = threadIdx.x; k < 4 * H; k += blockDim.x) d[k] = V{0, 0};
-    __syncthreads();
-    const int64_t C4 = 4 * (int64_t)S;
-    for (int t = threadIdx.x; t < 4 * (M + 1); t += blockDim.x) {
-        int f = t / (M + 1), m = t - f * (M + 1);
-        V x = Fin[((int64_t)m * nlat + j) * C4 + (int64_t)f * S + s];
-        if (m == 0) x.y = 0;
-        d[f * H + m] = x;
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < 4 * (H / 2 + 1); t += blockDim.x) {
-        int f = t / (H / 2 + 1), k = t - f * (H / 2 + 1);
-        c2r_prepare(d + f * H, H, k, tw);
-    }
-    __syncthreads();
-    V* r = fft_block<T, +1>(d, sc, fp, tw, 4, H);
-    const double muj = mu[j];
-    const T ic2 = (T)(1.0 / ((1.0 - muj) * (1.0 + muj)));
-    for (int n = threadIdx.x; n < H; n += blockDim.x) {
-        // each complex element carries two grid points (2n, 2n+1) of the same field
-        V ph = r[n], xi = r[H + n], U = r[2 * H + n], Vv = r[3 * H + n];
-        r[n] = V{xi.x * U.x * ic2, xi.y * U.y * ic2};
-        r[H + n] = V{xi.x * Vv.x * ic2, xi.y * Vv.y * ic2};
-        r[2 * H + n] = V{ph.x * U.x * ic2, ph.y * U.y * ic2};
-        r[3 * H + n] = V{ph.x * Vv.x * ic2, ph.y * Vv.y * ic2};
-        r[4 * H + n] = V{(T)0.5 * (U.x * U.x + Vv.x * Vv.x) * ic2, (T)0.5 * (U.y * U.y + Vv.y * Vv.y) * ic2};
-    }
-    __syncthreads();
-    V* other = (r == d) ? sc : d;
-    V* q = fft_block<T, -1>(r, other, fp, tw, 5, H);
-    const T scale = (T)(w[j] / (double)(2 * H));
-    const int64_t C5 = 5 * (int64_t)S;
-    for (int t = threadIdx.x; t < 5 * (M + 1); t += blockDim.x) {
-        int f = t / (M + 1), m = t - f * (M + 1);
-        Fout[((int64_t)m * nlat + j) * C5 + (int64_t)f * S + s] = r2c_mode<T>(q + f * H, H, m, tw, scale);
-    }
-}
-
 FFTPlan make_fft_plan(const swe_plan* p) {
     FFTPlan fp;
     fp.n = p->nlon / 2;
@@ -458,33 +408,119 @@ swe_status ring_forward(const swe_plan* p, const void* grid, void* F, int C, cud
     return SWE_OK;
 }
 
-swe_status ring_nonlinear(const swe_plan* p, const void* Fin, void* Fout, int S, cudaStream_t st) {
+namespace {
+
+// ----------------------------------------------------------------------------- launch configs
+// Candidate (slices per block, threads, butterflies per thread, min blocks per SM) of the
+// fused nonlinear ring kernel; the first call of a plan with S >= 8 slices times every
+// candidate that fits (5 G H / 4 <= W NT) on its real operands and keeps the fastest.
+struct RingCfg {
+    int G, NT, W;
+};
+template <typename T>
+struct RingLaunch {
+    static void launch(int id, dim3 g, size_t sm, cudaStream_t st, const void* Fin, void* Fout, int M, int nlat, int S,
+                       int G, const FFTPlan& fp, const void* tw, const double* mu, const double* w) {
+        using V = typename CT<T>::V;
+        const V* fi = (const V*)Fin;
+        V* fo = (V*)Fout;
+        const V* t = (const V*)tw;
+        switch (id) {
+            case 0: k_ring_nl_g<T, 512, 4, 1><<<g, 512, sm, st>>>(fi, fo, M, nlat, S, G, fp, t, mu, w); break;
+            case 1: k_ring_nl_g<T, 512, 2, 2><<<g, 512, sm, st>>>(fi, fo, M, nlat, S, G, fp, t, mu, w); break;
+            case 2: k_ring_nl_g<T, 256, 4, 2><<<g, 256, sm, st>>>(fi, fo, M, nlat, S, G, fp, t, mu, w); break;
+            default: k_ring_nl_g<T, 256, 2, 3><<<g, 256, sm, st>>>(fi, fo, M, nlat, S, G, fp, t, mu, w); break;
+        }
+    }
+    static swe_status set_attr(int id, size_t sm) {
+        switch (id) {
+            case 0: return set_smem(k_ring_nl_g<T, 512, 4, 1>, sm);
+            case 1: return set_smem(k_ring_nl_g<T, 512, 2, 2>, sm);
+            case 2: return set_smem(k_ring_nl_g<T, 256, 4, 2>, sm);
+            default: return set_smem(k_ring_nl_g<T, 256, 2, 3>, sm);
+        }
+    }
+};
+const int kRingNT[4] = {512, 512, 256, 256};
+const int kRingW[4] = {4, 2, 4, 2};
+
+bool ring_fits(int id, int G, int H) { return 5 * G * H <= 4 * kRingW[id] * kRingNT[id]; }
+
+template <typename T>
+swe_status ring_run(const swe_plan* p, int id, int G, const void* Fin, void* Fout, int S, cudaStream_t st) {
     FFTPlan fp = make_fft_plan(p);
-    const bool f64 = (p->prec == SWE_FP64);
-    const int T = f64 ? CT<double>::threads : CT<float>::threads;
-    // slices per block: largest of 4, 2, 1 with 5 G H <= 16 T (register staging bound of the passes)
-    int G = 4;
-    while (G > 1 && 5 * G * fp.n > 16 * T) G >>= 1;
-    if (G > S) G = S < 4 ? (S < 2 ? 1 : 2) : G;
     dim3 g((S + G - 1) / G, p->nlat);
+    size_t sm = (size_t)G * 5 * sizeof(typename CT<T>::V) * fp.n;
+    SWE_CHECK(RingLaunch<T>::set_attr(id, sm));
+    const void* tw = (p->prec == SWE_FP64) ? (const void*)p->tw : (const void*)p->twf;
+    RingLaunch<T>::launch(id, g, sm, st, Fin, Fout, p->M, p->nlat, S, G, fp, tw, p->mu, p->w);
+    SWE_CHECK_LAUNCH("k_ring_nl_g");
+    return SWE_OK;
+}
+
+}  // namespace
+
+swe_status ring_nonlinear(const swe_plan* pc, const void* Fin, void* Fout, int S, cudaStream_t st) {
+    swe_plan* p = const_cast<swe_plan*>(pc);
+    const bool f64 = (p->prec == SWE_FP64);
+    const int H = p->nlon / 2;
+    int id = p->ring_cfg, G = p->ring_G;
+    if (id < 0 || G > S) {
+        // default: the largest group that fits the first candidate with room, else 1 slice
+        id = -1;
+        G = 1;
+        for (int gg = 4; gg >= 1 && id < 0; gg >>= 1)
+            for (int c = 0; c < 4 && id < 0; ++c)
+                if (gg <= S && ring_fits(c, gg, H)) {
+                    id = c;
+                    G = gg;
+                }
+        if (id < 0) {
+            swe_set_error("ring_nonlinear: nlon = %d too large for the ring kernels", p->nlon);
+            return SWE_EINVAL;
+        }
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cs);
+        if (S >= 8 && cs == cudaStreamCaptureStatusNone && p->ring_cfg < 0) {
+            // autotune on the real operands (the kernel only reads Fin and writes Fout)
+            float best = 1e30f;
+            int bid = id, bG = G;
+            cudaEvent_t e0, e1;
+            SWE_CHECK_CUDA(cudaEventCreate(&e0));
+            SWE_CHECK_CUDA(cudaEventCreate(&e1));
+            for (int gg = 1; gg <= 4; gg <<= 1)
+                for (int c = 0; c < 4; ++c) {
+                    if (!ring_fits(c, gg, H)) continue;
+                    float ms = 0.f;
+                    for (int rep = 0; rep < 2; ++rep) {      // first run warms up, second is timed
+                        SWE_CHECK_CUDA(cudaEventRecord(e0, st));
+                        if (f64) SWE_CHECK(ring_run<double>(p, c, gg, Fin, Fout, S, st));
+                        else SWE_CHECK(ring_run<float>(p, c, gg, Fin, Fout, S, st));
+                        SWE_CHECK_CUDA(cudaEventRecord(e1, st));
+                        SWE_CHECK_CUDA(cudaEventSynchronize(e1));
+                        SWE_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    }
+                    if (ms < best) {
+                        best = ms;
+                        bid = c;
+                        bG = gg;
+                    }
+                }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            p->ring_cfg = bid;
+            p->ring_G = bG;
+            id = bid;
+            G = bG;
+        }
+    }
     // algorithmic traffic: read 4 and write 5 Fourier rows of (M+1) modes per ring;
     // 9 real FFTs of length nlon (2.5 N log2 N each) + ~30 flops per grid point
     const double fe = f64 ? 16.0 : 8.0;
     const double by = fe * 9.0 * (p->M + 1.0) * p->nlat * S;
     const double fl = ((9.0 * 2.5 * log2((double)p->nlon)) + 30.0) * p->nlon * (double)p->nlat * S;
     ProfToken tk = prof_begin(f64 ? "ring_nl_f64" : "ring_nl_f32", st, fl, by);
-    if (f64) {
-        size_t sm = (size_t)G * 5 * sizeof(double2) * fp.n;
-        SWE_CHECK(set_smem(k_ring_nl_g<double>, sm));
-        k_ring_nl_g<double><<<g, T, sm, st>>>((const double2*)Fin, (double2*)Fout, p->M, p->nlat, S, G, fp, p->tw,
-                                              p->mu, p->w);
-    } else {
-        size_t sm = (size_t)G * 5 * sizeof(float2) * fp.n;
-        SWE_CHECK(set_smem(k_ring_nl_g<float>, sm));
-        k_ring_nl_g<float><<<g, T, sm, st>>>((const float2*)Fin, (float2*)Fout, p->M, p->nlat, S, G, fp, p->twf,
-                                             p->mu, p->w);
-    }
+    swe_status r = f64 ? ring_run<double>(p, id, G, Fin, Fout, S, st) : ring_run<float>(p, id, G, Fin, Fout, S, st);
     prof_end(tk, st);
-    SWE_CHECK_LAUNCH("k_ring_nl_g");
-    return SWE_OK;
+    return r;
 }

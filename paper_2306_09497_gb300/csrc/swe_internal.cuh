@@ -92,6 +92,8 @@ struct swe_plan {
     int* flags = nullptr;
     // extended latitudes for semi-Lagrangian interpolation (built on first use)
     double* thx = nullptr;
+    // launch configuration of the fused nonlinear ring kernel (autotuned on first large call)
+    int ring_cfg = -1, ring_G = 1;
 };
 
 // ---------------------------------------------------------------------------
