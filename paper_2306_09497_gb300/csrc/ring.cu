@@ -233,12 +233,14 @@ __device__ __forceinline__ void fft_inplace(typename CT<T>::V* x, const FFTPlan&
 template <typename T, int NT, int W, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_ring_nl_g(const typename CT<T>::V* __restrict__ Fin,
                                                    typename CT<T>::V* __restrict__ Fout, int M, int nlat, int S, int G,
-                                                   FFTPlan fp, const typename CT<T>::V* __restrict__ tw,
+                                                   FFTPlan fp, const typename CT<T>::V* __restrict__ twg,
                                                    const double* __restrict__ mu, const double* __restrict__ w) {
     using V = typename CT<T>::V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int H = fp.n;
     V* d = reinterpret_cast<V*>(smem_raw);      // [g][5][H]
+    V* tw = d + (size_t)G * 5 * H;              // twiddle table staged in shared memory
+    for (int k = threadIdx.x; k < 2 * H; k += blockDim.x) tw[k] = twg[k];
     const int s0 = blockIdx.x * G;
     const int Gv = min(G, S - s0);
     const int j = blockIdx.y;
@@ -295,12 +297,14 @@ constexpr int RING_G = 4;   // columns per block in the plain transforms
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_ring_inv(const typename CT<T>::V* __restrict__ F, T* __restrict__ grid, int M,
-                                                  int nlat, int C, FFTPlan fp, const typename CT<T>::V* __restrict__ tw) {
+                                                  int nlat, int C, FFTPlan fp, const typename CT<T>::V* __restrict__ twg) {
     using V = typename CT<T>::V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int H = fp.n;
     V* a = reinterpret_cast<V*>(smem_raw);
     V* b = a + RING_G * H;
+    V* tw = b + RING_G * H;                        // twiddle table staged in shared memory
+    for (int k = threadIdx.x; k < 2 * H; k += blockDim.x) tw[k] = twg[k];
     const int j = blockIdx.y;
     const int c0 = RING_G * blockIdx.x;
     const int G = min(RING_G, C - c0);
@@ -330,13 +334,15 @@ __global__ void __launch_bounds__(256) k_ring_inv(const typename CT<T>::V* __res
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_ring_fwd(const T* __restrict__ grid, typename CT<T>::V* __restrict__ F, int M,
-                                                  int nlat, int C, FFTPlan fp, const typename CT<T>::V* __restrict__ tw,
+                                                  int nlat, int C, FFTPlan fp, const typename CT<T>::V* __restrict__ twg,
                                                   const double* __restrict__ w) {
     using V = typename CT<T>::V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int H = fp.n;
     V* a = reinterpret_cast<V*>(smem_raw);
     V* b = a + RING_G * H;
+    V* tw = b + RING_G * H;                        // twiddle table staged in shared memory
+    for (int k = threadIdx.x; k < 2 * H; k += blockDim.x) tw[k] = twg[k];
     const int j = blockIdx.y;
     const int c0 = RING_G * blockIdx.x;
     const int G = min(RING_G, C - c0);
@@ -380,11 +386,11 @@ swe_status ring_inverse(const swe_plan* p, const void* F, void* grid, int C, cud
     FFTPlan fp = make_fft_plan(p);
     dim3 g((C + RING_G - 1) / RING_G, p->nlat);
     if (p->prec == SWE_FP64) {
-        size_t sm = 2 * RING_G * sizeof(double2) * fp.n;
+        size_t sm = (2 * RING_G + 2) * sizeof(double2) * fp.n;
         SWE_CHECK(set_smem(k_ring_inv<double>, sm));
         k_ring_inv<double><<<g, 256, sm, st>>>((const double2*)F, (double*)grid, p->M, p->nlat, C, fp, p->tw);
     } else {
-        size_t sm = 2 * RING_G * sizeof(float2) * fp.n;
+        size_t sm = (2 * RING_G + 2) * sizeof(float2) * fp.n;
         SWE_CHECK(set_smem(k_ring_inv<float>, sm));
         k_ring_inv<float><<<g, 256, sm, st>>>((const float2*)F, (float*)grid, p->M, p->nlat, C, fp, p->twf);
     }
@@ -396,11 +402,11 @@ swe_status ring_forward(const swe_plan* p, const void* grid, void* F, int C, cud
     FFTPlan fp = make_fft_plan(p);
     dim3 g((C + RING_G - 1) / RING_G, p->nlat);
     if (p->prec == SWE_FP64) {
-        size_t sm = 2 * RING_G * sizeof(double2) * fp.n;
+        size_t sm = (2 * RING_G + 2) * sizeof(double2) * fp.n;
         SWE_CHECK(set_smem(k_ring_fwd<double>, sm));
         k_ring_fwd<double><<<g, 256, sm, st>>>((const double*)grid, (double2*)F, p->M, p->nlat, C, fp, p->tw, p->w);
     } else {
-        size_t sm = 2 * RING_G * sizeof(float2) * fp.n;
+        size_t sm = (2 * RING_G + 2) * sizeof(float2) * fp.n;
         SWE_CHECK(set_smem(k_ring_fwd<float>, sm));
         k_ring_fwd<float><<<g, 256, sm, st>>>((const float*)grid, (float2*)F, p->M, p->nlat, C, fp, p->twf, p->w);
     }
@@ -450,7 +456,7 @@ template <typename T>
 swe_status ring_run(const swe_plan* p, int id, int G, const void* Fin, void* Fout, int S, cudaStream_t st) {
     FFTPlan fp = make_fft_plan(p);
     dim3 g((S + G - 1) / G, p->nlat);
-    size_t sm = (size_t)G * 5 * sizeof(typename CT<T>::V) * fp.n;
+    size_t sm = ((size_t)G * 5 + 2) * sizeof(typename CT<T>::V) * fp.n;
     SWE_CHECK(RingLaunch<T>::set_attr(id, sm));
     const void* tw = (p->prec == SWE_FP64) ? (const void*)p->tw : (const void*)p->twf;
     RingLaunch<T>::launch(id, g, sm, st, Fin, Fout, p->M, p->nlat, S, G, fp, tw, p->mu, p->w);
