@@ -220,6 +220,48 @@ swe_status mgrit_cycle(swe_mgrit_t g, int ncycles, double tol, int* k_done, doub
  * host or device). */
 swe_status swe_mgrit_cpoints(swe_mgrit_t g, double* U_out, void* stream);
 
+/* Continuous-batching forecast server.  A request is a Parareal (§3.1) or two-level
+ * MGRIT (§3.2) solve of one initial state; requests queue FIFO and are admitted at the
+ * start of a swe_server_step call while fewer than max_active run and the device memory
+ * they need fits in hbm_budget_bytes.  Each step advances every active request by one
+ * iteration / cycle.  Parareal requests with the same plans and steppers share their
+ * launches: all their slices go through one fine propagation, and their serial coarse
+ * chains advance together (one batched coarse step per chain position); requests
+ * admitted later join at the next step.  Every kernel treats state columns
+ * independently, so a result does not depend on the other requests in the batch.
+ * State stays in device memory from admission until swe_server_result. */
+typedef struct swe_server* swe_server_t;
+typedef enum { SWE_METHOD_PARAREAL = 0, SWE_METHOD_MGRIT2 = 1 } swe_method;
+typedef struct {
+    size_t hbm_budget_bytes;     /* admission budget for the requests' device state */
+    int max_active;              /* slots */
+} swe_server_desc;
+typedef struct {
+    swe_plan_t fine_plan, coarse_plan;
+    int method;                  /* swe_method */
+    swe_stepper_desc fine;       /* Parareal: fine propagator over one slice; MGRIT: one level-0 step */
+    swe_stepper_desc coarse;     /* Parareal: coarse propagator over one slice; MGRIT: one level-1 step */
+    int S;                       /* Parareal: slices; MGRIT: C-intervals (N0 = S * cf) */
+    int cf;                      /* MGRIT coarsening factor */
+    int nu_relax;                /* MGRIT F(CF)^nu */
+    int iters;                   /* Parareal iterations / MGRIT cycles */
+    const double* U0_host;       /* HOST [3][NC] initial state, copied by swe_server_submit */
+} swe_request_desc;
+
+swe_status swe_server_create(const swe_server_desc* desc, swe_server_t* out);
+swe_status swe_server_destroy(swe_server_t s);
+/* Queues a request; *id receives its handle.  Host-side only. */
+swe_status swe_server_submit(swe_server_t s, const swe_request_desc* req, long long* id);
+/* Admits what fits, advances every active request by one iteration and synchronises.
+ * Outputs (HOST, may be NULL): active, queued, and finished-in-this-step counts. */
+swe_status swe_server_step(swe_server_t s, int* n_active, int* n_queued, int* n_done);
+/* Result of a finished request: Parareal slice-boundary states [S+1][3][NC], MGRIT
+ * C-points [S+1][3][NC] (HOST, may be NULL); timing_host[3] = latency (s, submit to
+ * finish), queueing (s, submit to admission), iterations.  Frees the request. */
+swe_status swe_server_result(swe_server_t s, long long id, double* U_host, double* timing_host);
+/* Per-iteration FP64 convergence norms of a request (HOST array of max_norms); *n = count. */
+swe_status swe_server_norms(swe_server_t s, long long id, double* norms_host, int max_norms, int* n);
+
 /* Checkpoint / resume of the Parareal state: the iterate U^k_n, n = 0..S
  * ([S+1][3][NC]) and the coarse results phi_c(U^k_n), n = 0..S-1 ([S][3][NC]),
  * which is all the next iteration needs.  U and Gold may be HOST (pageable or

@@ -79,6 +79,17 @@ __global__ void k_parareal_correct(const double2* __restrict__ G, const double2*
 
 }  // namespace
 
+// Parareal correction of one slice boundary (used by the serving loop as well):
+// Unext <- G + F - Gold, Gold <- G, per-field max-norm reduction into red[6].
+swe_status parareal_correct_launch(const double2* G, const double2* F, double2* Gold, double2* Unext, int64_t nc,
+                                   unsigned long long* red, int* flags, cudaStream_t st) {
+    const int64_t per = 3 * nc;
+    k_parareal_correct<<<(unsigned)((per + 255) / 256 < 1184 ? (per + 255) / 256 : 1184), 256, 0, st>>>(
+        G, F, Gold, Unext, nc, red, flags);
+    SWE_CHECK_LAUNCH("k_parareal_correct");
+    return SWE_OK;
+}
+
 extern "C" swe_status swe_pint_create(const swe_pint_desc* d, swe_pint_t* out) {
     if (!d || !out || !d->fine_plan || !d->coarse_plan || d->S < 1) {
         swe_set_error("swe_pint_create: invalid descriptor");

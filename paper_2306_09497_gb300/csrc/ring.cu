@@ -151,6 +151,60 @@ __device__ __forceinline__ V r2c_mode(const V* Z, int H, int k, const V* twN, T 
     return V{(T)0.5 * (s1.x + t.x) * scale, (T)0.5 * (s1.y + t.y) * scale};
 }
 
+// Per-ring fused nonlinear kernel (one slice, one latitude per block): Fin [M+1][nlat][4S] (Phi', xi, U, V), Fout [M+1][nlat][5S]
+// (A1 = xi U/c2, B1 = xi V/c2, A2 = Phi' U/c2, B2 = Phi' V/c2, KE = (U^2+V^2)/(2 c2)), c2 = 1 - mu^2.
+template <typename T>
+__global__ void __launch_bounds__(256) k_ring_nl_1(const typename CT<T>::V* __restrict__ Fin,
+                                                 typename CT<T>::V* __restrict__ Fout, int M, int nlat, int S,
+                                                 FFTPlan fp, const typename CT<T>::V* __restrict__ twg,
+                                                 const double* __restrict__ mu, const double* __restrict__ w) {
+    using V = typename CT<T>::V;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int H = fp.n;
+    V* d = reinterpret_cast<V*>(smem_raw);   // 5 sequences
+    V* sc = d + 5 * H;                        // 5 scratch sequences
+    V* tw = sc + 5 * H;                       // twiddle table staged in shared memory
+    for (int k = threadIdx.x; k < 2 * H; k += blockDim.x) tw[k] = twg[k];
+    const int s = blockIdx.x;
+    const int j = blockIdx.y;
+    for (int k = threadIdx.x; k < 4 * H; k += blockDim.x) d[k] = V{0, 0};
+    __syncthreads();
+    const int64_t C4 = 4 * (int64_t)S;
+    for (int t = threadIdx.x; t < 4 * (M + 1); t += blockDim.x) {
+        int f = t / (M + 1), m = t - f * (M + 1);
+        V x = Fin[((int64_t)m * nlat + j) * C4 + (int64_t)f * S + s];
+        if (m == 0) x.y = 0;
+        d[f * H + m] = x;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 4 * (H / 2 + 1); t += blockDim.x) {
+        int f = t / (H / 2 + 1), k = t - f * (H / 2 + 1);
+        c2r_prepare(d + f * H, H, k, tw);
+    }
+    __syncthreads();
+    V* r = fft_block<T, +1>(d, sc, fp, tw, 4, H);
+    const double muj = mu[j];
+    const T ic2 = (T)(1.0 / ((1.0 - muj) * (1.0 + muj)));
+    for (int n = threadIdx.x; n < H; n += blockDim.x) {
+        // each complex element carries two grid points (2n, 2n+1) of the same field
+        V ph = r[n], xi = r[H + n], U = r[2 * H + n], Vv = r[3 * H + n];
+        r[n] = V{xi.x * U.x * ic2, xi.y * U.y * ic2};
+        r[H + n] = V{xi.x * Vv.x * ic2, xi.y * Vv.y * ic2};
+        r[2 * H + n] = V{ph.x * U.x * ic2, ph.y * U.y * ic2};
+        r[3 * H + n] = V{ph.x * Vv.x * ic2, ph.y * Vv.y * ic2};
+        r[4 * H + n] = V{(T)0.5 * (U.x * U.x + Vv.x * Vv.x) * ic2, (T)0.5 * (U.y * U.y + Vv.y * Vv.y) * ic2};
+    }
+    __syncthreads();
+    V* other = (r == d) ? sc : d;
+    V* q = fft_block<T, -1>(r, other, fp, tw, 5, H);
+    const T scale = (T)(w[j] / (double)(2 * H));
+    const int64_t C5 = 5 * (int64_t)S;
+    for (int t = threadIdx.x; t < 5 * (M + 1); t += blockDim.x) {
+        int f = t / (M + 1), m = t - f * (M + 1);
+        Fout[((int64_t)m * nlat + j) * C5 + (int64_t)f * S + s] = r2c_mode<T>(q + f * H, H, m, tw, scale);
+    }
+}
+
 // In-place Stockham pass: every thread first loads the inputs of all its butterflies
 // (at most W of them) into registers, the block synchronises, and the outputs are
 // written back into the same buffer.  Needs nfft * N / R <= W * blockDim.x.
@@ -435,7 +489,8 @@ struct RingLaunch {
             case 0: k_ring_nl_g<T, 512, 4, 1><<<g, 512, sm, st>>>(fi, fo, M, nlat, S, G, fp, t, mu, w); break;
             case 1: k_ring_nl_g<T, 512, 2, 2><<<g, 512, sm, st>>>(fi, fo, M, nlat, S, G, fp, t, mu, w); break;
             case 2: k_ring_nl_g<T, 256, 4, 2><<<g, 256, sm, st>>>(fi, fo, M, nlat, S, G, fp, t, mu, w); break;
-            default: k_ring_nl_g<T, 256, 2, 3><<<g, 256, sm, st>>>(fi, fo, M, nlat, S, G, fp, t, mu, w); break;
+            case 3: k_ring_nl_g<T, 256, 2, 3><<<g, 256, sm, st>>>(fi, fo, M, nlat, S, G, fp, t, mu, w); break;
+            default: k_ring_nl_1<T><<<g, 256, sm, st>>>(fi, fo, M, nlat, S, fp, t, mu, w); break;
         }
     }
     static swe_status set_attr(int id, size_t sm) {
@@ -443,20 +498,26 @@ struct RingLaunch {
             case 0: return set_smem(k_ring_nl_g<T, 512, 4, 1>, sm);
             case 1: return set_smem(k_ring_nl_g<T, 512, 2, 2>, sm);
             case 2: return set_smem(k_ring_nl_g<T, 256, 4, 2>, sm);
-            default: return set_smem(k_ring_nl_g<T, 256, 2, 3>, sm);
+            case 3: return set_smem(k_ring_nl_g<T, 256, 2, 3>, sm);
+            default: return set_smem(k_ring_nl_1<T>, sm);
         }
     }
 };
-const int kRingNT[4] = {512, 512, 256, 256};
-const int kRingW[4] = {4, 2, 4, 2};
+const int kRingNT[5] = {512, 512, 256, 256, 256};
+const int kRingW[5] = {4, 2, 4, 2, 0};
+constexpr int kRingCandidates = 5;
 
-bool ring_fits(int id, int G, int H) { return 5 * G * H <= 4 * kRingW[id] * kRingNT[id]; }
+// candidate 4 is the per-ring kernel with a scratch buffer (one slice per block)
+bool ring_fits(int id, int G, int H) {
+    if (id == 4) return G == 1;
+    return 5 * G * H <= 4 * kRingW[id] * kRingNT[id];
+}
 
 template <typename T>
 swe_status ring_run(const swe_plan* p, int id, int G, const void* Fin, void* Fout, int S, cudaStream_t st) {
     FFTPlan fp = make_fft_plan(p);
     dim3 g((S + G - 1) / G, p->nlat);
-    size_t sm = ((size_t)G * 5 + 2) * sizeof(typename CT<T>::V) * fp.n;
+    size_t sm = (id == 4 ? (size_t)12 : (size_t)G * 5 + 2) * sizeof(typename CT<T>::V) * fp.n;
     SWE_CHECK(RingLaunch<T>::set_attr(id, sm));
     const void* tw = (p->prec == SWE_FP64) ? (const void*)p->tw : (const void*)p->twf;
     RingLaunch<T>::launch(id, g, sm, st, Fin, Fout, p->M, p->nlat, S, G, fp, tw, p->mu, p->w);
@@ -476,7 +537,7 @@ swe_status ring_nonlinear(const swe_plan* pc, const void* Fin, void* Fout, int S
         id = -1;
         G = 1;
         for (int gg = 4; gg >= 1 && id < 0; gg >>= 1)
-            for (int c = 0; c < 4 && id < 0; ++c)
+            for (int c = 0; c < kRingCandidates && id < 0; ++c)
                 if (gg <= S && ring_fits(c, gg, H)) {
                     id = c;
                     G = gg;
@@ -495,7 +556,7 @@ swe_status ring_nonlinear(const swe_plan* pc, const void* Fin, void* Fout, int S
             SWE_CHECK_CUDA(cudaEventCreate(&e0));
             SWE_CHECK_CUDA(cudaEventCreate(&e1));
             for (int gg = 1; gg <= 4; gg <<= 1)
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < kRingCandidates; ++c) {
                     if (!ring_fits(c, gg, H)) continue;
                     float ms = 0.f;
                     for (int rep = 0; rep < 2; ++rep) {      // first run warms up, second is timed

@@ -176,3 +176,7 @@ swe_status propagate_strided(swe_plan* p, const swe_stepper_desc* sd, const doub
                              cudaStream_t st);
 swe_status nonlinear_soa(swe_plan* p, const double2* Ua, const double2* Ub, double beta,
                          double2* N, int S, char* ws, cudaStream_t st);
+
+// Parareal correction of one slice boundary (pint.cu)
+swe_status parareal_correct_launch(const double2* G, const double2* F, double2* Gold, double2* Unext, int64_t nc,
+                                   unsigned long long* red, int* flags, cudaStream_t st);

@@ -27,8 +27,10 @@ EXPORTED = [
     "propagate_F", "propagate_G", "swe_pint_create", "swe_pint_destroy", "swe_pint_init", "parareal_iterate",
     "swe_pint_solution", "swe_pint_load", "swe_pint_save", "swe_launch_count", "swe_prof_enable",
     "swe_prof_reset", "swe_prof_read", "sht_inverse_noalloc", "swe_mgrit_create", "swe_mgrit_destroy",
-    "swe_mgrit_init", "mgrit_cycle", "swe_mgrit_cpoints",
+    "swe_mgrit_init", "mgrit_cycle", "swe_mgrit_cpoints", "swe_server_create", "swe_server_destroy",
+    "swe_server_submit", "swe_server_step", "swe_server_result", "swe_server_norms",
 ]
+SWE_METHOD_PARAREAL, SWE_METHOD_MGRIT2 = 0, 1
 
 
 class SWEError(RuntimeError):
@@ -55,6 +57,16 @@ class PintDesc(ct.Structure):
 class MgritDesc(ct.Structure):
     _fields_ = [("L", ct.c_int), ("cf", ct.c_int), ("nu", ct.c_int), ("N0", ct.c_int), ("cycle", ct.c_int),
                 ("plan", ct.c_void_p * 8), ("step", StepperDesc * 8)]
+
+
+class ServerDesc(ct.Structure):
+    _fields_ = [("hbm_budget_bytes", ct.c_size_t), ("max_active", ct.c_int)]
+
+
+class RequestDesc(ct.Structure):
+    _fields_ = [("fine_plan", ct.c_void_p), ("coarse_plan", ct.c_void_p), ("method", ct.c_int),
+                ("fine", StepperDesc), ("coarse", StepperDesc), ("S", ct.c_int), ("cf", ct.c_int),
+                ("nu_relax", ct.c_int), ("iters", ct.c_int), ("U0_host", ct.c_void_p)]
 
 
 _lib = None
@@ -103,6 +115,12 @@ def load(path: Optional[str] = None) -> ct.CDLL:
         "swe_mgrit_init": ([vp, vp, vp], i),
         "mgrit_cycle": ([vp, i, d, ct.POINTER(i), ct.POINTER(d), vp], i),
         "swe_mgrit_cpoints": ([vp, vp, vp], i),
+        "swe_server_create": ([ct.POINTER(ServerDesc), ct.POINTER(vp)], i),
+        "swe_server_destroy": ([vp], i),
+        "swe_server_submit": ([vp, ct.POINTER(RequestDesc), ct.POINTER(ct.c_longlong)], i),
+        "swe_server_step": ([vp, ct.POINTER(i), ct.POINTER(i), ct.POINTER(i)], i),
+        "swe_server_result": ([vp, ct.c_longlong, vp, vp], i),
+        "swe_server_norms": ([vp, ct.c_longlong, vp, i, ct.POINTER(i)], i),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -292,6 +310,59 @@ class MGRIT:
 
     def cpoints(self, U_out, stream=None):
         _check(load().swe_mgrit_cpoints(self.h, _ptr(U_out), _stream(stream)))
+
+
+class Server:
+    """Continuous-batching forecast server (swe_server_*)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_active: int):
+        h = ct.c_void_p()
+        _check(load().swe_server_create(ct.byref(ServerDesc(hbm_budget_bytes, max_active)), ct.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().swe_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, fine_plan: Plan, coarse_plan: Plan, method: int, fine: StepperDesc, coarse: StepperDesc,
+               S: int, iters: int, U0_host, cf: int = 1, nu_relax: int = 0) -> int:
+        """U0_host: numpy complex128 [3][NC] (copied)."""
+        import numpy as np
+        u0 = np.ascontiguousarray(U0_host, dtype=np.complex128)
+        d = RequestDesc(fine_plan.h.value, coarse_plan.h.value, method, fine, coarse, S, cf, nu_relax, iters,
+                        u0.ctypes.data)
+        rid = ct.c_longlong(0)
+        _check(load().swe_server_submit(self.h, ct.byref(d), ct.byref(rid)))
+        self._keep[rid.value] = (S, fine_plan.nc)
+        return rid.value
+
+    def step(self):
+        a, q, dn = ct.c_int(0), ct.c_int(0), ct.c_int(0)
+        _check(load().swe_server_step(self.h, ct.byref(a), ct.byref(q), ct.byref(dn)))
+        return a.value, q.value, dn.value
+
+    def result(self, rid: int):
+        """(states [S+1][3][NC] complex128, latency s, queueing s, iterations) of a finished request."""
+        import numpy as np
+        S, nc = self._keep.pop(rid)
+        out = np.empty((S + 1, 3, nc), dtype=np.complex128)
+        tm = (ct.c_double * 3)()
+        _check(load().swe_server_result(self.h, rid, out.ctypes.data, tm))
+        return out, tm[0], tm[1], int(tm[2])
+
+    def norms(self, rid: int):
+        buf = (ct.c_double * 64)()
+        n = ct.c_int(0)
+        _check(load().swe_server_norms(self.h, rid, buf, 64, ct.byref(n)))
+        return [buf[i] for i in range(min(n.value, 64))]
 
 
 def launch_count() -> int:
