@@ -352,10 +352,11 @@ class Server:
     def result(self, rid: int):
         """(states [S+1][3][NC] complex128, latency s, queueing s, iterations) of a finished request."""
         import numpy as np
-        S, nc = self._keep.pop(rid)
+        S, nc = self._keep[rid]
         out = np.empty((S + 1, 3, nc), dtype=np.complex128)
         tm = (ct.c_double * 3)()
         _check(load().swe_server_result(self.h, rid, out.ctypes.data, tm))
+        del self._keep[rid]
         return out, tm[0], tm[1], int(tm[2])
 
     def norms(self, rid: int):
