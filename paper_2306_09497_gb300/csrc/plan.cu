@@ -130,6 +130,24 @@ __global__ void k_row_m(int M, int* row_m, int* srow_m) {
     for (int n = m; n <= M; ++n) srow_m[so + (n - m)] = m;
 }
 
+__global__ void k_row_coef(int M, double a, double* rc) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m > M) return;
+    auto il = [&](int n) { return (n >= 1 && n <= M && n >= m) ? -a * a / ((double)n * (n + 1.0)) : 0.0; };
+    for (int n = m; n <= M + 1; ++n) {
+        double* c = rc + (ex_off(m, M) + (n - m)) * RC_NUM;
+        const double en = eps_nm(m, n), en1 = eps_nm(m, n + 1);
+        c[RC_UC0] = m * il(n) / a;
+        c[RC_UCM] = (n - 1 >= m) ? (n - 1.0) * en * il(n - 1) / a : 0.0;
+        c[RC_UCP] = (n + 2.0) * en1 * il(n + 1) / a;
+        c[RC_DCP] = n * en1 / a;
+        c[RC_DCM] = (n + 1.0) * en / a;
+        c[RC_P] = n >= 1 ? (n + 1.0) / n * en : 0.0;
+        c[RC_Q] = n >= 1 ? n / (n + 1.0) * en1 : 0.0;
+        c[RC_R] = n >= 1 ? (double)m / ((double)n * (n + 1.0)) : 0.0;
+    }
+}
+
 static bool factor_radices(int N, int* rad, int* nrad) {
     int k = 0;
     while (N % 4 == 0) { rad[k++] = 4; N /= 4; }
@@ -194,6 +212,7 @@ extern "C" swe_status swe_plan_create(const swe_plan_desc* d, swe_plan_t* out) {
     ALLOC(p->tw, sizeof(double2) * p->nlon);
     ALLOC(p->twf, sizeof(float2) * p->nlon);
     ALLOC(p->flags, sizeof(int) * 4);
+    ALLOC(p->rc, sizeof(double) * RC_NUM * p->ncx);
 #undef ALLOC
     cudaMemset(p->flags, 0, sizeof(int) * 4);
     k_gauss<<<(p->nlat2 + 63) / 64, 64>>>(p->nlat, p->mu, p->w);
@@ -203,6 +222,7 @@ extern "C" swe_status swe_plan_create(const swe_plan_desc* d, swe_plan_t* out) {
     }
     k_twiddle<<<(p->nlon + 255) / 256, 256>>>(p->nlon, p->tw, p->twf);
     k_row_m<<<(p->M + 1 + 127) / 128, 128>>>(p->M, p->row_m, p->srow_m);
+    k_row_coef<<<(p->M + 1 + 127) / 128, 128>>>(p->M, p->a, p->rc);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -231,6 +251,7 @@ extern "C" swe_status swe_plan_destroy(swe_plan_t p) {
     cudaFree(p->twf);
     cudaFree(p->flags);
     cudaFree(p->thx);
+    cudaFree(p->rc);
     split_tables_free(p);
     for (int i = 0; i < p->ncn; ++i) cudaFree(p->cn[i].fac);
     if (p->ws.base) cudaFree(p->ws.base);

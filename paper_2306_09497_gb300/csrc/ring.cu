@@ -439,6 +439,8 @@ swe_status set_smem(K kernel, size_t bytes) {
 swe_status ring_inverse(const swe_plan* p, const void* F, void* grid, int C, cudaStream_t st) {
     FFTPlan fp = make_fft_plan(p);
     dim3 g((C + RING_G - 1) / RING_G, p->nlat);
+    const double fe_ = p->prec == SWE_FP64 ? 8.0 : 4.0;   // bytes per real element
+    ProfToken tk = prof_begin("ring_inv", st, 0.0, fe_ * (double)C * p->nlat * (2.0 * (p->M + 1) + p->nlon));
     if (p->prec == SWE_FP64) {
         size_t sm = (2 * RING_G + 2) * sizeof(double2) * fp.n;
         SWE_CHECK(set_smem(k_ring_inv<double>, sm));
@@ -448,6 +450,7 @@ swe_status ring_inverse(const swe_plan* p, const void* F, void* grid, int C, cud
         SWE_CHECK(set_smem(k_ring_inv<float>, sm));
         k_ring_inv<float><<<g, 256, sm, st>>>((const float2*)F, (float*)grid, p->M, p->nlat, C, fp, p->twf);
     }
+    prof_end(tk, st);
     SWE_CHECK_LAUNCH("k_ring_inv");
     return SWE_OK;
 }
@@ -455,6 +458,8 @@ swe_status ring_inverse(const swe_plan* p, const void* F, void* grid, int C, cud
 swe_status ring_forward(const swe_plan* p, const void* grid, void* F, int C, cudaStream_t st) {
     FFTPlan fp = make_fft_plan(p);
     dim3 g((C + RING_G - 1) / RING_G, p->nlat);
+    const double fe_ = p->prec == SWE_FP64 ? 8.0 : 4.0;   // bytes per real element
+    ProfToken tk = prof_begin("ring_fwd", st, 0.0, fe_ * (double)C * p->nlat * (2.0 * (p->M + 1) + p->nlon));
     if (p->prec == SWE_FP64) {
         size_t sm = (2 * RING_G + 2) * sizeof(double2) * fp.n;
         SWE_CHECK(set_smem(k_ring_fwd<double>, sm));
@@ -464,6 +469,7 @@ swe_status ring_forward(const swe_plan* p, const void* grid, void* F, int C, cud
         SWE_CHECK(set_smem(k_ring_fwd<float>, sm));
         k_ring_fwd<float><<<g, 256, sm, st>>>((const float*)grid, (float2*)F, p->M, p->nlat, C, fp, p->twf, p->w);
     }
+    prof_end(tk, st);
     SWE_CHECK_LAUNCH("k_ring_fwd");
     return SWE_OK;
 }

@@ -14,14 +14,8 @@
 
 namespace {
 
-__device__ __forceinline__ double2 c_add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 c_sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 c_scale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
-__device__ __forceinline__ double2 c_imul(double2 a, double s) { return make_double2(-a.y * s, a.x * s); }
 __device__ __forceinline__ double2 czero() { return make_double2(0.0, 0.0); }
-__device__ __forceinline__ double cp_(int m, int n) { return n >= 1 ? (n + 1.0) / n * eps_nm(m, n) : 0.0; }
-__device__ __forceinline__ double cq_(int m, int n) { return n >= 1 ? n / (n + 1.0) * eps_nm(m, n + 1) : 0.0; }
-__device__ __forceinline__ double cr_(int m, int n) { return n >= 1 ? (double)m / ((double)n * (n + 1.0)) : 0.0; }
 
 struct SV {   // SoA spectral state view
     const double2* u;
@@ -38,7 +32,8 @@ struct SV {   // SoA spectral state view
 //   full = 1: f = 0..2 X = U + h L U (h = dt/2), 3 Phi', 4 delta, 5 U_cos, 6 V_cos   (7 fields)
 //   full = 0: f = 0 Phi', 1 delta, 2 U_cos, 3 V_cos                                 (4 fields)
 __global__ void k_sl_operands(SV U, double2* __restrict__ X, const int* __restrict__ row_m, int64_t ncx, int nf,
-                              int full, double h, double a, double omega, double phibar) {
+                              int full, double h, double ia2, double omega, double phibar,
+                              const double* __restrict__ rc) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int S = U.S, M = U.M;
     if (t >= ncx * S) return;
@@ -46,23 +41,17 @@ __global__ void k_sl_operands(SV U, double2* __restrict__ X, const int* __restri
     const int64_t rx = t / S;
     const int m = row_m[rx];
     const int n = m + (int)(rx - ex_off(m, M));
-    const double a2 = a * a;
-    auto psi = [&](int k) -> double2 {
-        if (k < 1 || k < m) return czero();
-        return c_scale(U.get(1, m, k, s), -a2 / ((double)k * (k + 1.0)));
-    };
-    auto chi = [&](int k) -> double2 {
-        if (k < 1 || k < m) return czero();
-        return c_scale(U.get(2, m, k, s), -a2 / ((double)k * (k + 1.0)));
-    };
-    const double en = eps_nm(m, n), en1 = eps_nm(m, n + 1), ia = 1.0 / a;
-    double2 Uh = c_scale(c_add(c_imul(chi(n), (double)m),
-                               c_sub(c_scale(psi(n - 1), (n - 1.0) * en), c_scale(psi(n + 1), (n + 2.0) * en1))),
-                         ia);
-    double2 Vh = c_scale(c_add(c_imul(psi(n), (double)m),
-                               c_sub(c_scale(chi(n + 1), (n + 2.0) * en1), c_scale(chi(n - 1), (n - 1.0) * en))),
-                         ia);
-    double2 ph = U.get(0, m, n, s), xi = U.get(1, m, n, s), de = U.get(2, m, n, s);
+    const double* c = rc + rx * RC_NUM;
+    const double uc0 = c[RC_UC0], ucm = c[RC_UCM], ucp = c[RC_UCP];
+    const double2 ph = U.get(0, m, n, s), xi = U.get(1, m, n, s), de = U.get(2, m, n, s);
+    const double2 xim = U.get(1, m, n - 1, s), dem = U.get(2, m, n - 1, s);
+    const double2 xip = U.get(1, m, n + 1, s), dep = U.get(2, m, n + 1, s);
+    // U_cos, V_cos from psi = lap^{-1} xi, chi = lap^{-1} delta (coefficients folded in rc)
+    double2 Uh, Vh;
+    Uh.x = fma(ucm, xim.x, fma(-ucp, xip.x, -uc0 * de.y));
+    Uh.y = fma(ucm, xim.y, fma(-ucp, xip.y, uc0 * de.x));
+    Vh.x = fma(-ucm, dem.x, fma(ucp, dep.x, -uc0 * xi.y));
+    Vh.y = fma(-ucm, dem.y, fma(ucp, dep.y, uc0 * xi.x));
     double2* row = X + rx * (int64_t)nf * S + s;
     if (n > M) {
         // the extended row n = M+1 carries only the velocity operands; every other field is
@@ -73,16 +62,16 @@ __global__ void k_sl_operands(SV U, double2* __restrict__ X, const int* __restri
         return;
     }
     if (full) {
-        const double w2 = 2.0 * omega, p = cp_(m, n), q = cq_(m, n), r = cr_(m, n);
-        double2 L0 = c_scale(de, -phibar);
-        double2 L1 = c_add(c_scale(c_add(c_scale(U.get(2, m, n - 1, s), p), c_scale(U.get(2, m, n + 1, s), q)), -w2),
-                           c_imul(xi, w2 * r));
-        double2 L2 = c_add(c_scale(ph, (double)n * (n + 1.0) / a2),
-                           c_add(c_scale(c_add(c_scale(U.get(1, m, n - 1, s), p), c_scale(U.get(1, m, n + 1, s), q)), w2),
-                                 c_imul(de, w2 * r)));
-        row[0] = c_add(ph, c_scale(L0, h));
-        row[S] = c_add(xi, c_scale(L1, h));
-        row[2 * S] = c_add(de, c_scale(L2, h));
+        const double w2 = 2.0 * omega, p = w2 * c[RC_P], q = w2 * c[RC_Q], r = w2 * c[RC_R];
+        const double lap = (double)(n * (n + 1)) * ia2;
+        const double2 L0 = c_scale(de, -phibar);
+        const double2 L1 = make_double2(-fma(p, dem.x, fma(q, dep.x, r * xi.y)),
+                                        -fma(p, dem.y, fma(q, dep.y, -r * xi.x)));
+        const double2 L2 = make_double2(fma(lap, ph.x, fma(p, xim.x, fma(q, xip.x, -r * de.y))),
+                                        fma(lap, ph.y, fma(p, xim.y, fma(q, xip.y, r * de.x))));
+        row[0] = make_double2(fma(h, L0.x, ph.x), fma(h, L0.y, ph.y));
+        row[S] = make_double2(fma(h, L1.x, xi.x), fma(h, L1.y, xi.y));
+        row[2 * S] = make_double2(fma(h, L2.x, de.x), fma(h, L2.y, de.y));
         row[3 * S] = ph;
         row[4 * S] = de;
         row[5 * S] = Uh;
@@ -97,44 +86,57 @@ __global__ void k_sl_operands(SV U, double2* __restrict__ X, const int* __restri
 
 // Cartesian velocity (m/s) and N_R = -Phi' delta on the grid, from fields
 // (Phi', delta, U_cos, V_cos) at field offsets (fp, fd, fu, fv) of a grid block [nf*S][nlat][nlon].
+// Grid-point kernels compute in the grid type T (double for FP64 plans, float for
+// mixed plans: GB300's FP64 rate is 1/64 of its FP32 rate, and the grid values are
+// FP32 there anyway).  Geometry comes from a per-plan table in T (built in FP64):
+//   tab[0 .. nlat+3]             extended latitudes (two halo rows beyond each pole)
+//   tab[nlat+4 .. 2 nlat+3]      sin(latitude) = mu
+//   tab[2 nlat+4 .. 3 nlat+3]    cos(latitude)
+__device__ __forceinline__ void sc_pi(double x, double* s, double* c) { sincospi(x, s, c); }
+__device__ __forceinline__ void sc_pi(float x, float* s, float* c) { sincospif(x, s, c); }
+
 template <typename T>
 __global__ void k_sl_vel(const T* __restrict__ G, int fp, int fd, int fu, int fv, T* __restrict__ Vc,
-                         T* __restrict__ NR, const double* __restrict__ mu, int S, int nlat, int nlon) {
+                         T* __restrict__ NR, const T* __restrict__ tab, int S, int nlat, int nlon) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t npt = (int64_t)nlat * nlon;
     if (t >= npt * S) return;
     const int s = (int)(t / npt);
     const int64_t p = t - (int64_t)s * npt;
     const int j = (int)(p / nlon), k = (int)(p - (int64_t)j * nlon);
-    auto at = [&](int f) { return (double)G[((int64_t)f * S + s) * npt + p]; };
-    const double sinl = mu[j], cosl = sqrt((1.0 - sinl) * (1.0 + sinl));
-    const double u = at(fu) / cosl, v = at(fv) / cosl;
-    double sl, cl;
-    sincospi(2.0 * k / nlon, &sl, &cl);
-    Vc[((int64_t)0 * S + s) * npt + p] = (T)(-u * sl - v * sinl * cl);
-    Vc[((int64_t)1 * S + s) * npt + p] = (T)(u * cl - v * sinl * sl);
-    Vc[((int64_t)2 * S + s) * npt + p] = (T)(v * cosl);
-    NR[(int64_t)s * npt + p] = (T)(-at(fp) * at(fd));
+    auto at = [&](int f) { return G[((int64_t)f * S + s) * npt + p]; };
+    const T sinl = tab[nlat + 4 + j], cosl = tab[2 * nlat + 4 + j];
+    const T u = at(fu) / cosl, v = at(fv) / cosl;
+    T sl, cl;
+    sc_pi((T)(2 * k) / (T)nlon, &sl, &cl);
+    Vc[((int64_t)0 * S + s) * npt + p] = -u * sl - v * sinl * cl;
+    Vc[((int64_t)1 * S + s) * npt + p] = u * cl - v * sinl * sl;
+    Vc[((int64_t)2 * S + s) * npt + p] = v * cosl;
+    NR[(int64_t)s * npt + p] = -at(fp) * at(fd);
 }
 
 // X_Phi += h (2 N_R^n - N_R^{n-1}) in place (field 0 of the 7-field block)
 template <typename T>
-__global__ void k_sl_xphi(T* __restrict__ G, const T* __restrict__ NRn, const T* __restrict__ NRm, double h, int S,
+__global__ void k_sl_xphi(T* __restrict__ G, const T* __restrict__ NRn, const T* __restrict__ NRm, T h, int S,
                           int64_t npt) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= npt * S) return;
-    G[t] = (T)((double)G[t] + h * (2.0 * (double)NRn[t] - (double)NRm[t]));
+    G[t] = G[t] + h * ((T)2 * NRn[t] - NRm[t]);
 }
 
+template <typename T>
 struct Stencil {
-    int row[4], shift[4], col0;
-    double wl[4], wx[4];
+    int base[4];      // first of the four columns of each row, before wrapping (may be -1 or >= nlon)
+    int64_t row[4];   // row offsets (grid row * nlon)
+    T wl[4], wx[4];
 };
 
-// bracket + Lagrange weights of the departure point (latd, lond); thx = extended latitudes (nlat+4)
-__device__ __forceinline__ void make_stencil(double latd, double lond, const double* __restrict__ thx, int nlat,
-                                             int nlon, Stencil& st) {
-    // i = (number of extended latitudes >= latd) - 1, clipped to [1, nlat+1]  (thx descending)
+// bracket + Lagrange weights of the departure point (latd, xd = longitude in grid
+// cells, in [0, nlon)); thx = extended latitudes (nlat+4, descending)
+template <typename T>
+__device__ __forceinline__ void make_stencil(T latd, T xd, const T* __restrict__ thx, int nlat, int nlon,
+                                             Stencil<T>& st) {
+    // i = (number of extended latitudes >= latd) - 1, clipped to [1, nlat+1]
     int lo = 0, hi = nlat + 4;                 // count of entries >= latd lies in [lo, hi]
     while (lo < hi) {
         int mid = (lo + hi) >> 1;
@@ -142,7 +144,10 @@ __device__ __forceinline__ void make_stencil(double latd, double lond, const dou
     }
     int i = lo - 1;
     i = i < 1 ? 1 : (i > nlat + 1 ? nlat + 1 : i);
-    double y[4];
+    int i0 = (int)floor(xd);
+    const T t = xd - (T)i0;
+    if (i0 >= nlon) i0 -= nlon;
+    T y[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         const int e = i - 1 + r;               // extended index 0..nlat+3
@@ -157,106 +162,107 @@ __device__ __forceinline__ void make_stencil(double latd, double lond, const dou
             rowi = nlat - 1 - (e - (nlat + 2));
             sh = nlon / 2;
         }
-        st.row[r] = rowi;
-        st.shift[r] = sh;
+        st.row[r] = (int64_t)rowi * nlon;
+        st.base[r] = i0 - 1 + sh;
     }
+    // Lagrange weights: w_r = prod_{q != r} (latd - y_q) / prod_{q != r} (y_r - y_q)
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-        double w = 1.0;
+        T num = (T)1, den = (T)1;
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            if (q != r) w *= (latd - y[q]) / (y[r] - y[q]);
-        st.wl[r] = w;
+            if (q != r) {
+                num *= latd - y[q];
+                den *= y[r] - y[q];
+            }
+        st.wl[r] = num / den;
     }
-    const double dl = 2.0 * M_PI / nlon;
-    double x = fmod(lond, 2.0 * M_PI);
-    if (x < 0) x += 2.0 * M_PI;
-    x /= dl;
-    int i0 = (int)floor(x);
-    const double t = x - i0;
-    i0 = ((i0 % nlon) + nlon) % nlon;
-    st.col0 = i0;
-    st.wx[0] = -t * (t - 1.0) * (t - 2.0) / 6.0;
-    st.wx[1] = (t + 1.0) * (t - 1.0) * (t - 2.0) / 2.0;
-    st.wx[2] = -(t + 1.0) * t * (t - 2.0) / 2.0;
-    st.wx[3] = (t + 1.0) * t * (t - 1.0) / 6.0;
+    const T sixth = (T)1 / (T)6;
+    st.wx[0] = -t * (t - (T)1) * (t - (T)2) * sixth;
+    st.wx[1] = (t + (T)1) * (t - (T)1) * (t - (T)2) * (T)0.5;
+    st.wx[2] = -(t + (T)1) * t * (t - (T)2) * (T)0.5;
+    st.wx[3] = (t + (T)1) * t * (t - (T)1) * sixth;
 }
 
 template <typename T>
-__device__ __forceinline__ double interp(const T* __restrict__ F, const Stencil& st, int nlon) {
-    double acc = 0.0;
+__device__ __forceinline__ T interp(const T* __restrict__ F, const Stencil<T>& st, int nlon) {
+    T acc = (T)0;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-        const T* row = F + (int64_t)st.row[r] * nlon;
-        double a = 0.0;
+        const T* row = F + st.row[r];
+        T a = (T)0;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            int col = st.col0 - 1 + c + st.shift[r];
-            col = ((col % nlon) + nlon) % nlon;
-            a += st.wx[c] * (double)row[col];
+            int col = st.base[r] + c;          // in [-1, 3 nlon / 2 + 1]
+            if (col < 0) col += nlon;
+            if (col >= nlon) col -= nlon;
+            a += st.wx[c] * row[col];
         }
         acc += st.wl[r] * a;
     }
     return acc;
 }
 
+// departure point (latitude, longitude in grid cells) of the Cartesian point xd (any length)
+template <typename T>
+__device__ __forceinline__ void to_latlon(const T* xd, int nlon, T& latd, T& lonc) {
+    latd = atan2(xd[2], sqrt(xd[0] * xd[0] + xd[1] * xd[1]));
+    lonc = atan2(xd[1], xd[0]) * ((T)nlon / (T)(2.0 * M_PI));
+    if (lonc < (T)0) lonc += (T)nlon;
+    if (lonc >= (T)nlon) lonc -= (T)nlon;
+}
+
 // departure points + gather: R[f*S + s] = X_f(x_d) (+ h N_R^n(x_a) for f = 0)
 template <typename T>
-__global__ void k_sl_depart(const T* __restrict__ G, const T* __restrict__ Vn, const T* __restrict__ Vm,
-                            const T* __restrict__ NRn, T* __restrict__ R, const double* __restrict__ thx, double h,
-                            double a, int S, int nlat, int nlon) {
+__global__ void __launch_bounds__(128) k_sl_depart(const T* __restrict__ G, const T* __restrict__ Vn,
+                                                   const T* __restrict__ Vm, const T* __restrict__ NRn,
+                                                   T* __restrict__ R, const T* __restrict__ tab, T h, T a, int S,
+                                                   int nlat, int nlon) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t npt = (int64_t)nlat * nlon;
     if (t >= npt * S) return;
     const int s = (int)(t / npt);
     const int64_t p = t - (int64_t)s * npt;
     const int j = (int)(p / nlon), k = (int)(p - (int64_t)j * nlon);
-    const double lat = thx[j + 2];
-    double sl, cl, sp, cp;
-    sincospi(2.0 * k / nlon, &sl, &cl);
-    sincos(lat, &sp, &cp);
-    const double xa[3] = {cp * cl, cp * sl, sp};
-    double va[3], vm[3];
+    const T sp = tab[nlat + 4 + j], cp = tab[2 * nlat + 4 + j];
+    T sl, cl;
+    sc_pi((T)(2 * k) / (T)nlon, &sl, &cl);
+    const T xa[3] = {cp * cl, cp * sl, sp};
+    T va[3], vm[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        va[d] = (double)Vn[((int64_t)d * S + s) * npt + p];
-        vm[d] = (double)Vm[((int64_t)d * S + s) * npt + p];
+        va[d] = Vn[((int64_t)d * S + s) * npt + p];
+        vm[d] = Vm[((int64_t)d * S + s) * npt + p];
     }
-    const double sc = h / a;   // (dt/2) / a
-    double latd = lat, lond = 2.0 * M_PI * k / nlon;
-    double vn[3] = {va[0], va[1], va[2]};   // x_d^0 = x_a: grid values
-    Stencil st;
+    const T sc = h / a;   // (dt/2) / a
+    T vn[3] = {va[0], va[1], va[2]};   // x_d^0 = x_a: grid values
+    Stencil<T> st;
+    T xd[3];
     for (int it = 0; it < 2; ++it) {
         if (it > 0) {
-            make_stencil(latd, lond, thx, nlat, nlon, st);
+            T latd, lonc;
+            to_latlon(xd, nlon, latd, lonc);
+            make_stencil(latd, lonc, tab, nlat, nlon, st);
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 vn[d] = interp(Vn + ((int64_t)d * S + s) * npt, st, nlon);
                 vm[d] = interp(Vm + ((int64_t)d * S + s) * npt, st, nlon);
             }
         }
-        double xd[3], nrm = 0.0;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            xd[d] = xa[d] - sc * (2.0 * vn[d] - vm[d] + va[d]);
-            nrm += xd[d] * xd[d];
-        }
-        nrm = 1.0 / sqrt(nrm);
-        const double z = fmin(1.0, fmax(-1.0, xd[2] * nrm));
-        latd = asin(z);
-        lond = atan2(xd[1], xd[0]);
-        if (lond < 0) lond += 2.0 * M_PI;
+        for (int d = 0; d < 3; ++d) xd[d] = xa[d] - sc * ((T)2 * vn[d] - vm[d] + va[d]);
     }
-    make_stencil(latd, lond, thx, nlat, nlon, st);
+    T latd, lonc;
+    to_latlon(xd, nlon, latd, lonc);
+    make_stencil(latd, lonc, tab, nlat, nlon, st);
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
-        double v = interp(G + ((int64_t)f * S + s) * npt, st, nlon);
-        if (f == 0) v += h * (double)NRn[(int64_t)s * npt + p];
-        R[((int64_t)f * S + s) * npt + p] = (T)v;
+        T v = interp(G + ((int64_t)f * S + s) * npt, st, nlon);
+        if (f == 0) v += h * NRn[(int64_t)s * npt + p];
+        R[((int64_t)f * S + s) * npt + p] = v;
     }
 }
 
-// forward results Y [ncx][3S] -> SoA state [3][NC][S] (rows n <= M)
 __global__ void k_sl_unpack(const double2* __restrict__ Y, double2* __restrict__ R, const int* __restrict__ srow_m,
                             int M, int64_t nc, int S) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -270,14 +276,20 @@ __global__ void k_sl_unpack(const double2* __restrict__ Y, double2* __restrict__
     for (int f = 0; f < 3; ++f) R[((int64_t)f * nc + r) * S + s] = y[(int64_t)f * S];
 }
 
-__global__ void k_thx(const double* __restrict__ mu, double* __restrict__ thx, int nlat) {
+template <typename T>
+__global__ void k_sl_table(const double* __restrict__ mu, T* __restrict__ tab, int nlat) {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nlat + 4) return;
-    double v;
-    if (e < 2) v = M_PI - asin(mu[1 - e]);
-    else if (e < nlat + 2) v = asin(mu[e - 2]);
-    else v = -M_PI - asin(mu[nlat - 1 - (e - (nlat + 2))]);
-    thx[e] = v;
+    if (e < nlat + 4) {
+        double v;
+        if (e < 2) v = M_PI - asin(mu[1 - e]);
+        else if (e < nlat + 2) v = asin(mu[e - 2]);
+        else v = -M_PI - asin(mu[nlat - 1 - (e - (nlat + 2))]);
+        tab[e] = (T)v;
+    }
+    if (e < nlat) {
+        tab[nlat + 4 + e] = (T)mu[e];
+        tab[2 * nlat + 4 + e] = (T)sqrt((1.0 - mu[e]) * (1.0 + mu[e]));
+    }
 }
 
 inline unsigned nb(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
@@ -332,9 +344,15 @@ static SLBuf sl_carve(const swe_plan* p, char* c, int S) {
 
 static swe_status ensure_thx(swe_plan* p) {
     if (p->thx) return SWE_OK;
-    SWE_CHECK_CUDA(cudaMalloc((void**)&p->thx, sizeof(double) * (p->nlat + 4)));
-    k_thx<<<nb(p->nlat + 4, 64), 64>>>(p->mu, p->thx, p->nlat);
-    SWE_CHECK_LAUNCH("k_thx");
+    const size_t n = 3 * (size_t)p->nlat + 4;
+    if (p->prec == SWE_FP64) {
+        SWE_CHECK_CUDA(cudaMalloc(&p->thx, sizeof(double) * n));
+        k_sl_table<double><<<nb(p->nlat + 4, 64), 64>>>(p->mu, (double*)p->thx, p->nlat);
+    } else {
+        SWE_CHECK_CUDA(cudaMalloc(&p->thx, sizeof(float) * n));
+        k_sl_table<float><<<nb(p->nlat + 4, 64), 64>>>(p->mu, (float*)p->thx, p->nlat);
+    }
+    SWE_CHECK_LAUNCH("k_sl_table");
     SWE_CHECK_CUDA(cudaDeviceSynchronize());
     return SWE_OK;
 }
@@ -345,7 +363,8 @@ template <typename T>
 static swe_status vel_launch(const swe_plan* p, const void* G, int fp, int fd, int fu, int fv, void* Vc, void* NR,
                              int S, cudaStream_t st) {
     const int64_t n = (int64_t)p->nlat * p->nlon * S;
-    k_sl_vel<T><<<nb(n), 256, 0, st>>>((const T*)G, fp, fd, fu, fv, (T*)Vc, (T*)NR, p->mu, S, p->nlat, p->nlon);
+    k_sl_vel<T><<<nb(n), 256, 0, st>>>((const T*)G, fp, fd, fu, fv, (T*)Vc, (T*)NR, (const T*)p->thx, S, p->nlat,
+                                       p->nlon);
     SWE_CHECK_LAUNCH("k_sl_vel");
     return SWE_OK;
 }
@@ -362,7 +381,12 @@ swe_status sl_step(swe_plan* p, double dt, double nu, int q, const double2* Upre
     const int64_t npt = (int64_t)p->nlat * p->nlon;
     // operands of the current state (7 fields) -> grid
     SV v{U, p->nc, S, p->M};
-    k_sl_operands<<<nb(p->ncx * S), 256, 0, st>>>(v, b.X, p->row_m, p->ncx, 7, 1, h, p->a, p->omega, p->phibar);
+    {
+        ProfToken tk_ = prof_begin("sl_operands", st, 0.0, 16.0 * S * (3.0 * p->nc + 7.0 * p->ncx));
+        k_sl_operands<<<nb(p->ncx * S), 256, 0, st>>>(v, b.X, p->row_m, p->ncx, 7, 1, h, 1.0 / (p->a * p->a),
+                                                      p->omega, p->phibar, p->rc);
+        prof_end(tk_, st);
+    }
     SWE_CHECK_LAUNCH("k_sl_operands");
     SWE_CHECK(leg_inverse(p, b.X, b.Fq, 7 * S, st));
     SWE_CHECK(ring_inverse(p, b.Fq, b.G, 7 * S, st));
@@ -378,7 +402,8 @@ swe_status sl_step(swe_plan* p, double dt, double nu, int q, const double2* Upre
     } else if (Uprev) {
         // grid fields (Phi', delta, U_cos, V_cos) of the previous state -> previous velocity / N_R
         SV vp{Uprev, p->nc, S, p->M};
-        k_sl_operands<<<nb(p->ncx * S), 256, 0, st>>>(vp, b.X, p->row_m, p->ncx, 4, 0, h, p->a, p->omega, p->phibar);
+        k_sl_operands<<<nb(p->ncx * S), 256, 0, st>>>(vp, b.X, p->row_m, p->ncx, 4, 0, h, 1.0 / (p->a * p->a), p->omega,
+                                                      p->phibar, p->rc);
         SWE_CHECK_LAUNCH("k_sl_operands(prev)");
         SWE_CHECK(leg_inverse(p, b.X, b.Fq, 4 * S, st));
         SWE_CHECK(ring_inverse(p, b.Fq, b.Gp, 4 * S, st));
@@ -389,24 +414,39 @@ swe_status sl_step(swe_plan* p, double dt, double nu, int q, const double2* Upre
     }
     // X_Phi += h (2 N_R^n - N_R^{n-1})
     if (f64) {
-        k_sl_xphi<double><<<nb(npt * S), 256, 0, st>>>((double*)b.G, (const double*)b.Nc, (const double*)Nm, h, S, npt);
+        k_sl_xphi<double><<<nb(npt * S), 256, 0, st>>>((double*)b.G, (const double*)b.Nc, (const double*)Nm, h, S,
+                                                        npt);
     } else {
-        k_sl_xphi<float><<<nb(npt * S), 256, 0, st>>>((float*)b.G, (const float*)b.Nc, (const float*)Nm, h, S, npt);
+        k_sl_xphi<float><<<nb(npt * S), 256, 0, st>>>((float*)b.G, (const float*)b.Nc, (const float*)Nm, (float)h, S,
+                                                       npt);
     }
     SWE_CHECK_LAUNCH("k_sl_xphi");
     if (f64) {
-        k_sl_depart<double><<<nb(npt * S, 128), 128, 0, st>>>((const double*)b.G, (const double*)b.Vc,
+        {
+            ProfToken tk_ = prof_begin("sl_depart", st, 0.0, (f64 ? 8.0 : 4.0) * 13.0 * npt * S);
+            k_sl_depart<double><<<nb(npt * S, 128), 128, 0, st>>>((const double*)b.G, (const double*)b.Vc,
                                                               (const double*)Vm, (const double*)b.Nc, (double*)b.R,
-                                                              p->thx, h, p->a, S, p->nlat, p->nlon);
+                                                              (const double*)p->thx, h, p->a, S, p->nlat, p->nlon);
+            prof_end(tk_, st);
+        }
     } else {
-        k_sl_depart<float><<<nb(npt * S, 128), 128, 0, st>>>((const float*)b.G, (const float*)b.Vc,
+        {
+            ProfToken tk_ = prof_begin("sl_depart", st, 0.0, (f64 ? 8.0 : 4.0) * 13.0 * npt * S);
+            k_sl_depart<float><<<nb(npt * S, 128), 128, 0, st>>>((const float*)b.G, (const float*)b.Vc,
                                                              (const float*)Vm, (const float*)b.Nc, (float*)b.R,
-                                                             p->thx, h, p->a, S, p->nlat, p->nlon);
+                                                             (const float*)p->thx, (float)h, (float)p->a, S,
+                                                             p->nlat, p->nlon);
+            prof_end(tk_, st);
+        }
     }
     SWE_CHECK_LAUNCH("k_sl_depart");
     SWE_CHECK(ring_forward(p, b.R, b.Fq, 3 * S, st));
     SWE_CHECK(leg_forward(p, b.Fq, b.Y, 3 * S, st));
-    k_sl_unpack<<<nb(p->nc * S), 256, 0, st>>>(b.Y, b.Rs, p->srow_m, p->M, p->nc, S);
+    {
+        ProfToken tk_ = prof_begin("sl_unpack", st, 0.0, 16.0 * 6.0 * p->nc * S);
+        k_sl_unpack<<<nb(p->nc * S), 256, 0, st>>>(b.Y, b.Rs, p->srow_m, p->M, p->nc, S);
+        prof_end(tk_, st);
+    }
     SWE_CHECK_LAUNCH("k_sl_unpack");
     SWE_CHECK(k_implicit(p, h, 0, b.Rs, Uout, dt, nu, q, S, st));
     if (swap_prev) {

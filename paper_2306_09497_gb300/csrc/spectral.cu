@@ -31,7 +31,6 @@ __device__ __forceinline__ double2 c_scale(double2 a, double s) { return make_do
 __device__ __forceinline__ double2 c_mul(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-__device__ __forceinline__ double2 c_imul(double2 a, double s) { return make_double2(-a.y * s, a.x * s); }  // i s a
 __device__ __forceinline__ double2 c_inv(double2 a) {
     double d = a.x * a.x + a.y * a.y;
     return make_double2(a.x / d, -a.y / d);
@@ -127,7 +126,7 @@ struct StateView {
 };
 
 __global__ void k_nl_pre_kernel(StateView U, double2* __restrict__ X, const int* __restrict__ row_m, int64_t ncx,
-                                double a) {
+                                const double* __restrict__ rc) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int S = U.S, M = U.M;
     if (t >= ncx * S) return;
@@ -135,30 +134,20 @@ __global__ void k_nl_pre_kernel(StateView U, double2* __restrict__ X, const int*
     int64_t rx = t / S;
     int m = row_m[rx];
     int n = m + (int)(rx - ex_off(m, M));
-    const double a2 = a * a;
-    auto psi = [&](int k) -> double2 {
-        if (k < 1) return czero();
-        return c_scale(U.get(1, m, k, s), -a2 / ((double)k * (k + 1.0)));
-    };
-    auto chi = [&](int k) -> double2 {
-        if (k < 1) return czero();
-        return c_scale(U.get(2, m, k, s), -a2 / ((double)k * (k + 1.0)));
-    };
-    const double en = eps_nm(m, n), en1 = eps_nm(m, n + 1);
-    double2 ps_m = (n - 1 >= m) ? psi(n - 1) : czero();
-    double2 ch_m = (n - 1 >= m) ? chi(n - 1) : czero();
-    double2 ps_p = psi(n + 1), ch_p = chi(n + 1);
-    double2 ps_0 = psi(n), ch_0 = chi(n);
-    const double ia = 1.0 / a;
-    double2 Uh = c_scale(c_add(c_imul(ch_0, (double)m),
-                               c_sub(c_scale(ps_m, (n - 1.0) * en), c_scale(ps_p, (n + 2.0) * en1))),
-                         ia);
-    double2 Vh = c_scale(c_add(c_imul(ps_0, (double)m),
-                               c_sub(c_scale(ch_p, (n + 2.0) * en1), c_scale(ch_m, (n - 1.0) * en))),
-                         ia);
+    const double* c = rc + rx * RC_NUM;
+    const double uc0 = c[RC_UC0], ucm = c[RC_UCM], ucp = c[RC_UCP];
+    // U = i m chi_n/a + (n-1) eps_n psi_{n-1}/a - (n+2) eps_{n+1} psi_{n+1}/a, V likewise (psi <-> chi)
+    const double2 xi0 = U.get(1, m, n, s), de0 = U.get(2, m, n, s);
+    const double2 xim = U.get(1, m, n - 1, s), dem = U.get(2, m, n - 1, s);
+    const double2 xip = U.get(1, m, n + 1, s), dep = U.get(2, m, n + 1, s);
+    double2 Uh, Vh;
+    Uh.x = fma(ucm, xim.x, fma(-ucp, xip.x, -uc0 * de0.y));
+    Uh.y = fma(ucm, xim.y, fma(-ucp, xip.y, uc0 * de0.x));
+    Vh.x = fma(-ucm, dem.x, fma(ucp, dep.x, -uc0 * xi0.y));
+    Vh.y = fma(-ucm, dem.y, fma(ucp, dep.y, uc0 * xi0.x));
     double2* row = X + rx * 4 * (int64_t)S + s;
     row[0] = U.get(0, m, n, s);
-    row[S] = U.get(1, m, n, s);
+    row[S] = xi0;
     row[2 * S] = Uh;
     row[3 * S] = Vh;
 }
@@ -166,31 +155,31 @@ __global__ void k_nl_pre_kernel(StateView U, double2* __restrict__ X, const int*
 __global__ void k_nl_post_kernel(const double2* __restrict__ Y, int mode, double dt, const double2* __restrict__ in0,
                                  const double2* __restrict__ in1, double2* __restrict__ out0,
                                  double2* __restrict__ out1, const int* __restrict__ srow_m, int M, int64_t nc, int S,
-                                 double a, int* flags) {
+                                 double ia, const double* __restrict__ rc, int* flags) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= nc * S) return;
     int s = (int)(t % S);
     int64_t r = t / S;
     int m = srow_m[r];
     int n = m + (int)(r - st_off(m, M));
+    const int64_t rx = ex_off(m, M) + (n - m);
     const int64_t C5 = 5 * (int64_t)S;
-    const double2* y0 = Y + (ex_off(m, M) + (n - m)) * C5 + s;
+    const double2* y0 = Y + rx * C5 + s;
     const double2* yp = y0 + C5;                       // n + 1 (<= M + 1 always present)
     const bool hm = (n - 1 >= m);
     const double2* ym = y0 - C5;
     double2 A1 = y0[0], B1 = y0[S], A2 = y0[2 * S], KE = y0[4 * S];
     double2 A1p = yp[0], B1p = yp[S], B2p = yp[3 * S];
     double2 A1m = hm ? ym[0] : czero(), B1m = hm ? ym[S] : czero(), B2m = hm ? ym[3 * S] : czero();
-    const double en = eps_nm(m, n), en1 = eps_nm(m, n + 1);
-    const double ia = 1.0 / a;
-    const double cp = n * en1, cm = (n + 1.0) * en;
-    double2 div1 = c_scale(c_add(c_imul(A1, (double)m), c_sub(c_scale(B1p, cp), c_scale(B1m, cm))), ia);
-    double2 curl1 = c_scale(c_add(c_imul(B1, (double)m), c_sub(c_scale(A1m, cm), c_scale(A1p, cp))), ia);
-    double2 div2 = c_scale(c_add(c_imul(A2, (double)m), c_sub(c_scale(B2p, cp), c_scale(B2m, cm))), ia);
+    const double* c = rc + rx * RC_NUM;
+    const double cp = c[RC_DCP], cm = c[RC_DCM], ma = m * ia;
+    // div = i m A/a + n eps_{n+1} B_{n+1}/a - (n+1) eps_n B_{n-1}/a ; curl likewise (A <-> B, sign)
     double2 N[3];
-    N[0] = c_scale(div2, -1.0);
-    N[1] = c_scale(div1, -1.0);
-    N[2] = c_add(curl1, c_scale(KE, (double)n * (n + 1.0) * ia * ia));
+    N[0] = make_double2(-fma(cp, B2p.x, fma(-cm, B2m.x, -ma * A2.y)), -fma(cp, B2p.y, fma(-cm, B2m.y, ma * A2.x)));
+    N[1] = make_double2(-fma(cp, B1p.x, fma(-cm, B1m.x, -ma * A1.y)), -fma(cp, B1p.y, fma(-cm, B1m.y, ma * A1.x)));
+    const double ke = (double)(n * (n + 1)) * ia * ia;
+    N[2] = make_double2(fma(cm, A1m.x, fma(-cp, A1p.x, fma(ke, KE.x, -ma * B1.y))),
+                        fma(cm, A1m.y, fma(-cp, A1p.y, fma(ke, KE.y, ma * B1.x))));
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
         int64_t i = ((int64_t)f * nc + r) * S + s;
@@ -210,7 +199,7 @@ __global__ void k_nl_post_kernel(const double2* __restrict__ Y, int mode, double
 // ------------------------------------------------------------------ linear operator
 // mode 0: out = L U ; mode 1: out = U + alpha L U
 __global__ void k_linop(StateView U, double2* __restrict__ out, const int* __restrict__ srow_m, int mode,
-                        double alpha, double a, double omega, double phibar) {
+                        double alpha, double ia2, double omega, double phibar, const double* __restrict__ rc) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int S = U.S, M = U.M;
     const int64_t nc = U.nc;
@@ -222,17 +211,19 @@ __global__ void k_linop(StateView U, double2* __restrict__ out, const int* __res
     double2 ph = U.get(0, m, n, s), xi = U.get(1, m, n, s), de = U.get(2, m, n, s);
     double2 xim = U.get(1, m, n - 1, s), xip = U.get(1, m, n + 1, s);
     double2 dem = U.get(2, m, n - 1, s), dep = U.get(2, m, n + 1, s);
+    const double* c = rc + (ex_off(m, M) + (n - m)) * RC_NUM;
     const double w2 = 2.0 * omega;
-    const double p = coef_p(m, n), q = coef_q(m, n), rr = coef_r(m, n);
+    const double p = w2 * c[RC_P], q = w2 * c[RC_Q], rr = w2 * c[RC_R];
+    const double lap = (double)(n * (n + 1)) * ia2;
     double2 L0 = c_scale(de, -phibar);
-    double2 L1 = c_add(c_scale(c_add(c_scale(dem, p), c_scale(dep, q)), -w2), c_imul(xi, w2 * rr));
-    double2 L2 = c_add(c_scale(ph, (double)n * (n + 1.0) / (a * a)),
-                       c_add(c_scale(c_add(c_scale(xim, p), c_scale(xip, q)), w2), c_imul(de, w2 * rr)));
+    double2 L1 = make_double2(-fma(p, dem.x, fma(q, dep.x, rr * xi.y)), -fma(p, dem.y, fma(q, dep.y, -rr * xi.x)));
+    double2 L2 = make_double2(fma(lap, ph.x, fma(p, xim.x, fma(q, xip.x, -rr * de.y))),
+                              fma(lap, ph.y, fma(p, xim.y, fma(q, xip.y, rr * de.x))));
     double2 o[3] = {L0, L1, L2};
     if (mode == 1) {
-        o[0] = c_add(ph, c_scale(L0, alpha));
-        o[1] = c_add(xi, c_scale(L1, alpha));
-        o[2] = c_add(de, c_scale(L2, alpha));
+        o[0] = make_double2(fma(alpha, L0.x, ph.x), fma(alpha, L0.y, ph.y));
+        o[1] = make_double2(fma(alpha, L1.x, xi.x), fma(alpha, L1.y, xi.y));
+        o[2] = make_double2(fma(alpha, L2.x, de.x), fma(alpha, L2.y, de.y));
     }
 #pragma unroll
     for (int f = 0; f < 3; ++f) out[((int64_t)f * nc + r) * S + s] = o[f];
@@ -538,20 +529,29 @@ swe_status k_unpack_scalar(const swe_plan* p, const double2* Y, double2* spec, i
 swe_status k_nl_pre(const swe_plan* p, const double2* Ua, const double2* Ub, double beta, double2* X, int S,
                     cudaStream_t st) {
     StateView v{Ua, Ub, beta, p->nc, S, p->M};
-    k_nl_pre_kernel<<<nblk(p->ncx * S), 256, 0, st>>>(v, X, p->row_m, p->ncx, p->a);
+    {
+        ProfToken tk_ = prof_begin("nl_pre", st, 0.0, 16.0 * S * (3.0 * p->nc * (beta != 0.0 ? 2.0 : 1.0) + 4.0 * p->ncx));
+        k_nl_pre_kernel<<<nblk(p->ncx * S), 256, 0, st>>>(v, X, p->row_m, p->ncx, p->rc);
+        prof_end(tk_, st);
+    }
     SWE_CHECK_LAUNCH("k_nl_pre");
     return SWE_OK;
 }
 swe_status k_nl_post(const swe_plan* p, const double2* Y, int mode, double dt, const double2* in0, const double2* in1,
                      double2* out0, double2* out1, int S, cudaStream_t st) {
-    k_nl_post_kernel<<<nblk(p->nc * S), 256, 0, st>>>(Y, mode, dt, in0, in1, out0, out1, p->srow_m, p->M, p->nc, S,
-                                                     p->a, p->flags);
+    {
+        ProfToken tk_ = prof_begin("nl_post", st, 0.0, 16.0 * S * (5.0 * p->ncx + 3.0 * p->nc * (in1 ? 4.0 : 3.0)));
+        k_nl_post_kernel<<<nblk(p->nc * S), 256, 0, st>>>(Y, mode, dt, in0, in1, out0, out1, p->srow_m, p->M, p->nc, S,
+                                                          1.0 / p->a, p->rc, p->flags);
+        prof_end(tk_, st);
+    }
     SWE_CHECK_LAUNCH("k_nl_post");
     return SWE_OK;
 }
 swe_status k_linear(const swe_plan* p, const double2* U, double2* LU, int S, cudaStream_t st) {
     StateView v{U, nullptr, 0.0, p->nc, S, p->M};
-    k_linop<<<nblk(p->nc * S), 256, 0, st>>>(v, LU, p->srow_m, 0, 0.0, p->a, p->omega, p->phibar);
+    k_linop<<<nblk(p->nc * S), 256, 0, st>>>(v, LU, p->srow_m, 0, 0.0, 1.0 / (p->a * p->a), p->omega, p->phibar,
+                                             p->rc);
     SWE_CHECK_LAUNCH("k_linop");
     return SWE_OK;
 }
@@ -589,7 +589,12 @@ swe_status k_implicit(swe_plan* p, double alpha, int with_rhs, const double2* in
             return SWE_EINVAL;
         }
         StateView v{in, nullptr, 0.0, p->nc, S, p->M};
-        k_linop<<<nblk(p->nc * S), 256, 0, st>>>(v, out, p->srow_m, 1, alpha, p->a, p->omega, p->phibar);
+        {
+            ProfToken tk_ = prof_begin("linop_rhs", st, 0.0, 16.0 * 6.0 * p->nc * S);
+            k_linop<<<nblk(p->nc * S), 256, 0, st>>>(v, out, p->srow_m, 1, alpha, 1.0 / (p->a * p->a), p->omega,
+                                                     p->phibar, p->rc);
+            prof_end(tk_, st);
+        }
         SWE_CHECK_LAUNCH("k_linop(rhs)");
         R = out;
     }
@@ -629,14 +634,22 @@ swe_status k_truncate(const double2* in, int Min, double2* out, int Mout, int S,
 
 swe_status k_aos_to_soa_strided(const swe_plan* p, const double2* in, int64_t stride, double2* out, int S,
                                 cudaStream_t st) {
-    k_aos_soa_strided<<<nblk(3 * p->nc * S), 256, 0, st>>>(in, stride, out, p->nc, S);
+    {
+        ProfToken tk_ = prof_begin("aos_soa", st, 0.0, 16.0 * 6.0 * p->nc * S);
+        k_aos_soa_strided<<<nblk(3 * p->nc * S), 256, 0, st>>>(in, stride, out, p->nc, S);
+        prof_end(tk_, st);
+    }
     SWE_CHECK_LAUNCH("k_aos_soa_strided");
     return SWE_OK;
 }
 
 swe_status k_soa_to_aos_strided(const swe_plan* p, const double2* in, double2* out, int64_t stride, const double2* add,
                                 int64_t add_stride, int S, cudaStream_t st) {
-    k_soa_aos_strided<<<nblk(3 * p->nc * S), 256, 0, st>>>(in, out, stride, add, add_stride, p->nc, S);
+    {
+        ProfToken tk_ = prof_begin("soa_aos", st, 0.0, 16.0 * (add ? 9.0 : 6.0) * p->nc * S);
+        k_soa_aos_strided<<<nblk(3 * p->nc * S), 256, 0, st>>>(in, out, stride, add, add_stride, p->nc, S);
+        prof_end(tk_, st);
+    }
     SWE_CHECK_LAUNCH("k_soa_aos_strided");
     return SWE_OK;
 }

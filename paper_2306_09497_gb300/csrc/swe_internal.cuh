@@ -47,6 +47,21 @@ __host__ __device__ inline int64_t nc_state(int M) { return (int64_t)(M + 1) * (
 __host__ __device__ inline int64_t nc_ext(int M) { return (int64_t)(M + 1) * (M + 4) / 2; }
 
 // epsilon_n^m = sqrt((n^2 - m^2) / (4 n^2 - 1)), zero for n <= m
+// Per extended row (m, n <= M+1) coefficient table, built once per plan in FP64 so that
+// the spectral kernels do no division or square root per element (GB300 runs FP64 at
+// 1/64 of the FP32 rate).  il_n = -a^2/(n(n+1)) for 1 <= n <= M, else 0.
+enum RowCoef {
+    RC_UC0 = 0,   // m il_n / a
+    RC_UCM = 1,   // (n-1) eps_n il_{n-1} / a       (n-1 >= m)
+    RC_UCP = 2,   // (n+2) eps_{n+1} il_{n+1} / a
+    RC_DCP = 3,   // n eps_{n+1} / a
+    RC_DCM = 4,   // (n+1) eps_n / a
+    RC_P = 5,     // p_n = (n+1)/n eps_n
+    RC_Q = 6,     // q_n = n/(n+1) eps_{n+1}
+    RC_R = 7,     // r_n = m/(n(n+1))
+    RC_NUM = 8
+};
+
 __host__ __device__ inline double eps_nm(int m, int n) {
     if (n <= m) return 0.0;
     double nn = (double)n, mm = (double)m;
@@ -90,8 +105,11 @@ struct swe_plan {
     Workspace ws;
     // device flags: [0] non-finite seen
     int* flags = nullptr;
-    // extended latitudes for semi-Lagrangian interpolation (built on first use)
-    double* thx = nullptr;
+    // row coefficients [ncx][RC_NUM] (see RowCoef)
+    double* rc = nullptr;
+    // semi-Lagrangian geometry in the grid type (extended latitudes, sin and cos of the
+    // Gaussian latitudes; built on first use)
+    void* thx = nullptr;
     // launch configuration of the fused nonlinear ring kernel (autotuned on first large call)
     int ring_cfg = -1, ring_G = 1;
 };
