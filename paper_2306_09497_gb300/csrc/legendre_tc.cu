@@ -18,12 +18,14 @@
 // Data movement: the Legendre operand (B) is pre-split and pre-tiled on the device
 // into the canonical no-swizzle K-major core-matrix layout and streamed into shared
 // memory by the bulk-copy engine (cp.async.bulk + mbarrier transaction counts);
-// the data operand (A) is loaded coalesced by the CTA's 128 threads (one per
-// column), split in registers and stored in the same layout.  One elected thread
-// issues tcgen05.mma (kind::f16, bf16 x bf16 -> f32, M = 128, K = 16) into two
-// TMEM accumulators (one per parity); a two-stage ring overlaps the operand
-// loads of chunk q+1 with the MMAs of chunk q; the epilogue reads TMEM with
-// tcgen05.ld and writes coalesced rows.  Every mbarrier wait is bounded: on
+// the data operand (A) is prefetched a few chunks ahead by per-thread cp.async
+// (coalesced rows; 4 threads per column, each a quarter of the chunk), then split
+// in registers and stored in the same layout.  One elected thread issues
+// tcgen05.mma (kind::f16, bf16 x bf16 -> f32, M = 128, K = 16) into two TMEM
+// accumulators (one per parity); a two-stage ring overlaps the split of chunk q+1
+// with the MMAs of chunk q; the epilogue reads TMEM with tcgen05.ld (16 warps,
+// each a lane quarter and a quarter of the accumulator columns) and writes
+// coalesced rows.  Every mbarrier wait is bounded: on
 // timeout the kernel sets an error flag, stops issuing work, releases its tensor
 // memory and returns.
 #include <cuda_bf16.h>
@@ -35,11 +37,16 @@
 namespace {
 
 constexpr int BM = 128;          // data columns per CTA (MMA M)
+constexpr int NTH = 512;         // threads per CTA: 4 per data column, each a quarter of a K chunk
+constexpr int KQ = 4;            // K values per thread per chunk
 constexpr int KC = 16;           // K per chunk (one MMA)
 constexpr int NPLANE = 3;        // bf16 split terms
 constexpr int NTERMS = 6;        // partial products kept
 constexpr uint32_t TMEM_COLS = 512;
 constexpr unsigned long long WAIT_LIMIT = 1ull << 22;   // bounded polling (about a second)
+constexpr int NR_INV = 3;        // raw data-operand prefetch depth, inverse (FP64 rows)
+constexpr int NR_FWD = 4;        // raw data-operand prefetch depth, forward (FP32 rows)
+constexpr int NT_MAX = 224;      // largest N tile (two parity accumulators + a 32-column read fit in 512)
 
 __constant__ int c_terms[NTERMS][2] = {{0, 0}, {0, 1}, {1, 0}, {0, 2}, {2, 0}, {1, 1}};
 
@@ -82,6 +89,19 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
+
+// per-thread asynchronous global -> shared copies (zero-filled when !pred)
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool pred) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(pred ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool pred) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(pred ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -151,19 +171,18 @@ __host__ __device__ __forceinline__ uint32_t tile_off(int row, int k) {
     return (uint32_t)((row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
-// Writes one thread's 16 values (its row of a 16-K chunk) as three bf16 planes.
-__device__ __forceinline__ void store_row_planes(unsigned char* plane0, uint32_t plane_bytes, int row, const float* v) {
-    __nv_bfloat16 h[NPLANE][KC];
+// Writes one thread's 4 consecutive K values (k0..k0+3, k0 a multiple of 4) of its row
+// as three bf16 planes (8-byte stores).
+__device__ __forceinline__ void store_quad_planes(unsigned char* plane0, uint32_t plane_bytes, int row, int k0,
+                                                  const float* v) {
+    __nv_bfloat16 h[NPLANE][KQ];
 #pragma unroll
-    for (int k = 0; k < KC; ++k) split3(v[k], h[0][k], h[1][k], h[2][k]);
+    for (int k = 0; k < KQ; ++k) split3(v[k], h[0][k], h[1][k], h[2][k]);
 #pragma unroll
     for (int pl = 0; pl < NPLANE; ++pl) {
-        unsigned char* base = plane0 + pl * plane_bytes;
-        uint4 lo, hi;
-        memcpy(&lo, &h[pl][0], 16);
-        memcpy(&hi, &h[pl][8], 16);
-        *reinterpret_cast<uint4*>(base + tile_off(row, 0)) = lo;
-        *reinterpret_cast<uint4*>(base + tile_off(row, 8)) = hi;
+        uint2 u;
+        memcpy(&u, &h[pl][0], 8);
+        *reinterpret_cast<uint2*>(plane0 + pl * plane_bytes + tile_off(row, k0)) = u;
     }
 }
 
@@ -172,10 +191,71 @@ struct TCShape {
     int nt;                      // N tile (multiple of 16, <= 256)
 };
 
+// Both kernels share one pipeline per 16-deep K chunk q (stage s = q mod 2 for the bf16
+// planes and the table tile, raw stage q mod NR for the unsplit data):
+//   every thread: cp.async its own column of chunk q+NR-1 (it alone reads that column,
+//                 so the raw ring needs no block barrier), wait for chunk q's copies;
+//   thread 0:     wait until the MMAs of chunk q-2 released stage s, then start the
+//                 bulk copy of chunk q's table tile into stage s;
+//   every thread: split its column of chunk q into three bf16 planes in stage s;
+//   thread 0:     wait for the table tile, issue 2 x 6 MMAs, commit to stage s's barrier.
+struct Pipe {
+    uint64_t* bar_tma;
+    uint64_t* bar_mma;
+};
+
+// tid 0: bounded drain of this CTA's copies and MMAs still in flight after a timeout
+__device__ __forceinline__ void drain(Pipe pp) {
+    for (int s2 = 0; s2 < 2; ++s2) {
+        mbar_wait(&pp.bar_tma[s2], 0);
+        mbar_wait(&pp.bar_mma[s2], 0);
+    }
+}
+
+// tid 0: 2 parities x 6 partial products of one chunk into the two accumulators
+__device__ __forceinline__ void issue_mmas(const unsigned char* sA, uint32_t a_plane, const unsigned char* sB,
+                                           uint32_t b_plane, uint32_t tmem, int acc_stride, uint32_t idesc,
+                                           bool first) {
+    tc_fence_after();
+#pragma unroll
+    for (int par = 0; par < 2; ++par) {
+        for (int t = 0; t < NTERMS; ++t) {
+            const unsigned char* a = sA + par * NPLANE * a_plane + c_terms[t][0] * a_plane;
+            const unsigned char* b = sB + par * NPLANE * b_plane + c_terms[t][1] * b_plane;
+            mma_bf16(tmem + par * acc_stride, smem_desc(a, 128, 256), smem_desc(b, 128, 256), idesc,
+                     (!first || t > 0) ? 1u : 0u);
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t tmem_setup(uint64_t* bars, uint32_t* tmem_slot, int tid) {
+    if (tid == 0) {
+        for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if ((tid >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    return *tmem_slot;
+}
+
+__device__ __forceinline__ void tmem_release(uint32_t tmem, int tid) {
+    tc_fence_before();
+    __syncthreads();
+    if ((tid >> 5) == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
 // ----------------------------------------------------------------------------- inverse
 // grid: (ceil(ncol/128), M+1, n-tiles over j).  Table Binv: for each m, chunk q, parity,
 // N-tile: a [nt x 16] bf16 tile x 3 planes, contiguous (offsets from inv_off[m]).
-__global__ void __launch_bounds__(128, 1) k_leg_inv_tc(const double* __restrict__ X, float* __restrict__ F,
+__global__ void __launch_bounds__(NTH, 1) k_leg_inv_tc(const double* __restrict__ X, float* __restrict__ F,
                                                        const unsigned char* __restrict__ Binv,
                                                        const long long* __restrict__ inv_off,
                                                        const int* __restrict__ inv_nq, TCShape sh, int* err) {
@@ -187,12 +267,13 @@ __global__ void __launch_bounds__(128, 1) k_leg_inv_tc(const double* __restrict_
     const uint32_t b_stage = 2 * NPLANE * b_plane;
     unsigned char* sA[2] = {smem, smem + a_stage};
     unsigned char* sB[2] = {smem + 2 * a_stage, smem + 2 * a_stage + b_stage};
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * a_stage + 2 * b_stage);
-    uint64_t* bar_tma = bars;          // [2]
-    uint64_t* bar_mma = bars + 2;      // [2]
+    double* raw = reinterpret_cast<double*>(smem + 2 * a_stage + 2 * b_stage);   // [NR][2][KC][BM]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(raw + NR_INV * 2 * KC * BM);
+    Pipe pp{bars, bars + 2};
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+    // thread (sub, col): data column col, K values 4 sub .. 4 sub + 3 of every chunk
+    const int tid = threadIdx.x, warp = tid >> 5, col = tid & (BM - 1), sub = tid >> 7;
     const int M = sh.M;
     const int m = M - (int)blockIdx.y;
     const int c0 = blockIdx.x * BM;
@@ -200,98 +281,87 @@ __global__ void __launch_bounds__(128, 1) k_leg_inv_tc(const double* __restrict_
     const int nq = inv_nq[m];
     const int Kx = M + 2 - m;                              // extended rows of this m
     const int64_t xrow0 = ex_off(m, M);
+    const int c = c0 + col;
+    const bool cin = c < sh.ncol;
 
-    if (tid == 0) {
-        mbar_init(&bar_tma[0], 1);
-        mbar_init(&bar_tma[1], 1);
-        mbar_init(&bar_mma[0], 1);
-        mbar_init(&bar_mma[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
+    // raw prefetch of chunk qq (rows n = m + par + 2k, k in [16 qq, 16 qq + 16)): this thread's
+    // column and quarter
+    auto prefetch = [&](int qq) {
+        if (qq < nq) {
+            double* r = raw + (qq % NR_INV) * (2 * KC * BM);
+#pragma unroll
+            for (int par = 0; par < 2; ++par)
+#pragma unroll
+                for (int i = 0; i < KQ; ++i) {
+                    const int kk = KQ * sub + i;
+                    const int rr = par + 2 * (KC * qq + kk);
+                    const bool pr = cin && rr < Kx;
+                    cp_async8(&r[(par * KC + kk) * BM + col], pr ? (const void*)&X[(xrow0 + rr) * sh.ncol + c] : X,
+                              pr);
+                }
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int qq = 0; qq < NR_INV - 1; ++qq) prefetch(qq);
+
+    const uint32_t tmem = tmem_setup(bars, tmem_slot, tid);
     const uint32_t idesc = make_idesc(nt);
     const unsigned char* Bm = Binv + inv_off[m] + (int64_t)blockIdx.z * 2 * NPLANE * b_plane;
     const int64_t bchunk = (int64_t)gridDim.z * 2 * NPLANE * b_plane;   // bytes per chunk over all n-tiles
     bool ok = true;
-    const int c = c0 + tid;
     for (int q = 0; q < nq && ok; ++q) {
         const int s = q & 1;
-        if (q >= 2) {
-            // stage s is free once the MMAs of chunk q-2 completed (one thread waits, all follow)
-            if (tid == 0) ok = mbar_wait(&bar_mma[s], ((q - 2) >> 1) & 1);
-            ok = __syncthreads_and(ok);
-            if (!ok) break;
-        }
+        prefetch(q + NR_INV - 1);
         if (tid == 0) {
-            mbar_expect_tx(&bar_tma[s], b_stage);
-            bulk_g2s(sB[s], Bm + (int64_t)q * bchunk, b_stage, &bar_tma[s]);
+            // stage s is free once the MMAs of chunk q-2 completed
+            if (q >= 2) ok = mbar_wait(&pp.bar_mma[s], ((q - 2) >> 1) & 1);
+            if (ok) {
+                mbar_expect_tx(&pp.bar_tma[s], b_stage);
+                bulk_g2s(sB[s], Bm + (int64_t)q * bchunk, b_stage, &pp.bar_tma[s]);
+            }
         }
-        // data operand: rows n = m + par + 2k, k in [16q, 16q+16)
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
+        cp_async_wait<NR_INV - 1>();
+        const double* r = raw + (q % NR_INV) * (2 * KC * BM);
 #pragma unroll
         for (int par = 0; par < 2; ++par) {
-            float v[KC];
+            float v[KQ];
 #pragma unroll
-            for (int kk = 0; kk < KC; ++kk) {
-                const int rr = par + 2 * (KC * q + kk);
-                v[kk] = (rr < Kx && c < sh.ncol) ? (float)X[(xrow0 + rr) * sh.ncol + c] : 0.f;
-            }
-            store_row_planes(sA[s] + par * NPLANE * a_plane, a_plane, tid, v);
+            for (int i = 0; i < KQ; ++i) v[i] = (float)r[(par * KC + KQ * sub + i) * BM + col];
+            store_quad_planes(sA[s] + par * NPLANE * a_plane, a_plane, col, KQ * sub, v);
         }
         fence_proxy_async();
         __syncthreads();
         if (tid == 0) {
-            ok = mbar_wait(&bar_tma[s], (q >> 1) & 1);
+            ok = mbar_wait(&pp.bar_tma[s], (q >> 1) & 1);
             if (ok) {
-                tc_fence_after();
-#pragma unroll
-                for (int par = 0; par < 2; ++par) {
-                    for (int t = 0; t < NTERMS; ++t) {
-                        const unsigned char* a = sA[s] + par * NPLANE * a_plane + c_terms[t][0] * a_plane;
-                        const unsigned char* b = sB[s] + par * NPLANE * b_plane + c_terms[t][1] * b_plane;
-                        mma_bf16(tmem + par * nt, smem_desc(a, 128, 256), smem_desc(b, 128, 256), idesc,
-                                 (q > 0 || t > 0) ? 1u : 0u);
-                    }
-                }
-                mma_commit(&bar_mma[s]);
+                issue_mmas(sA[s], a_plane, sB[s], b_plane, tmem, nt, idesc, q == 0);   // nt: multiple of 32
+                mma_commit(&pp.bar_mma[s]);
             }
         }
-        // broadcast a timeout seen by the issuing thread
-        ok = __syncthreads_and(ok);
     }
+    cp_async_wait<0>();
     if (tid == 0) {
-        if (ok && nq > 0) {
-            ok = mbar_wait(&bar_mma[(nq - 1) & 1], ((nq - 1) >> 1) & 1);
-        } else if (!ok) {
-            // bounded drain of this CTA's own copies and MMAs still in flight
-            for (int s2 = 0; s2 < 2; ++s2) {
-                mbar_wait(&bar_tma[s2], 0);
-                mbar_wait(&bar_mma[s2], 0);
-            }
-        }
+        if (ok && nq > 0) ok = mbar_wait(&pp.bar_mma[(nq - 1) & 1], ((nq - 1) >> 1) & 1);
+        if (!ok) drain(pp);
     }
     ok = __syncthreads_and(ok);
     tc_fence_after();
     if (ok) {
-        // epilogue: warp w owns TMEM lanes (= data columns) 32w..32w+31
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-        for (int j0 = 0; j0 < nt; j0 += 32) {
+        // epilogue: warp w reads TMEM lanes (= data columns) 32 (w mod 4) .. + 31, and the
+        // 32-column groups j0 = 32 sub + 128 i of the accumulators
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        for (int j0 = 32 * sub; j0 < nt; j0 += 128) {
             float e[32], o[32];
             tmem_ld32(tmem + lane_base + (uint32_t)j0, e);
             tmem_ld32(tmem + lane_base + (uint32_t)(nt + j0), o);
-            if (c < sh.ncol) {
+            if (cin) {
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
                     const int j = jt0 + j0 + i;
-                    if (j < sh.nlat2) {
+                    if (j0 + i < nt && j < sh.nlat2) {
                         F[((int64_t)m * sh.nlat + j) * sh.ncol + c] = e[i] + o[i];
                         F[((int64_t)m * sh.nlat + (sh.nlat - 1 - j)) * sh.ncol + c] = e[i] - o[i];
                     }
@@ -301,147 +371,135 @@ __global__ void __launch_bounds__(128, 1) k_leg_inv_tc(const double* __restrict_
     } else if (tid == 0) {
         atomicOr(err, 2);
     }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    tmem_release(tmem, tid);
 }
 
 // ----------------------------------------------------------------------------- forward
-// grid: (ceil(ncol/128), M+1, n-tiles over k).  Table Bfwd: for each m, j-chunk q, parity,
-// N-tile: a [nt x 16] tile x 3 planes (rows k = degree index within the parity).
-__global__ void __launch_bounds__(128, 1) k_leg_fwd_tc(const float* __restrict__ F, double* __restrict__ Y,
+// grid: (ceil(ncol/128), M+1, max n-tiles over k).  Table Bfwd: for each m, j-chunk q,
+// n-tile z, parity: a [nt_m x 16] tile x 3 planes (rows k = degree index within the
+// parity); nt_m = fwd_nt[m] follows the number of degrees of m (multiple of 16).
+__global__ void __launch_bounds__(NTH, 1) k_leg_fwd_tc(const float* __restrict__ F, double* __restrict__ Y,
                                                        const unsigned char* __restrict__ Bfwd,
                                                        const long long* __restrict__ fwd_off,
-                                                       const int* __restrict__ fwd_ntiles, TCShape sh, int* err) {
+                                                       const int* __restrict__ fwd_ntiles,
+                                                       const int* __restrict__ fwd_nt, TCShape sh, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const int nt = sh.nt;
+    const int M = sh.M;
+    const int m = M - (int)blockIdx.y;
+    const int nz = fwd_ntiles[m];
+    if ((int)blockIdx.z >= nz) return;                     // uniform for the CTA: before any barrier
+    const int nt = fwd_nt[m];
+    const int acc = (nt + 31) & ~31;                       // TMEM column offset of the parity-1 accumulator
     const uint32_t a_plane = BM * KC * 2;
     const uint32_t b_plane = (uint32_t)nt * KC * 2;
     const uint32_t a_stage = 2 * NPLANE * a_plane;
     const uint32_t b_stage = 2 * NPLANE * b_plane;
+    const uint32_t b_stage_max = 2 * NPLANE * (uint32_t)sh.nt * KC * 2;
     unsigned char* sA[2] = {smem, smem + a_stage};
-    unsigned char* sB[2] = {smem + 2 * a_stage, smem + 2 * a_stage + b_stage};
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * a_stage + 2 * b_stage);
-    uint64_t* bar_tma = bars;
-    uint64_t* bar_mma = bars + 2;
+    unsigned char* sB[2] = {smem + 2 * a_stage, smem + 2 * a_stage + b_stage_max};
+    float* raw = reinterpret_cast<float*>(smem + 2 * a_stage + 2 * b_stage_max);   // [NR][2 KC][BM]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(raw + NR_FWD * 2 * KC * BM);
+    Pipe pp{bars, bars + 2};
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
 
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int M = sh.M;
-    const int m = M - (int)blockIdx.y;
-    if ((int)blockIdx.z >= fwd_ntiles[m]) return;          // uniform for the CTA: before any barrier
+    const int tid = threadIdx.x, warp = tid >> 5, col = tid & (BM - 1), sub = tid >> 7;
     const int c0 = blockIdx.x * BM;
     const int kt0 = blockIdx.z * nt;
     const int nq = (sh.nlat2 + KC - 1) / KC;
     const int Kx = M + 2 - m;
     const int64_t yrow0 = ex_off(m, M);
-
-    if (tid == 0) {
-        mbar_init(&bar_tma[0], 1);
-        mbar_init(&bar_tma[1], 1);
-        mbar_init(&bar_mma[0], 1);
-        mbar_init(&bar_mma[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
-    const uint32_t idesc = make_idesc(nt);
-    const unsigned char* Bm = Bfwd + fwd_off[m] + (int64_t)blockIdx.z * 2 * NPLANE * b_plane;
-    const int64_t bchunk = (int64_t)fwd_ntiles[m] * 2 * NPLANE * b_plane;
-    bool ok = true;
-    const int c = c0 + tid;
+    const int c = c0 + col;
+    const bool cin = c < sh.ncol;
     const float* Fm = F + (int64_t)m * sh.nlat * sh.ncol;
+
+    // raw prefetch of chunk qq: rows j = 16 qq + jj (north) and nlat-1-j (south), this thread's
+    // column and quarter
+    auto prefetch = [&](int qq) {
+        if (qq < nq) {
+            float* r = raw + (qq % NR_FWD) * (2 * KC * BM);
+#pragma unroll
+            for (int i = 0; i < KQ; ++i) {
+                const int jj = KQ * sub + i;
+                const int j = KC * qq + jj;
+                const bool pr = cin && j < sh.nlat2;
+                cp_async4(&r[jj * BM + col], pr ? (const void*)&Fm[(int64_t)j * sh.ncol + c] : F, pr);
+                cp_async4(&r[(KC + jj) * BM + col],
+                          pr ? (const void*)&Fm[(int64_t)(sh.nlat - 1 - j) * sh.ncol + c] : F, pr);
+            }
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int qq = 0; qq < NR_FWD - 1; ++qq) prefetch(qq);
+
+    const uint32_t tmem = tmem_setup(bars, tmem_slot, tid);
+    const uint32_t idesc = make_idesc(nt);
+    const unsigned char* Bm = Bfwd + fwd_off[m] + (int64_t)blockIdx.z * b_stage;
+    const int64_t bchunk = (int64_t)nz * b_stage;
+    bool ok = true;
     for (int q = 0; q < nq && ok; ++q) {
         const int s = q & 1;
-        if (q >= 2) {
-            // stage s is free once the MMAs of chunk q-2 completed (one thread waits, all follow)
-            if (tid == 0) ok = mbar_wait(&bar_mma[s], ((q - 2) >> 1) & 1);
-            ok = __syncthreads_and(ok);
-            if (!ok) break;
-        }
+        prefetch(q + NR_FWD - 1);
         if (tid == 0) {
-            mbar_expect_tx(&bar_tma[s], b_stage);
-            bulk_g2s(sB[s], Bm + (int64_t)q * bchunk, b_stage, &bar_tma[s]);
-        }
-        float vs[KC], va[KC];
-#pragma unroll
-        for (int jj = 0; jj < KC; ++jj) {
-            const int j = KC * q + jj;
-            float fn = 0.f, fs = 0.f;
-            if (j < sh.nlat2 && c < sh.ncol) {
-                fn = Fm[(int64_t)j * sh.ncol + c];
-                fs = Fm[(int64_t)(sh.nlat - 1 - j) * sh.ncol + c];
-            }
-            vs[jj] = fn + fs;
-            va[jj] = fn - fs;
-        }
-        store_row_planes(sA[s], a_plane, tid, vs);
-        store_row_planes(sA[s] + NPLANE * a_plane, a_plane, tid, va);
-        fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-            ok = mbar_wait(&bar_tma[s], (q >> 1) & 1);
+            if (q >= 2) ok = mbar_wait(&pp.bar_mma[s], ((q - 2) >> 1) & 1);
             if (ok) {
-                tc_fence_after();
-#pragma unroll
-                for (int par = 0; par < 2; ++par) {
-                    for (int t = 0; t < NTERMS; ++t) {
-                        const unsigned char* a = sA[s] + par * NPLANE * a_plane + c_terms[t][0] * a_plane;
-                        const unsigned char* b = sB[s] + par * NPLANE * b_plane + c_terms[t][1] * b_plane;
-                        mma_bf16(tmem + par * nt, smem_desc(a, 128, 256), smem_desc(b, 128, 256), idesc,
-                                 (q > 0 || t > 0) ? 1u : 0u);
-                    }
-                }
-                mma_commit(&bar_mma[s]);
+                mbar_expect_tx(&pp.bar_tma[s], b_stage);
+                bulk_g2s(sB[s], Bm + (int64_t)q * bchunk, b_stage, &pp.bar_tma[s]);
             }
         }
         ok = __syncthreads_and(ok);
-    }
-    if (tid == 0) {
-        if (ok && nq > 0) {
-            ok = mbar_wait(&bar_mma[(nq - 1) & 1], ((nq - 1) >> 1) & 1);
-        } else if (!ok) {
-            // bounded drain of this CTA's own copies and MMAs still in flight
-            for (int s2 = 0; s2 < 2; ++s2) {
-                mbar_wait(&bar_tma[s2], 0);
-                mbar_wait(&bar_mma[s2], 0);
+        if (!ok) break;
+        cp_async_wait<NR_FWD - 1>();
+        const float* r = raw + (q % NR_FWD) * (2 * KC * BM);
+        float vs[KQ], va[KQ];
+#pragma unroll
+        for (int i = 0; i < KQ; ++i) {
+            const int jj = KQ * sub + i;
+            const float fn = r[jj * BM + col], fs = r[(KC + jj) * BM + col];
+            vs[i] = fn + fs;
+            va[i] = fn - fs;
+        }
+        store_quad_planes(sA[s], a_plane, col, KQ * sub, vs);
+        store_quad_planes(sA[s] + NPLANE * a_plane, a_plane, col, KQ * sub, va);
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            ok = mbar_wait(&pp.bar_tma[s], (q >> 1) & 1);
+            if (ok) {
+                issue_mmas(sA[s], a_plane, sB[s], b_plane, tmem, acc, idesc, q == 0);
+                mma_commit(&pp.bar_mma[s]);
             }
         }
+    }
+    cp_async_wait<0>();
+    if (tid == 0) {
+        if (ok && nq > 0) ok = mbar_wait(&pp.bar_mma[(nq - 1) & 1], ((nq - 1) >> 1) & 1);
+        if (!ok) drain(pp);
     }
     ok = __syncthreads_and(ok);
     tc_fence_after();
     if (ok) {
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-        for (int k0 = 0; k0 < nt; k0 += 32) {
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        for (int k0 = 32 * sub; k0 < nt; k0 += 128) {
             float d0[32], d1[32];
             tmem_ld32(tmem + lane_base + (uint32_t)k0, d0);
-            tmem_ld32(tmem + lane_base + (uint32_t)(nt + k0), d1);
-            if (c < sh.ncol) {
+            tmem_ld32(tmem + lane_base + (uint32_t)(acc + k0), d1);
+            if (cin) {
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
                     const int k = kt0 + k0 + i;
                     const int r0 = 2 * k, r1 = 2 * k + 1;        // extended-row offsets of parities 0 / 1
-                    if (r0 < Kx) Y[(yrow0 + r0) * sh.ncol + c] = (double)d0[i];
-                    if (r1 < Kx) Y[(yrow0 + r1) * sh.ncol + c] = (double)d1[i];
+                    if (k0 + i < nt) {
+                        if (r0 < Kx) Y[(yrow0 + r0) * sh.ncol + c] = (double)d0[i];
+                        if (r1 < Kx) Y[(yrow0 + r1) * sh.ncol + c] = (double)d1[i];
+                    }
                 }
             }
         }
     } else if (tid == 0) {
         atomicOr(err, 2);
     }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    tmem_release(tmem, tid);
 }
 
 // ----------------------------------------------------------------------------- table builders
@@ -476,12 +534,14 @@ __global__ void k_build_inv_table(const double* __restrict__ P, unsigned char* _
     }
 }
 
-// Forward table: element (k, jj) of tile (m, q, tile z, par, plane) = P_{m+par+2k}(mu_{16q+jj}), k = z*nt + row
+// Forward table: element (k, jj) of tile (m, q, tile z, par, plane) = P_{m+par+2k}(mu_{16q+jj}),
+// k = z*nt_m + row
 __global__ void k_build_fwd_table(const double* __restrict__ P, unsigned char* __restrict__ T,
-                                  const long long* __restrict__ fwd_off, const int* __restrict__ fwd_ntiles, int M,
-                                  int nlat2, int nt) {
+                                  const long long* __restrict__ fwd_off, const int* __restrict__ fwd_ntiles,
+                                  const int* __restrict__ fwd_nt, int M, int nlat2) {
     const int m = blockIdx.y;
     const int nz = fwd_ntiles[m];
+    const int nt = fwd_nt[m];
     const int nq = (nlat2 + KC - 1) / KC;
     const uint32_t b_plane = (uint32_t)nt * KC * 2;
     const int64_t total = (int64_t)nq * nz * 2 * nt * KC;
@@ -513,53 +573,57 @@ __global__ void k_build_fwd_table(const double* __restrict__ P, unsigned char* _
 
 // ----------------------------------------------------------------------------- host side
 struct SplitTables {
-    int nt_inv, ntiles_inv, nt_fwd;
+    int nt_inv, ntiles_inv, nt_fwd, nz_fwd;   // nt_fwd, nz_fwd: largest over m
     unsigned char* inv = nullptr;
     unsigned char* fwd = nullptr;
     long long* inv_off = nullptr;
     int* inv_nq = nullptr;
     long long* fwd_off = nullptr;
     int* fwd_ntiles = nullptr;
+    int* fwd_nt = nullptr;
     int* err = nullptr;
     size_t smem_inv = 0, smem_fwd = 0;
 };
 
 static int round16(int x) { return (x + 15) / 16 * 16; }
 
-static size_t tc_smem(int nt) {
+// planes (2 stages) + table tiles (2 stages) + raw prefetch ring + barriers
+static size_t tc_smem(int nt, size_t raw_stage, int nr) {
     size_t a_stage = 2 * NPLANE * BM * KC * 2, b_stage = 2 * NPLANE * (size_t)nt * KC * 2;
-    return 2 * a_stage + 2 * b_stage + 64;
+    return 2 * a_stage + 2 * b_stage + (size_t)nr * raw_stage + 64;
 }
 
 swe_status split_tables_build(swe_plan* p) {
     if (p->Pbf) return SWE_OK;
     SplitTables* t = new SplitTables();
     const int M = p->M;
-    // inverse: N tiles over the northern latitudes, at most 256 (here: equal tiles)
-    int ntiles = (p->nlat2 + 255) / 256;
+    // inverse: N tiles over the northern latitudes, at most 192 (equal tiles), so that the
+    // table stages and a three-deep FP64 prefetch ring fit in shared memory
+    int ntiles = (p->nlat2 + 191) / 192;
     t->ntiles_inv = ntiles;
     t->nt_inv = round16((p->nlat2 + ntiles - 1) / ntiles);
     if (t->nt_inv % 32) t->nt_inv = (t->nt_inv + 31) / 32 * 32;   // epilogue reads 32 columns at a time
-    // forward: N tiles over the degree index within a parity; K_par <= (M + 2 - m + 1) / 2
-    t->nt_fwd = 0;
+    // forward: N tiles over the degree index within a parity, sized per m to its
+    // K_par = ceil((M + 2 - m) / 2) degrees (multiple of 16, at most NT_MAX)
     std::vector<long long> ioff(M + 1), foff(M + 1);
-    std::vector<int> inq(M + 1), fnt(M + 1);
+    std::vector<int> inq(M + 1), fnt(M + 1), fnz(M + 1);
     const int nqf = (p->nlat2 + KC - 1) / KC;
-    int kmax0 = (M + 2 + 1) / 2;                                   // K_par for m = 0
-    int nzf = (kmax0 + 255) / 256;
-    t->nt_fwd = round16((kmax0 + nzf - 1) / nzf);
-    if (t->nt_fwd % 32) t->nt_fwd = (t->nt_fwd + 31) / 32 * 32;
+    t->nt_fwd = 16;
+    t->nz_fwd = 1;
     long long oi = 0, of = 0;
-    const long long binv = 2LL * NPLANE * t->nt_inv * KC * 2, bfwd = 2LL * NPLANE * t->nt_fwd * KC * 2;
+    const long long binv = 2LL * NPLANE * t->nt_inv * KC * 2;
     for (int m = 0; m <= M; ++m) {
         int Kx = M + 2 - m;                 // extended rows
         int Kpar = (Kx + 1) / 2;            // rows in the larger parity
         inq[m] = (Kpar + KC - 1) / KC;
         ioff[m] = oi;
         oi += (long long)inq[m] * ntiles * binv;
-        fnt[m] = (Kpar + t->nt_fwd - 1) / t->nt_fwd;
+        fnz[m] = (Kpar + NT_MAX - 1) / NT_MAX;
+        fnt[m] = round16((Kpar + fnz[m] - 1) / fnz[m]);
+        t->nt_fwd = std::max(t->nt_fwd, fnt[m]);
+        t->nz_fwd = std::max(t->nz_fwd, fnz[m]);
         foff[m] = of;
-        of += (long long)nqf * fnt[m] * bfwd;
+        of += (long long)nqf * fnz[m] * 2LL * NPLANE * fnt[m] * KC * 2;
     }
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc((void**)&t->inv, oi);
@@ -568,11 +632,13 @@ swe_status split_tables_build(swe_plan* p) {
     if (e == cudaSuccess) e = cudaMalloc((void**)&t->inv_nq, sizeof(int) * (M + 1));
     if (e == cudaSuccess) e = cudaMalloc((void**)&t->fwd_off, sizeof(long long) * (M + 1));
     if (e == cudaSuccess) e = cudaMalloc((void**)&t->fwd_ntiles, sizeof(int) * (M + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&t->fwd_nt, sizeof(int) * (M + 1));
     if (e == cudaSuccess) e = cudaMalloc((void**)&t->err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(t->inv_off, ioff.data(), sizeof(long long) * (M + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(t->inv_nq, inq.data(), sizeof(int) * (M + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(t->fwd_off, foff.data(), sizeof(long long) * (M + 1), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(t->fwd_ntiles, fnt.data(), sizeof(int) * (M + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(t->fwd_ntiles, fnz.data(), sizeof(int) * (M + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(t->fwd_nt, fnt.data(), sizeof(int) * (M + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(t->err, 0, sizeof(int));
     if (e != cudaSuccess) {
         cudaFree(t->inv);
@@ -581,17 +647,23 @@ swe_status split_tables_build(swe_plan* p) {
         cudaFree(t->inv_nq);
         cudaFree(t->fwd_off);
         cudaFree(t->fwd_ntiles);
+        cudaFree(t->fwd_nt);
         cudaFree(t->err);
         delete t;
         return swe_cuda_status(e, "split tables");
     }
     k_build_inv_table<<<dim3(256, M + 1), 256>>>(p->P, t->inv, t->inv_off, t->inv_nq, M, p->nlat2, t->nt_inv,
                                                   ntiles);
-    k_build_fwd_table<<<dim3(256, M + 1), 256>>>(p->P, t->fwd, t->fwd_off, t->fwd_ntiles, M, p->nlat2, t->nt_fwd);
+    k_build_fwd_table<<<dim3(256, M + 1), 256>>>(p->P, t->fwd, t->fwd_off, t->fwd_ntiles, t->fwd_nt, M, p->nlat2);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    t->smem_inv = tc_smem(t->nt_inv);
-    t->smem_fwd = tc_smem(t->nt_fwd);
+    t->smem_inv = tc_smem(t->nt_inv, 2 * KC * BM * sizeof(double), NR_INV);
+    t->smem_fwd = tc_smem(t->nt_fwd, 2 * KC * BM * sizeof(float), NR_FWD);
+    if (t->smem_inv > 227 * 1024 || t->smem_fwd > 227 * 1024) {
+        p->Pbf = t;
+        swe_set_error("split tables: shared-memory footprint %zu / %zu B exceeds 227 KB", t->smem_inv, t->smem_fwd);
+        return SWE_EINVAL;
+    }
     // at least ~116 KB of shared memory so that a single CTA (holding all 512 TMEM columns) runs per SM
     const size_t one_per_sm = 116 * 1024;
     if (t->smem_inv < one_per_sm) t->smem_inv = one_per_sm;
@@ -612,6 +684,7 @@ void split_tables_free(swe_plan* p) {
     cudaFree(t->inv_nq);
     cudaFree(t->fwd_off);
     cudaFree(t->fwd_ntiles);
+    cudaFree(t->fwd_nt);
     cudaFree(t->err);
     delete t;
     p->Pbf = nullptr;
@@ -630,7 +703,7 @@ swe_status leg_inverse_split(const swe_plan* p, const double2* X, float2* F, int
     // the dynamic shared-memory limit is a per-function attribute shared by all plans: set it per launch
     SWE_CHECK_CUDA(cudaFuncSetAttribute(k_leg_inv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_inv));
     ProfToken tk = prof_begin("leg_inv_tc", st, fl, by);
-    k_leg_inv_tc<<<grid, BM, t->smem_inv, st>>>((const double*)X, (float*)F, t->inv, t->inv_off, t->inv_nq, sh,
+    k_leg_inv_tc<<<grid, NTH, t->smem_inv, st>>>((const double*)X, (float*)F, t->inv, t->inv_off, t->inv_nq, sh,
                                                 t->err);
     prof_end(tk, st);
     SWE_CHECK_LAUNCH("k_leg_inv_tc");
@@ -644,14 +717,13 @@ swe_status leg_forward_split(const swe_plan* p, const float2* F, double2* Y, int
         return SWE_EINVAL;
     }
     TCShape sh{p->M, p->nlat, p->nlat2, 2 * C, t->nt_fwd};
-    const int kmax0 = (p->M + 2 + 1) / 2;
-    dim3 grid((sh.ncol + BM - 1) / BM, p->M + 1, (kmax0 + t->nt_fwd - 1) / t->nt_fwd);
+    dim3 grid((sh.ncol + BM - 1) / BM, p->M + 1, t->nz_fwd);
     const double fl = (double)C * p->nlat * (p->M + 1.0) * (p->M + 2.0);
     const double by = 8.0 * C * (p->M + 1.0) * p->nlat + 16.0 * C * p->ncx;
     SWE_CHECK_CUDA(cudaFuncSetAttribute(k_leg_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_fwd));
     ProfToken tk = prof_begin("leg_fwd_tc", st, fl, by);
-    k_leg_fwd_tc<<<grid, BM, t->smem_fwd, st>>>((const float*)F, (double*)Y, t->fwd, t->fwd_off, t->fwd_ntiles, sh,
-                                                t->err);
+    k_leg_fwd_tc<<<grid, NTH, t->smem_fwd, st>>>((const float*)F, (double*)Y, t->fwd, t->fwd_off, t->fwd_ntiles,
+                                                t->fwd_nt, sh, t->err);
     prof_end(tk, st);
     SWE_CHECK_LAUNCH("k_leg_fwd_tc");
     return SWE_OK;

@@ -85,3 +85,42 @@ def test_split_imex_propagation_height_bound(M, nlat, nlon, nsteps):
         assert err[0] < 1e-6, err
         assert err[1] < 1e-5 and err[2] < 1e-5, err
     plan.close()
+
+
+def test_split_tiled_shapes_match_fp64_path():
+    """T447 on a 450 x 1024 grid: the inverse contraction runs in two latitude tiles and the
+    forward one in two degree tiles for the low wavenumbers.  Beyond the oracle's sizes, so
+    the split path is held to the FP64 path (itself oracle-pinned at T31-T255)."""
+    from paper_2306_09497_gb300 import swe
+    M, nlat, nlon = 447, 450, 1024
+    p64 = swe.Plan(M, nlat, nlon, prec=swe.SWE_FP64)
+    pmx = swe.Plan(M, nlat, nlon, prec=swe.SWE_SPLIT_BF16X3)
+    try:
+        B = 3
+        coef = _dev(inputs.random_coeffs(M, B, seed=23))
+        g64 = torch.empty((B, nlat, nlon), dtype=torch.float64, device="cuda")
+        gmx = torch.empty((B, nlat, nlon), dtype=torch.float32, device="cuda")
+        p64.sht_inverse(coef, g64, B)
+        pmx.sht_inverse(coef, gmx, B)
+        ref = g64.cpu().numpy()
+        got = gmx.cpu().numpy().astype(np.float64)
+        # FP32 accumulation over K = (M + 2)/2 = 224 degrees per parity and an FP32 FFT of
+        # length 1024: worst-case rounding (224 + 10) 2^-24 = 1.4e-5 of the largest value;
+        # held at 5e-6 (T255 with half the K holds 1e-6 above)
+        err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+        assert err < 5e-6, err
+
+        g = inputs.random_grid(nlat, nlon, B, seed=24).astype(np.float32)
+        s64 = torch.empty((B, p64.nc * 2), dtype=torch.float64, device="cuda")
+        smx = torch.empty((B, pmx.nc * 2), dtype=torch.float64, device="cuda")
+        p64.sht_forward(torch.from_numpy(g.astype(np.float64)).cuda(), s64, B)
+        pmx.sht_forward(torch.from_numpy(g).cuda(), smx, B)
+        ref = s64.cpu().numpy()
+        got = smx.cpu().numpy()
+        # white noise, as in test_split_sht_forward, with the cancellation factor
+        # sqrt(nlat nlon) 1.25 times that of T255 and K = 225 latitudes per hemisphere
+        err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+        assert err < 1e-5, err
+    finally:
+        p64.close()
+        pmx.close()
