@@ -346,6 +346,313 @@ __global__ void __launch_bounds__(NT, MINB) k_ring_nl_g(const typename CT<T>::V*
     }
 }
 
+// ---------------------------------------------------------------------------
+// Lane-group FP32 path for H = nlon/2 = 12 T, T in {8, 16, 32}: T lanes of one warp own
+// one ring and every lane holds 12 values in registers.  Each H-point transform is a
+// Stockham sequence of passes (radix R, span Ns): butterfly j reads x[j + r H/R],
+// applies e^{-+2 pi i r (j mod Ns) / (Ns R)} and writes y[(j - j mod Ns) R + j mod Ns + r Ns];
+// lane t takes the butterflies j = t + T b.  Between passes the values go through a
+// padded per-ring shared-memory buffer (index i + i/16 against bank conflicts), with
+// a warp barrier only, since a ring never leaves its warp.
+//   inverse radices 12, then T = 32: 4 4 2 | 16: 4 4 | 8: 4 2 ; the first pass takes the
+//     c2r-prepared spectrum straight from the staged modes, the last keeps its outputs
+//     in registers (lane t, register b R + r: grid pair n = t + T (b + r 12/R));
+//   forward radices in the reverse order, so its first pass reads exactly that register
+//     layout, and its last (radix 12, span T) leaves X_{t + T r} in register r, whose
+//     r2c partner X_{H-k} is register 11 - r of lane T - t (one shuffle per r).
+// The grid products of the nonlinear terms are taken in registers.  Twiddles of each
+// pass live in a shared table ordered by (j mod Ns, r).  Each block holds G = 128 / T
+// rings (G consecutive slices of one latitude), so every (mode, field) access of the
+// block touches G contiguous columns.
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+template <int S> __device__ __forceinline__ float2 twd(float2 w) { return S > 0 ? f2(w.x, -w.y) : w; }
+
+template <int R, int S> __device__ __forceinline__ void bfly(float2 (&v)[R]) {
+    if constexpr (R == 2) {
+        float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (R == 3) {
+        const float h = 0.86602540378443864676f;
+        float2 t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
+        float2 a = f2(v[0].x - 0.5f * t1.x, v[0].y - 0.5f * t1.y);
+        float2 b = cmul_si<S>(f2(h * t2.x, h * t2.y));
+        v[0] = cadd(v[0], t1);
+        v[1] = cadd(a, b);
+        v[2] = csub(a, b);
+    } else if constexpr (R == 4) {
+        float2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+        float2 b0 = cadd(v[1], v[3]), b1 = cmul_si<S>(csub(v[1], v[3]));
+        v[0] = cadd(a0, b0);
+        v[1] = cadd(a1, b1);
+        v[2] = csub(a0, b0);
+        v[3] = csub(a1, b1);
+    } else {   // R == 12 = 4 x 3: radix-4 over stride 3, twiddles e^{-+2 pi i q p / 12}, radix-3 over stride 1
+        const float c = 0.86602540378443864676f;
+        float2 u[12];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            float2 w4[4] = {v[q], v[q + 3], v[q + 6], v[q + 9]};
+            bfly<4, S>(w4);
+#pragma unroll
+            for (int p = 0; p < 4; ++p) u[4 * q + p] = w4[p];
+        }
+        // twiddle e^{S 2 pi i q p / 12} for q = 1, 2 and p = 1..3 (angles 30, 60, 90, 120, 180 degrees)
+        const float2 w30 = f2(c, S * 0.5f), w60 = f2(0.5f, S * c);
+        u[5] = cmul(u[5], w30);
+        u[6] = cmul(u[6], w60);
+        u[7] = cmul_si<S>(u[7]);
+        u[9] = cmul(u[9], w60);
+        u[10] = cmul(u[10], f2(-0.5f, S * c));
+        u[11] = f2(-u[11].x, -u[11].y);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            float2 w3[3] = {u[p], u[4 + p], u[8 + p]};
+            bfly<3, S>(w3);
+            v[p] = w3[0];
+            v[p + 4] = w3[1];
+            v[p + 8] = w3[2];
+        }
+    }
+}
+
+constexpr int EL = 12;                 // values per lane
+__device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
+
+// One Stockham pass over a ring of H = 12 T values.  Register b R + r holds input
+// x[j_b + r H/R] (LOAD: read from buf first) and receives output y[(j_b - k) R + k + r Ns]
+// (STORE: written to buf instead).
+template <int T, int R, int Ns, int S, bool LOAD, bool STORE>
+__device__ __forceinline__ void spass(float2 (&a)[EL], float2* buf, const float2* twp, int t) {
+    constexpr int H = EL * T, NB = EL / R;
+    if constexpr (LOAD) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int r = 0; r < R; ++r) a[b * R + r] = buf[padi(t + T * b + r * (H / R))];
+        if constexpr (STORE) __syncwarp();
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int j = t + T * b;
+        const int k = (Ns == 1) ? 0 : j % Ns;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = a[b * R + r];
+        if constexpr (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twd<S>(twp[k * (R - 1) + r - 1]));
+        }
+        bfly<R, S>(v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if constexpr (STORE) buf[padi((j - k) * R + k + r * Ns)] = v[r];
+            else a[b * R + r] = v[r];
+        }
+    }
+}
+
+// twiddle-table layout per T: offsets of the passes' tables (entries (Ns)(R-1))
+template <int T> struct RingTw;
+template <> struct RingTw<32> { static constexpr int i1 = 0, i2 = 36, i3 = 180, f1 = 372, f2 = 378, f3 = 402, n = 754; };
+template <> struct RingTw<16> { static constexpr int i1 = 0, i2 = 36, f1 = 180, f2 = 192, n = 368; };
+template <> struct RingTw<8> { static constexpr int i1 = 0, i2 = 36, f1 = 84, f2 = 90, n = 178; };
+
+// entries e^{-2 pi i r k / (Ns R)}, k < Ns, r = 1..R-1, from the 2H-point table twg
+__device__ __forceinline__ void fill_tw(float2* dst, int R, int Ns, int H, const float2* twg) {
+    const int n = Ns * (R - 1);
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int k = e / (R - 1), r = e - k * (R - 1) + 1;
+        dst[e] = twg[2 * ((r * k * (H / (Ns * R))) % H)];
+    }
+}
+template <int T> __device__ __forceinline__ void fill_ring_tw(float2* tws, const float2* twg) {
+    constexpr int H = EL * T;
+    using L = RingTw<T>;
+    if constexpr (T == 32) {
+        fill_tw(tws + L::i1, 4, 12, H, twg);
+        fill_tw(tws + L::i2, 4, 48, H, twg);
+        fill_tw(tws + L::i3, 2, 192, H, twg);
+        fill_tw(tws + L::f1, 4, 2, H, twg);
+        fill_tw(tws + L::f2, 4, 8, H, twg);
+        fill_tw(tws + L::f3, 12, 32, H, twg);
+    } else if constexpr (T == 16) {
+        fill_tw(tws + L::i1, 4, 12, H, twg);
+        fill_tw(tws + L::i2, 4, 48, H, twg);
+        fill_tw(tws + L::f1, 4, 4, H, twg);
+        fill_tw(tws + L::f2, 12, 16, H, twg);
+    } else {
+        fill_tw(tws + L::i1, 4, 12, H, twg);
+        fill_tw(tws + L::i2, 2, 48, H, twg);
+        fill_tw(tws + L::f1, 4, 2, H, twg);
+        fill_tw(tws + L::f2, 12, 8, H, twg);
+    }
+}
+
+// inverse transform of one field: modes X[0..M] (staged) -> grid pairs in registers
+template <int T>
+__device__ __forceinline__ void ring_inverse_regs(const float2* X, int M, const float2* twN, const float2* tws,
+                                                  float2* buf, int t, float2 (&a)[EL]) {
+    constexpr int H = EL * T;
+    using L = RingTw<T>;
+#pragma unroll
+    for (int r = 0; r < EL; ++r) {
+        const int k = t + T * r;
+        float2 xa = (k <= M) ? X[k] : f2(0.f, 0.f);
+        if (k == 0) xa.y = 0.f;                             // the m = 0 mode is real
+        const float2 xb = (k > 0 && H - k <= M) ? X[H - k] : f2(0.f, 0.f);
+        const float2 e = f2(twN[k].x, -twN[k].y);          // e^{+i theta_k}, theta_k = 2 pi k / (2H)
+        const float2 s1 = cadd(xa, cconj(xb)), d1 = csub(xa, cconj(xb));
+        a[r] = cadd(s1, cmul_si<1>(cmul(e, d1)));
+    }
+    __syncwarp();                                          // buf free (previous transform done)
+    spass<T, 12, 1, +1, false, true>(a, buf, nullptr, t);
+    __syncwarp();
+    if constexpr (T == 32) {
+        spass<T, 4, 12, +1, true, true>(a, buf, tws + L::i1, t);
+        __syncwarp();
+        spass<T, 4, 48, +1, true, true>(a, buf, tws + L::i2, t);
+        __syncwarp();
+        spass<T, 2, 192, +1, true, false>(a, buf, tws + L::i3, t);
+    } else if constexpr (T == 16) {
+        spass<T, 4, 12, +1, true, true>(a, buf, tws + L::i1, t);
+        __syncwarp();
+        spass<T, 4, 48, +1, true, false>(a, buf, tws + L::i2, t);
+    } else {
+        spass<T, 4, 12, +1, true, true>(a, buf, tws + L::i1, t);
+        __syncwarp();
+        spass<T, 2, 48, +1, true, false>(a, buf, tws + L::i2, t);
+    }
+}
+
+// forward transform of one field from the grid pairs in registers -> modes X[0..M] (scaled)
+template <int T>
+__device__ __forceinline__ void ring_forward_regs(float2 (&a)[EL], int M, const float2* twN, const float2* tws,
+                                                  float2* buf, int t, float scale, float2* X) {
+    using L = RingTw<T>;
+    __syncwarp();
+    if constexpr (T == 32) {
+        spass<T, 2, 1, -1, false, true>(a, buf, nullptr, t);
+        __syncwarp();
+        spass<T, 4, 2, -1, true, true>(a, buf, tws + L::f1, t);
+        __syncwarp();
+        spass<T, 4, 8, -1, true, true>(a, buf, tws + L::f2, t);
+        __syncwarp();
+        spass<T, 12, 32, -1, true, false>(a, buf, tws + L::f3, t);
+    } else if constexpr (T == 16) {
+        spass<T, 4, 1, -1, false, true>(a, buf, nullptr, t);
+        __syncwarp();
+        spass<T, 4, 4, -1, true, true>(a, buf, tws + L::f1, t);
+        __syncwarp();
+        spass<T, 12, 16, -1, true, false>(a, buf, tws + L::f2, t);
+    } else {
+        spass<T, 2, 1, -1, false, true>(a, buf, nullptr, t);
+        __syncwarp();
+        spass<T, 4, 2, -1, true, true>(a, buf, tws + L::f1, t);
+        __syncwarp();
+        spass<T, 12, 8, -1, true, false>(a, buf, tws + L::f2, t);
+    }
+    const int partner = (T - t) & (T - 1);
+#pragma unroll
+    for (int r = 0; r < EL; ++r) {
+        // Z_{H-k}: lane T - t, register 11 - r (t >= 1); lane 0: its own register (12 - r) mod 12
+        float2 zp;
+        zp.x = __shfl_sync(0xffffffffu, a[EL - 1 - r].x, partner, T);
+        zp.y = __shfl_sync(0xffffffffu, a[EL - 1 - r].y, partner, T);
+        if (t == 0) zp = a[(EL - r) % EL];
+        const int k = t + T * r;
+        if (k <= M) {
+            const float2 zk = a[r], zn = cconj(zp);
+            const float2 s1 = cadd(zk, zn), d1 = csub(zk, zn);
+            const float2 tt = cmul_si<-1>(cmul(twN[k], d1));
+            X[k] = f2(0.5f * (s1.x + tt.x) * scale, 0.5f * (s1.y + tt.y) * scale);
+        }
+    }
+}
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool pred) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(pred ? 8 : 0)
+                 : "memory");
+}
+
+template <int T>
+__global__ void __launch_bounds__(128) k_ring_nl_lg(const float2* __restrict__ Fin, float2* __restrict__ Fout, int M,
+                                                    int nlat, int S, const float2* __restrict__ twg,
+                                                    const double* __restrict__ mu, const double* __restrict__ w) {
+    constexpr int H = EL * T, G = 128 / T, HB = H + H / 16 + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* twN = reinterpret_cast<float2*>(smem_raw);     // 2H entries e^{-2 pi i k / (2H)}
+    float2* tws = twN + 2 * H;                              // pass tables
+    float2* fbuf = tws + RingTw<T>::n;                      // [G][HB]
+    float2* reg = fbuf + G * HB;                            // [G][5][M+1]
+    const int Mp = M + 1;
+    const int s0 = blockIdx.x * G;
+    const int j = blockIdx.y;
+    const int64_t C4 = 4 * (int64_t)S, C5 = 5 * (int64_t)S;
+    // stage the 4 input fields of the G rings: every copy in flight at once
+    for (int q = threadIdx.x; q < 4 * Mp * G; q += blockDim.x) {
+        const int g = q % G, fm = q / G;
+        const int m = fm % Mp, f = fm / Mp;
+        const bool ok = s0 + g < S;
+        cp_async8(&reg[(g * 5 + f) * Mp + m], ok ? (const void*)&Fin[((int64_t)m * nlat + j) * C4 + (int64_t)f * S + s0 + g]
+                                                  : (const void*)Fin,
+                  ok);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (int k = threadIdx.x; k < 2 * H; k += blockDim.x) twN[k] = twg[k];
+    fill_ring_tw<T>(tws, twg);
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    const int t = threadIdx.x & (T - 1), g = threadIdx.x / T;
+    float2* R = reg + g * 5 * Mp;
+    float2* buf = fbuf + g * HB;
+    const double muj = mu[j];
+    const float ic2 = (float)(1.0 / ((1.0 - muj) * (1.0 + muj)));
+    const float scale = (float)(w[j] / (double)(2 * H));
+    // Inputs (slots): 0 Phi', 1 xi, 2 U, 3 V.  Inverse order U, V, xi, Phi'; after xi the
+    // products A1 = xi U -> slot 1, B1 = xi V -> slot 4; after Phi' A2 = Phi' U -> slot 0,
+    // B2 = Phi' V -> slot 3, KE = (U^2 + V^2)/2 -> slot 2 (all / (1 - mu^2)).  Rolled loops
+    // keep one copy of each transform in the instruction stream.
+    float2 u[EL], v[EL], x[EL], a[EL];
+#pragma unroll 1
+    for (int i = 0; i < 4; ++i) {
+        const int in_slot = i == 0 ? 2 : (i == 1 ? 3 : (i == 2 ? 1 : 0));
+        ring_inverse_regs<T>(R + in_slot * Mp, M, twN, tws, buf, t, a);
+#pragma unroll
+        for (int e = 0; e < EL; ++e) {
+            if (i == 0) u[e] = a[e];
+            else if (i == 1) v[e] = a[e];
+            else x[e] = a[e];
+        }
+        if (i < 2) continue;
+        __syncwarp();
+        const int nout = (i == 3) ? 3 : 2;
+#pragma unroll 1
+        for (int o = 0; o < nout; ++o) {
+            // o = 0: x U, o = 1: x V, o = 2: KE
+#pragma unroll
+            for (int e = 0; e < EL; ++e) {
+                const float2 fx = (o == 0) ? u[e] : v[e];
+                const float2 pr = f2(x[e].x * fx.x, x[e].y * fx.y);
+                const float2 ke = f2(0.5f * (u[e].x * u[e].x + v[e].x * v[e].x),
+                                     0.5f * (u[e].y * u[e].y + v[e].y * v[e].y));
+                const float2 q = (o == 2) ? ke : pr;
+                a[e] = f2(q.x * ic2, q.y * ic2);
+            }
+            const int out_slot = (i == 2) ? (o == 0 ? 1 : 4) : (o == 0 ? 0 : (o == 1 ? 3 : 2));
+            ring_forward_regs<T>(a, M, twN, tws, buf, t, scale, R + out_slot * Mp);
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 5 * Mp * G; q += blockDim.x) {
+        const int gg = q % G, fm = q / G;
+        const int m = fm % Mp, f = fm / Mp;
+        const int slot = f == 0 ? 1 : (f == 1 ? 4 : (f == 2 ? 0 : (f == 3 ? 3 : 2)));
+        if (s0 + gg < S) Fout[((int64_t)m * nlat + j) * C5 + (int64_t)f * S + s0 + gg] = reg[(gg * 5 + slot) * Mp + m];
+    }
+}
+
 constexpr int RING_G = 4;   // columns per block in the plain transforms
 
 // ---------------------------------------------------------------------------
@@ -533,10 +840,32 @@ swe_status ring_run(const swe_plan* p, int id, int G, const void* Fin, void* Fou
 
 }  // namespace
 
+// lane-group FP32 kernel for H = 12 T, T in {8, 16, 32}
+template <int T>
+static swe_status ring_lg_launch(const swe_plan* p, const void* Fin, void* Fout, int S, cudaStream_t st) {
+    constexpr int H = EL * T, G = 128 / T, HB = H + H / 16 + 1;
+    const size_t sm = (2 * (size_t)H + RingTw<T>::n + (size_t)G * HB + (size_t)G * 5 * (p->M + 1)) * sizeof(float2);
+    SWE_CHECK_CUDA(cudaFuncSetAttribute(k_ring_nl_lg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    dim3 g((S + G - 1) / G, p->nlat);
+    k_ring_nl_lg<T><<<g, 128, sm, st>>>((const float2*)Fin, (float2*)Fout, p->M, p->nlat, S, p->twf, p->mu, p->w);
+    SWE_CHECK_LAUNCH("k_ring_nl_lg");
+    return SWE_OK;
+}
+
 swe_status ring_nonlinear(const swe_plan* pc, const void* Fin, void* Fout, int S, cudaStream_t st) {
     swe_plan* p = const_cast<swe_plan*>(pc);
     const bool f64 = (p->prec == SWE_FP64);
     const int H = p->nlon / 2;
+    if (!f64 && (H == 96 || H == 192 || H == 384)) {
+        const double by = 8.0 * 9.0 * (p->M + 1.0) * p->nlat * S;
+        const double fl = ((9.0 * 2.5 * log2((double)p->nlon)) + 30.0) * p->nlon * (double)p->nlat * S;
+        ProfToken tk = prof_begin("ring_nl_f32", st, fl, by);
+        swe_status r = H == 96 ? ring_lg_launch<8>(p, Fin, Fout, S, st)
+                               : (H == 192 ? ring_lg_launch<16>(p, Fin, Fout, S, st)
+                                           : ring_lg_launch<32>(p, Fin, Fout, S, st));
+        prof_end(tk, st);
+        return r;
+    }
     int id = p->ring_cfg, G = p->ring_G;
     if (id < 0 || G > S) {
         // default: the largest group that fits the first candidate with room, else 1 slice

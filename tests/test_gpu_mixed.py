@@ -124,3 +124,40 @@ def test_split_tiled_shapes_match_fp64_path():
     finally:
         p64.close()
         pmx.close()
+
+
+@pytest.mark.parametrize("M,nlat,nlon", [(63, 96, 192), (127, 192, 384), (255, 384, 768)],
+                         ids=["T63", "T127", "T255"])
+def test_split_nonlinear_matches_oracle(M, nlat, nlon):
+    """One evaluation of the nonlinear terms (Eq. 1) on the split path: FP32 longitude
+    transforms and grid products, bf16 x 6 Legendre contractions.  S = 5 slices leave the
+    last group of 4 rings ragged."""
+    from paper_2306_09497_gb300 import swe
+    plan = swe.Plan(M, nlat, nlon, prec=swe.SWE_SPLIT_BF16X3)
+    s = Sphere(M, nlat, nlon)
+    sw = SWE(s)
+    S = 5
+    U0 = []
+    for b in range(S):
+        xi, noise = inputs.initial_fields(M, 40 + b)
+        xd = s.unpack(xi)
+        de = 0.1 * s.unpack(inputs.initial_fields(M, 60 + b)[0])   # a divergent part as well
+        U0.append(to_packed(s, (sw.balanced_geopotential(xd) + s.unpack(noise), xd, de)))
+    U0 = np.stack(U0)
+    out = torch.empty((S, 3, plan.nc * 2), dtype=torch.float64, device="cuda")
+    plan.nonlinear(_dev(U0), out, S)
+    got = out.cpu().numpy().view(np.complex128).reshape(S, 3, -1)
+    plan.close()
+    m, _ = inputs.mn_arrays(M)
+    w = np.where(m == 0, 1.0, 2.0)
+    for b in (0, S - 1):
+        ref = to_packed(s, sw.nonlinear(to_dense(s, U0[b])))
+        # FP32 grid values (2^-24, transforms included) through products, a divergence / curl
+        # whose result is one to two orders below the fluxes it differences, and for the
+        # divergence row the Laplacian of the kinetic energy, which weights the white FP32
+        # rounding of KE by n(n+1) against a steeply decaying spectrum (error growing with M;
+        # a numpy emulation rounding only the grid values to FP32 gives 5e-6..7e-6 at T63)
+        bound = (5e-5, 1e-5, 4e-6 * M)
+        for f in range(3):
+            err = np.sqrt(np.sum(w * np.abs(got[b, f] - ref[f]) ** 2) / np.sum(w * np.abs(ref[f]) ** 2))
+            assert err < bound[f], (b, f, err)
