@@ -577,7 +577,7 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src, bool pred)
 }
 
 template <int T>
-__global__ void __launch_bounds__(128) k_ring_nl_lg(const float2* __restrict__ Fin, float2* __restrict__ Fout, int M,
+__global__ void __launch_bounds__(128, 3) k_ring_nl_lg(const float2* __restrict__ Fin, float2* __restrict__ Fout, int M,
                                                     int nlat, int S, const float2* __restrict__ twg,
                                                     const double* __restrict__ mu, const double* __restrict__ w) {
     constexpr int H = EL * T, G = 128 / T, HB = H + H / 16 + 1;
@@ -610,35 +610,43 @@ __global__ void __launch_bounds__(128) k_ring_nl_lg(const float2* __restrict__ F
     const double muj = mu[j];
     const float ic2 = (float)(1.0 / ((1.0 - muj) * (1.0 + muj)));
     const float scale = (float)(w[j] / (double)(2 * H));
-    // Inputs (slots): 0 Phi', 1 xi, 2 U, 3 V.  Inverse order U, V, xi, Phi'; after xi the
-    // products A1 = xi U -> slot 1, B1 = xi V -> slot 4; after Phi' A2 = Phi' U -> slot 0,
-    // B2 = Phi' V -> slot 3, KE = (U^2 + V^2)/2 -> slot 2 (all / (1 - mu^2)).  Rolled loops
-    // keep one copy of each transform in the instruction stream.
-    float2 u[EL], v[EL], x[EL], a[EL];
+    // Inputs (slots): 0 Phi', 1 xi, 2 U, 3 V, 4 free.  Inverse order U, V, xi, Phi'.  With p
+    // = xi (then Phi') in registers: p V / c2 is parked lane-privately in slots 2-3 (free once
+    // U and V are in registers), p U / c2 is transformed, then the parked product:
+    //   xi:   A1 = xi U -> slot 1, B1 = xi V -> slot 4
+    //   Phi': A2 = Phi' U -> slot 0, B2 = Phi' V -> slot 3, KE = (U^2 + V^2)/2 -> slot 2
+    // Rolled loops keep one copy of each transform in the instruction stream.
+    float2 u[EL], v[EL], a[EL];
+    float2* park = R + 2 * Mp;                               // 2 (M+1) >= H entries
 #pragma unroll 1
     for (int i = 0; i < 4; ++i) {
         const int in_slot = i == 0 ? 2 : (i == 1 ? 3 : (i == 2 ? 1 : 0));
         ring_inverse_regs<T>(R + in_slot * Mp, M, twN, tws, buf, t, a);
+        if (i < 2) {
+#pragma unroll
+            for (int e = 0; e < EL; ++e) {
+                if (i == 0) u[e] = a[e];
+                else v[e] = a[e];
+            }
+            continue;
+        }
+        __syncwarp();                                        // slots 2-3 no longer read
 #pragma unroll
         for (int e = 0; e < EL; ++e) {
-            if (i == 0) u[e] = a[e];
-            else if (i == 1) v[e] = a[e];
-            else x[e] = a[e];
+            park[e * T + t] = f2(a[e].x * v[e].x * ic2, a[e].y * v[e].y * ic2);
+            a[e] = f2(a[e].x * u[e].x * ic2, a[e].y * u[e].y * ic2);
         }
-        if (i < 2) continue;
-        __syncwarp();
         const int nout = (i == 3) ? 3 : 2;
 #pragma unroll 1
         for (int o = 0; o < nout; ++o) {
-            // o = 0: x U, o = 1: x V, o = 2: KE
+            if (o == 1) {
 #pragma unroll
-            for (int e = 0; e < EL; ++e) {
-                const float2 fx = (o == 0) ? u[e] : v[e];
-                const float2 pr = f2(x[e].x * fx.x, x[e].y * fx.y);
-                const float2 ke = f2(0.5f * (u[e].x * u[e].x + v[e].x * v[e].x),
-                                     0.5f * (u[e].y * u[e].y + v[e].y * v[e].y));
-                const float2 q = (o == 2) ? ke : pr;
-                a[e] = f2(q.x * ic2, q.y * ic2);
+                for (int e = 0; e < EL; ++e) a[e] = park[e * T + t];
+            } else if (o == 2) {
+#pragma unroll
+                for (int e = 0; e < EL; ++e)
+                    a[e] = f2(0.5f * (u[e].x * u[e].x + v[e].x * v[e].x) * ic2,
+                              0.5f * (u[e].y * u[e].y + v[e].y * v[e].y) * ic2);
             }
             const int out_slot = (i == 2) ? (o == 0 ? 1 : 4) : (o == 0 ? 0 : (o == 1 ? 3 : 2));
             ring_forward_regs<T>(a, M, twN, tws, buf, t, scale, R + out_slot * Mp);
@@ -856,7 +864,8 @@ swe_status ring_nonlinear(const swe_plan* pc, const void* Fin, void* Fout, int S
     swe_plan* p = const_cast<swe_plan*>(pc);
     const bool f64 = (p->prec == SWE_FP64);
     const int H = p->nlon / 2;
-    if (!f64 && (H == 96 || H == 192 || H == 384)) {
+    // lane-group kernel: its parking area (two mode slots) must hold a ring of H values
+    if (!f64 && (H == 96 || H == 192 || H == 384) && 2 * (p->M + 1) >= H) {
         const double by = 8.0 * 9.0 * (p->M + 1.0) * p->nlat * S;
         const double fl = ((9.0 * 2.5 * log2((double)p->nlon)) + 30.0) * p->nlon * (double)p->nlat * S;
         ProfToken tk = prof_begin("ring_nl_f32", st, fl, by);
