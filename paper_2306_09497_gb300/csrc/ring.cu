@@ -661,6 +661,108 @@ __global__ void __launch_bounds__(128, 3) k_ring_nl_lg(const float2* __restrict_
     }
 }
 
+// Plain transforms on the lane-group path (FP32, H = 12 T): one ring per T lanes, G = 128/T
+// consecutive columns of one latitude per block.
+//   inverse: Fourier [M+1][nlat][C] -> grid [C][nlat][nlon]; modes staged with cp.async,
+//            grid pairs stored straight from registers (lane t holds n = t + T i: coalesced)
+//   forward: grid -> Fourier; grid pairs loaded straight into the forward's register layout,
+//            modes staged in shared memory for a coalesced write (G columns per mode)
+template <int T>
+__global__ void __launch_bounds__(128) k_ring_inv_lg(const float2* __restrict__ F, float* __restrict__ grid, int M,
+                                                     int nlat, int C, const float2* __restrict__ twg) {
+    constexpr int H = EL * T, G = 128 / T, HB = H + H / 16 + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* twN = reinterpret_cast<float2*>(smem_raw);
+    float2* tws = twN + 2 * H;
+    float2* fbuf = tws + RingTw<T>::n;                      // [G][HB]
+    float2* reg = fbuf + G * HB;                            // [G][M+1]
+    const int Mp = M + 1;
+    const int c0 = blockIdx.x * G;
+    const int j = blockIdx.y;
+    for (int q = threadIdx.x; q < Mp * G; q += blockDim.x) {
+        const int g = q % G, m = q / G;
+        const bool ok = c0 + g < C;
+        cp_async8(&reg[g * Mp + m], ok ? (const void*)&F[((int64_t)m * nlat + j) * C + c0 + g] : (const void*)F, ok);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (int k = threadIdx.x; k < 2 * H; k += blockDim.x) twN[k] = twg[k];
+    fill_ring_tw<T>(tws, twg);
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    const int t = threadIdx.x & (T - 1), g = threadIdx.x / T;
+    float2 a[EL];
+    ring_inverse_regs<T>(reg + g * Mp, M, twN, tws, fbuf + g * HB, t, a);
+    if (c0 + g < C) {
+        float2* row = reinterpret_cast<float2*>(grid + ((int64_t)(c0 + g) * nlat + j) * (2 * H));
+        constexpr int RL = (T == 16) ? 4 : 2;               // radix of the last inverse pass
+#pragma unroll
+        for (int b = 0; b < EL / RL; ++b)
+#pragma unroll
+            for (int r = 0; r < RL; ++r) row[t + T * (b + r * (EL / RL))] = a[b * RL + r];
+    }
+}
+
+template <int T>
+__global__ void __launch_bounds__(128) k_ring_fwd_lg(const float* __restrict__ grid, float2* __restrict__ F, int M,
+                                                     int nlat, int C, const float2* __restrict__ twg,
+                                                     const double* __restrict__ w) {
+    constexpr int H = EL * T, G = 128 / T, HB = H + H / 16 + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* twN = reinterpret_cast<float2*>(smem_raw);
+    float2* tws = twN + 2 * H;
+    float2* fbuf = tws + RingTw<T>::n;
+    float2* reg = fbuf + G * HB;                            // [G][M+1]
+    const int Mp = M + 1;
+    const int c0 = blockIdx.x * G;
+    const int j = blockIdx.y;
+    const int t = threadIdx.x & (T - 1), g = threadIdx.x / T;
+    float2 a[EL];
+    {
+        constexpr int RL = (T == 16) ? 4 : 2;               // radix of the first forward pass
+        const bool ok = c0 + g < C;
+        const float2* row = reinterpret_cast<const float2*>(grid + ((int64_t)(ok ? c0 + g : 0) * nlat + j) * (2 * H));
+#pragma unroll
+        for (int b = 0; b < EL / RL; ++b)
+#pragma unroll
+            for (int r = 0; r < RL; ++r) a[b * RL + r] = ok ? row[t + T * (b + r * (EL / RL))] : f2(0.f, 0.f);
+    }
+    for (int k = threadIdx.x; k < 2 * H; k += blockDim.x) twN[k] = twg[k];
+    fill_ring_tw<T>(tws, twg);
+    __syncthreads();
+    const float scale = (float)(w[j] / (double)(2 * H));
+    ring_forward_regs<T>(a, M, twN, tws, fbuf + g * HB, t, scale, reg + g * Mp);
+    __syncthreads();
+    for (int q = threadIdx.x; q < Mp * G; q += blockDim.x) {
+        const int gg = q % G, m = q / G;
+        if (c0 + gg < C) F[((int64_t)m * nlat + j) * C + c0 + gg] = reg[gg * Mp + m];
+    }
+}
+
+template <int T>
+static swe_status ring_plain_lg(const swe_plan* p, const void* in, void* out, int C, bool inverse, cudaStream_t st) {
+    constexpr int H = EL * T, G = 128 / T, HB = H + H / 16 + 1;
+    const size_t sm = (2 * (size_t)H + RingTw<T>::n + (size_t)G * HB + (size_t)G * (p->M + 1)) * sizeof(float2);
+    dim3 g((C + G - 1) / G, p->nlat);
+    if (inverse) {
+        SWE_CHECK_CUDA(cudaFuncSetAttribute(k_ring_inv_lg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_ring_inv_lg<T><<<g, 128, sm, st>>>((const float2*)in, (float*)out, p->M, p->nlat, C, p->twf);
+        SWE_CHECK_LAUNCH("k_ring_inv_lg");
+    } else {
+        SWE_CHECK_CUDA(cudaFuncSetAttribute(k_ring_fwd_lg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_ring_fwd_lg<T><<<g, 128, sm, st>>>((const float*)in, (float2*)out, p->M, p->nlat, C, p->twf, p->w);
+        SWE_CHECK_LAUNCH("k_ring_fwd_lg");
+    }
+    return SWE_OK;
+}
+
+// the lane-group kernels serve FP32 plans with nlon / 2 = 12 T whose two mode slots cover a ring
+static int ring_lg_T(const swe_plan* p) {
+    if (p->prec == SWE_FP64) return 0;
+    const int H = p->nlon / 2;
+    if (2 * (p->M + 1) < H) return 0;
+    return H == 96 ? 8 : (H == 192 ? 16 : (H == 384 ? 32 : 0));
+}
+
 constexpr int RING_G = 4;   // columns per block in the plain transforms
 
 // ---------------------------------------------------------------------------
@@ -752,6 +854,14 @@ swe_status set_smem(K kernel, size_t bytes) {
 }  // namespace
 
 swe_status ring_inverse(const swe_plan* p, const void* F, void* grid, int C, cudaStream_t st) {
+    if (const int lgT = ring_lg_T(p)) {
+        ProfToken tk = prof_begin("ring_inv", st, 0.0, 4.0 * (double)C * p->nlat * (2.0 * (p->M + 1) + p->nlon));
+        const swe_status r = lgT == 8    ? ring_plain_lg<8>(p, F, grid, C, true, st)
+                             : lgT == 16 ? ring_plain_lg<16>(p, F, grid, C, true, st)
+                                         : ring_plain_lg<32>(p, F, grid, C, true, st);
+        prof_end(tk, st);
+        return r;
+    }
     FFTPlan fp = make_fft_plan(p);
     dim3 g((C + RING_G - 1) / RING_G, p->nlat);
     const double fe_ = p->prec == SWE_FP64 ? 8.0 : 4.0;   // bytes per real element
@@ -771,6 +881,14 @@ swe_status ring_inverse(const swe_plan* p, const void* F, void* grid, int C, cud
 }
 
 swe_status ring_forward(const swe_plan* p, const void* grid, void* F, int C, cudaStream_t st) {
+    if (const int lgT = ring_lg_T(p)) {
+        ProfToken tk = prof_begin("ring_fwd", st, 0.0, 4.0 * (double)C * p->nlat * (2.0 * (p->M + 1) + p->nlon));
+        const swe_status r = lgT == 8    ? ring_plain_lg<8>(p, grid, F, C, false, st)
+                             : lgT == 16 ? ring_plain_lg<16>(p, grid, F, C, false, st)
+                                         : ring_plain_lg<32>(p, grid, F, C, false, st);
+        prof_end(tk, st);
+        return r;
+    }
     FFTPlan fp = make_fft_plan(p);
     dim3 g((C + RING_G - 1) / RING_G, p->nlat);
     const double fe_ = p->prec == SWE_FP64 ? 8.0 : 4.0;   // bytes per real element
@@ -864,8 +982,8 @@ swe_status ring_nonlinear(const swe_plan* pc, const void* Fin, void* Fout, int S
     swe_plan* p = const_cast<swe_plan*>(pc);
     const bool f64 = (p->prec == SWE_FP64);
     const int H = p->nlon / 2;
-    // lane-group kernel: its parking area (two mode slots) must hold a ring of H values
-    if (!f64 && (H == 96 || H == 192 || H == 384) && 2 * (p->M + 1) >= H) {
+    // lane-group kernel (its parking area, two mode slots, must hold a ring of H values)
+    if (ring_lg_T(p)) {
         const double by = 8.0 * 9.0 * (p->M + 1.0) * p->nlat * S;
         const double fl = ((9.0 * 2.5 * log2((double)p->nlon)) + 30.0) * p->nlon * (double)p->nlat * S;
         ProfToken tk = prof_begin("ring_nl_f32", st, fl, by);
