@@ -37,16 +37,18 @@
 namespace {
 
 constexpr int BM = 128;          // data columns per CTA (MMA M)
-constexpr int NTH = 512;         // threads per CTA: 4 per data column, each a quarter of a K chunk
+constexpr int NCV = 512;         // converter threads: 4 per data column, each a quarter of a K chunk
+constexpr int NTH = NCV + 32;    // + one control warp (table copies and MMA issue)
 constexpr int KQ = 4;            // K values per thread per chunk
 constexpr int KC = 16;           // K per chunk (one MMA)
 constexpr int NPLANE = 3;        // bf16 split terms
 constexpr int NTERMS = 6;        // partial products kept
 constexpr uint32_t TMEM_COLS = 512;
 constexpr unsigned long long WAIT_LIMIT = 1ull << 22;   // bounded polling (about a second)
-constexpr int NR_INV = 3;        // raw data-operand prefetch depth, inverse (FP64 rows)
+constexpr int NR_INV = 2;        // raw data-operand prefetch depth, inverse (FP64 rows)
 constexpr int NR_FWD = 4;        // raw data-operand prefetch depth, forward (FP32 rows)
 constexpr int NT_MAX = 224;      // largest N tile (two parity accumulators + a 32-column read fit in 512)
+constexpr int NB_MAX = 4;        // table-tile ring depth (set per plan from the shared-memory budget)
 
 __constant__ int c_terms[NTERMS][2] = {{0, 0}, {0, 1}, {1, 0}, {0, 2}, {2, 0}, {1, 1}};
 
@@ -62,25 +64,6 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
-}
-
-// bounded wait for completion of phase `parity`; returns false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    const uint32_t a = smem_u32(bar);
-    for (unsigned long long it = 0; it < WAIT_LIMIT; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n"
-            " .reg .pred p;\n"
-            " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n"
-            "}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
 }
 
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -191,32 +174,56 @@ struct TCShape {
     int nt;                      // N tile (multiple of 16, <= 256)
 };
 
-// Both kernels share one pipeline per 16-deep K chunk q (stage s = q mod 2 for the bf16
-// planes and the table tile, raw stage q mod NR for the unsplit data):
-//   every thread: cp.async its own column of chunk q+NR-1 (it alone reads that column,
-//                 so the raw ring needs no block barrier), wait for chunk q's copies;
-//   thread 0:     wait until the MMAs of chunk q-2 released stage s, then start the
-//                 bulk copy of chunk q's table tile into stage s;
-//   every thread: split its column of chunk q into three bf16 planes in stage s;
-//   thread 0:     wait for the table tile, issue 2 x 6 MMAs, commit to stage s's barrier.
-struct Pipe {
-    uint64_t* bar_tma;
-    uint64_t* bar_mma;
+// Both kernels run one warp-specialised pipeline over 16-deep K chunks q:
+//   converter warps 0-15 (4 threads per data column): cp.async their own column of chunk
+//     q + NR - 1 into the raw ring (only they read it back: no barrier), wait for the MMAs
+//     of chunk q - 2 to release bf16 stage q mod 2 (mbarrier "a_empty", signalled by
+//     tcgen05.commit), split chunk q into three bf16 planes there, fence the async proxy
+//     and arrive on "a_full" (one lane per warp);
+//   control warp 16, one lane: keeps the table tiles NB - 2 chunks ahead in an NB-deep ring
+//     (bulk copies on "b_full"; a stage is reused once "b_empty" says its MMAs are done),
+//     waits for "a_full" and "b_full" of chunk q, issues the 2 x 6 MMAs and commits them
+//     to "a_empty" and "b_empty"; after the last chunk it commits to "acc_full";
+//   then the converter warps read the accumulators (tcgen05.ld) and write the result.
+// There is no block barrier inside the loop.  Every wait is bounded; a thread that
+// gives up raises a shared abort flag that makes every other wait return at once, the
+// control lane drains the copies and MMAs it has in flight (bounded), and the CTA
+// reports the timeout and releases its tensor memory.
+struct WS {
+    uint64_t a_full[2], a_empty[2], b_full[NB_MAX], b_empty[NB_MAX], acc_full;
+    int abort;
+    uint32_t tmem_slot;
 };
 
-// tid 0: bounded drain of this CTA's copies and MMAs still in flight after a timeout
-__device__ __forceinline__ void drain(Pipe pp) {
-    for (int s2 = 0; s2 < 2; ++s2) {
-        mbar_wait(&pp.bar_tma[s2], 0);
-        mbar_wait(&pp.bar_mma[s2], 0);
+// bounded wait that also gives up once another thread raised the abort flag
+__device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    const uint32_t a = smem_u32(bar);
+    for (unsigned long long it = 0; it < WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n"
+            " .reg .pred p;\n"
+            " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n"
+            "}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 63) == 63 && *abort) return false;
     }
+    *abort = 1;
+    return false;
 }
 
-// tid 0: 2 parities x 6 partial products of one chunk into the two accumulators
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// 2 parities x 6 partial products of one chunk into the two accumulators
 __device__ __forceinline__ void issue_mmas(const unsigned char* sA, uint32_t a_plane, const unsigned char* sB,
                                            uint32_t b_plane, uint32_t tmem, int acc_stride, uint32_t idesc,
                                            bool first) {
-    tc_fence_after();
 #pragma unroll
     for (int par = 0; par < 2; ++par) {
         for (int t = 0; t < NTERMS; ++t) {
@@ -228,13 +235,22 @@ __device__ __forceinline__ void issue_mmas(const unsigned char* sA, uint32_t a_p
     }
 }
 
-__device__ __forceinline__ uint32_t tmem_setup(uint64_t* bars, uint32_t* tmem_slot, int tid) {
+__device__ __forceinline__ uint32_t ws_setup(WS* ws, int tid) {
     if (tid == 0) {
-        for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&ws->a_full[i], NCV / 32);
+            mbar_init(&ws->a_empty[i], 1);
+        }
+        for (int i = 0; i < NB_MAX; ++i) {
+            mbar_init(&ws->b_full[i], 1);
+            mbar_init(&ws->b_empty[i], 1);
+        }
+        mbar_init(&ws->acc_full, 1);
+        ws->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if ((tid >> 5) == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ws->tmem_slot)),
                      "r"(TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -242,7 +258,7 @@ __device__ __forceinline__ uint32_t tmem_setup(uint64_t* bars, uint32_t* tmem_sl
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    return *tmem_slot;
+    return ws->tmem_slot;
 }
 
 __device__ __forceinline__ void tmem_release(uint32_t tmem, int tid) {
@@ -252,13 +268,71 @@ __device__ __forceinline__ void tmem_release(uint32_t tmem, int tid) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
+// control lane: table-tile ring + MMA issue for chunks 0..nq-1 (see above)
+// (b_stride: byte distance of the ring's stages; b_bytes: bytes of one chunk's table tile)
+__device__ __forceinline__ void ws_control(WS* ws, unsigned char* const* sA, uint32_t a_plane, unsigned char* sB0,
+                                           uint32_t b_stride, uint32_t b_bytes, uint32_t b_plane, int NB,
+                                           const unsigned char* Bm, int64_t bchunk, int nq, uint32_t tmem,
+                                           int acc_stride, uint32_t idesc) {
+    volatile int* ab = &ws->abort;
+    const int D = NB - 2;                                   // table chunks in flight ahead of the MMAs
+    int issued_b = 0, last_mma = -1;
+    auto copy_b = [&](int c) {
+        mbar_expect_tx(&ws->b_full[c % NB], b_bytes);
+        bulk_g2s(sB0 + (size_t)(c % NB) * b_stride, Bm + (int64_t)c * bchunk, b_bytes, &ws->b_full[c % NB]);
+        issued_b = c + 1;
+    };
+    for (int c = 0; c < D && c < nq; ++c) copy_b(c);
+    bool ok = true;
+    for (int q = 0; q < nq && ok; ++q) {
+        const int c = q + D;
+        if (c < nq) {
+            if (c >= NB) ok = ws_wait(&ws->b_empty[c % NB], ((c / NB) - 1) & 1, ab);
+            if (!ok) break;
+            copy_b(c);
+        }
+        ok = ws_wait(&ws->a_full[q & 1], (q >> 1) & 1, ab) && ws_wait(&ws->b_full[q % NB], (q / NB) & 1, ab);
+        if (!ok) break;
+        tc_fence_after();
+        issue_mmas(sA[q & 1], a_plane, sB0 + (size_t)(q % NB) * b_stride, b_plane, tmem, acc_stride, idesc, q == 0);
+        mma_commit(&ws->a_empty[q & 1]);
+        mma_commit(&ws->b_empty[q % NB]);
+        last_mma = q;
+    }
+    if (ok) {
+        mma_commit(&ws->acc_full);
+        return;
+    }
+    *ab = 1;
+    // bounded drain of this CTA's own work in flight: the MMAs (their last commit) and
+    // the table copies not yet consumed
+    volatile int zero = 0;
+    if (last_mma >= 0) ws_wait(&ws->a_empty[last_mma & 1], (last_mma >> 1) & 1, &zero);
+    for (int c = last_mma + 1; c < issued_b; ++c) ws_wait(&ws->b_full[c % NB], (c / NB) & 1, &zero);
+}
+
+// converter side of chunk q, after its planes are stored: make them visible to the
+// tensor core and signal (one lane per warp)
+__device__ __forceinline__ void ws_planes_ready(WS* ws, int q, int lane) {
+    fence_proxy_async();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&ws->a_full[q & 1]);
+}
+
+// converter warp: wait (lane 0) for a barrier phase, broadcast the outcome
+__device__ __forceinline__ bool ws_warp_wait(WS* ws, uint64_t* bar, uint32_t parity, int lane) {
+    bool ok = true;
+    if (lane == 0) ok = ws_wait(bar, parity, &ws->abort);
+    return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+}
+
 // ----------------------------------------------------------------------------- inverse
 // grid: (ceil(ncol/128), M+1, n-tiles over j).  Table Binv: for each m, chunk q, parity,
 // N-tile: a [nt x 16] bf16 tile x 3 planes, contiguous (offsets from inv_off[m]).
 __global__ void __launch_bounds__(NTH, 1) k_leg_inv_tc(const double* __restrict__ X, float* __restrict__ F,
                                                        const unsigned char* __restrict__ Binv,
                                                        const long long* __restrict__ inv_off,
-                                                       const int* __restrict__ inv_nq, TCShape sh, int* err) {
+                                                       const int* __restrict__ inv_nq, TCShape sh, int NB, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int nt = sh.nt;
     const uint32_t a_plane = BM * KC * 2;                 // 4 KB
@@ -266,14 +340,12 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_inv_tc(const double* __restrict_
     const uint32_t a_stage = 2 * NPLANE * a_plane;        // two parities
     const uint32_t b_stage = 2 * NPLANE * b_plane;
     unsigned char* sA[2] = {smem, smem + a_stage};
-    unsigned char* sB[2] = {smem + 2 * a_stage, smem + 2 * a_stage + b_stage};
-    double* raw = reinterpret_cast<double*>(smem + 2 * a_stage + 2 * b_stage);   // [NR][2][KC][BM]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(raw + NR_INV * 2 * KC * BM);
-    Pipe pp{bars, bars + 2};
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
+    unsigned char* sB0 = smem + 2 * a_stage;
+    double* raw = reinterpret_cast<double*>(sB0 + (size_t)NB * b_stage);   // [NR][2][KC][BM]
+    WS* ws = reinterpret_cast<WS*>(raw + NR_INV * 2 * KC * BM);
 
-    // thread (sub, col): data column col, K values 4 sub .. 4 sub + 3 of every chunk
-    const int tid = threadIdx.x, warp = tid >> 5, col = tid & (BM - 1), sub = tid >> 7;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int col = tid & (BM - 1), sub = (tid >> 7) & 3;
     const int M = sh.M;
     const int m = M - (int)blockIdx.y;
     const int c0 = blockIdx.x * BM;
@@ -283,6 +355,7 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_inv_tc(const double* __restrict_
     const int64_t xrow0 = ex_off(m, M);
     const int c = c0 + col;
     const bool cin = c < sh.ncol;
+    const bool conv = tid < NCV;
 
     // raw prefetch of chunk qq (rows n = m + par + 2k, k in [16 qq, 16 qq + 16)): this thread's
     // column and quarter
@@ -302,68 +375,55 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_inv_tc(const double* __restrict_
         }
         cp_async_commit();
     };
+    if (conv) {
 #pragma unroll
-    for (int qq = 0; qq < NR_INV - 1; ++qq) prefetch(qq);
-
-    const uint32_t tmem = tmem_setup(bars, tmem_slot, tid);
+        for (int qq = 0; qq < NR_INV - 1; ++qq) prefetch(qq);
+    }
+    const uint32_t tmem = ws_setup(ws, tid);
     const uint32_t idesc = make_idesc(nt);
-    const unsigned char* Bm = Binv + inv_off[m] + (int64_t)blockIdx.z * 2 * NPLANE * b_plane;
-    const int64_t bchunk = (int64_t)gridDim.z * 2 * NPLANE * b_plane;   // bytes per chunk over all n-tiles
-    bool ok = true;
-    for (int q = 0; q < nq && ok; ++q) {
-        const int s = q & 1;
-        prefetch(q + NR_INV - 1);
-        if (tid == 0) {
-            // stage s is free once the MMAs of chunk q-2 completed
-            if (q >= 2) ok = mbar_wait(&pp.bar_mma[s], ((q - 2) >> 1) & 1);
-            if (ok) {
-                mbar_expect_tx(&pp.bar_tma[s], b_stage);
-                bulk_g2s(sB[s], Bm + (int64_t)q * bchunk, b_stage, &pp.bar_tma[s]);
-            }
+    if (!conv) {
+        if (lane == 0) {
+            const unsigned char* Bm = Binv + inv_off[m] + (int64_t)blockIdx.z * 2 * NPLANE * b_plane;
+            const int64_t bchunk = (int64_t)gridDim.z * 2 * NPLANE * b_plane;   // bytes per chunk, all n-tiles
+            ws_control(ws, sA, a_plane, sB0, b_stage, b_stage, b_plane, NB, Bm, bchunk, nq, tmem, nt, idesc);
         }
-        ok = __syncthreads_and(ok);
-        if (!ok) break;
-        cp_async_wait<NR_INV - 1>();
-        const double* r = raw + (q % NR_INV) * (2 * KC * BM);
+    } else {
+        for (int q = 0; q < nq; ++q) {
+            prefetch(q + NR_INV - 1);
+            cp_async_wait<NR_INV - 1>();
+            if (q >= 2 && !ws_warp_wait(ws, &ws->a_empty[q & 1], ((q - 2) >> 1) & 1, lane)) break;
+            const double* r = raw + (q % NR_INV) * (2 * KC * BM);
 #pragma unroll
-        for (int par = 0; par < 2; ++par) {
-            float v[KQ];
+            for (int par = 0; par < 2; ++par) {
+                float v[KQ];
 #pragma unroll
-            for (int i = 0; i < KQ; ++i) v[i] = (float)r[(par * KC + KQ * sub + i) * BM + col];
-            store_quad_planes(sA[s] + par * NPLANE * a_plane, a_plane, col, KQ * sub, v);
-        }
-        fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-            ok = mbar_wait(&pp.bar_tma[s], (q >> 1) & 1);
-            if (ok) {
-                issue_mmas(sA[s], a_plane, sB[s], b_plane, tmem, nt, idesc, q == 0);   // nt: multiple of 32
-                mma_commit(&pp.bar_mma[s]);
+                for (int i = 0; i < KQ; ++i) v[i] = (float)r[(par * KC + KQ * sub + i) * BM + col];
+                store_quad_planes(sA[q & 1] + par * NPLANE * a_plane, a_plane, col, KQ * sub, v);
             }
+            ws_planes_ready(ws, q, lane);
         }
+        cp_async_wait<0>();
+        ws_warp_wait(ws, &ws->acc_full, 0, lane);
     }
-    cp_async_wait<0>();
-    if (tid == 0) {
-        if (ok && nq > 0) ok = mbar_wait(&pp.bar_mma[(nq - 1) & 1], ((nq - 1) >> 1) & 1);
-        if (!ok) drain(pp);
-    }
-    ok = __syncthreads_and(ok);
+    __syncthreads();
     tc_fence_after();
-    if (ok) {
-        // epilogue: warp w reads TMEM lanes (= data columns) 32 (w mod 4) .. + 31, and the
-        // 32-column groups j0 = 32 sub + 128 i of the accumulators
-        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-        for (int j0 = 32 * sub; j0 < nt; j0 += 128) {
-            float e[32], o[32];
-            tmem_ld32(tmem + lane_base + (uint32_t)j0, e);
-            tmem_ld32(tmem + lane_base + (uint32_t)(nt + j0), o);
-            if (cin) {
+    if (!ws->abort) {
+        if (conv) {
+            // epilogue: warp w reads TMEM lanes (= data columns) 32 (w mod 4) .. + 31, and the
+            // 32-column groups j0 = 32 sub + 128 i of the accumulators
+            const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+            for (int j0 = 32 * sub; j0 < nt; j0 += 128) {
+                float e[32], o[32];
+                tmem_ld32(tmem + lane_base + (uint32_t)j0, e);
+                tmem_ld32(tmem + lane_base + (uint32_t)(nt + j0), o);
+                if (cin) {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int j = jt0 + j0 + i;
-                    if (j0 + i < nt && j < sh.nlat2) {
-                        F[((int64_t)m * sh.nlat + j) * sh.ncol + c] = e[i] + o[i];
-                        F[((int64_t)m * sh.nlat + (sh.nlat - 1 - j)) * sh.ncol + c] = e[i] - o[i];
+                    for (int i = 0; i < 32; ++i) {
+                        const int j = jt0 + j0 + i;
+                        if (j0 + i < nt && j < sh.nlat2) {
+                            F[((int64_t)m * sh.nlat + j) * sh.ncol + c] = e[i] + o[i];
+                            F[((int64_t)m * sh.nlat + (sh.nlat - 1 - j)) * sh.ncol + c] = e[i] - o[i];
+                        }
                     }
                 }
             }
@@ -382,7 +442,7 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_fwd_tc(const float* __restrict__
                                                        const unsigned char* __restrict__ Bfwd,
                                                        const long long* __restrict__ fwd_off,
                                                        const int* __restrict__ fwd_ntiles,
-                                                       const int* __restrict__ fwd_nt, TCShape sh, int* err) {
+                                                       const int* __restrict__ fwd_nt, TCShape sh, int NB, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int M = sh.M;
     const int m = M - (int)blockIdx.y;
@@ -396,13 +456,12 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_fwd_tc(const float* __restrict__
     const uint32_t b_stage = 2 * NPLANE * b_plane;
     const uint32_t b_stage_max = 2 * NPLANE * (uint32_t)sh.nt * KC * 2;
     unsigned char* sA[2] = {smem, smem + a_stage};
-    unsigned char* sB[2] = {smem + 2 * a_stage, smem + 2 * a_stage + b_stage_max};
-    float* raw = reinterpret_cast<float*>(smem + 2 * a_stage + 2 * b_stage_max);   // [NR][2 KC][BM]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(raw + NR_FWD * 2 * KC * BM);
-    Pipe pp{bars, bars + 2};
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
+    unsigned char* sB0 = smem + 2 * a_stage;               // NB stages of b_stage_max bytes
+    float* raw = reinterpret_cast<float*>(sB0 + (size_t)NB * b_stage_max);   // [NR][2 KC][BM]
+    WS* ws = reinterpret_cast<WS*>(raw + NR_FWD * 2 * KC * BM);
 
-    const int tid = threadIdx.x, warp = tid >> 5, col = tid & (BM - 1), sub = tid >> 7;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int col = tid & (BM - 1), sub = (tid >> 7) & 3;
     const int c0 = blockIdx.x * BM;
     const int kt0 = blockIdx.z * nt;
     const int nq = (sh.nlat2 + KC - 1) / KC;
@@ -410,6 +469,7 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_fwd_tc(const float* __restrict__
     const int64_t yrow0 = ex_off(m, M);
     const int c = c0 + col;
     const bool cin = c < sh.ncol;
+    const bool conv = tid < NCV;
     const float* Fm = F + (int64_t)m * sh.nlat * sh.ncol;
 
     // raw prefetch of chunk qq: rows j = 16 qq + jj (north) and nlat-1-j (south), this thread's
@@ -429,69 +489,59 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_fwd_tc(const float* __restrict__
         }
         cp_async_commit();
     };
+    if (conv) {
 #pragma unroll
-    for (int qq = 0; qq < NR_FWD - 1; ++qq) prefetch(qq);
-
-    const uint32_t tmem = tmem_setup(bars, tmem_slot, tid);
+        for (int qq = 0; qq < NR_FWD - 1; ++qq) prefetch(qq);
+    }
+    const uint32_t tmem = ws_setup(ws, tid);
     const uint32_t idesc = make_idesc(nt);
-    const unsigned char* Bm = Bfwd + fwd_off[m] + (int64_t)blockIdx.z * b_stage;
-    const int64_t bchunk = (int64_t)nz * b_stage;
-    bool ok = true;
-    for (int q = 0; q < nq && ok; ++q) {
-        const int s = q & 1;
-        prefetch(q + NR_FWD - 1);
-        if (tid == 0) {
-            if (q >= 2) ok = mbar_wait(&pp.bar_mma[s], ((q - 2) >> 1) & 1);
-            if (ok) {
-                mbar_expect_tx(&pp.bar_tma[s], b_stage);
-                bulk_g2s(sB[s], Bm + (int64_t)q * bchunk, b_stage, &pp.bar_tma[s]);
-            }
+    if (!conv) {
+        if (lane == 0) {
+            // the ring's stages are b_stage_max apart so that every wavenumber's tiles fit;
+            // the copies move this wavenumber's b_stage bytes
+            const unsigned char* Bm = Bfwd + fwd_off[m] + (int64_t)blockIdx.z * b_stage;
+            const int64_t bchunk = (int64_t)nz * b_stage;
+            ws_control(ws, sA, a_plane, sB0, b_stage_max, b_stage, b_plane, NB, Bm, bchunk, nq, tmem, acc, idesc);
         }
-        ok = __syncthreads_and(ok);
-        if (!ok) break;
-        cp_async_wait<NR_FWD - 1>();
-        const float* r = raw + (q % NR_FWD) * (2 * KC * BM);
-        float vs[KQ], va[KQ];
+    } else {
+        for (int q = 0; q < nq; ++q) {
+            prefetch(q + NR_FWD - 1);
+            cp_async_wait<NR_FWD - 1>();
+            if (q >= 2 && !ws_warp_wait(ws, &ws->a_empty[q & 1], ((q - 2) >> 1) & 1, lane)) break;
+            const float* r = raw + (q % NR_FWD) * (2 * KC * BM);
+            float vs[KQ], va[KQ];
 #pragma unroll
-        for (int i = 0; i < KQ; ++i) {
-            const int jj = KQ * sub + i;
-            const float fn = r[jj * BM + col], fs = r[(KC + jj) * BM + col];
-            vs[i] = fn + fs;
-            va[i] = fn - fs;
-        }
-        store_quad_planes(sA[s], a_plane, col, KQ * sub, vs);
-        store_quad_planes(sA[s] + NPLANE * a_plane, a_plane, col, KQ * sub, va);
-        fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-            ok = mbar_wait(&pp.bar_tma[s], (q >> 1) & 1);
-            if (ok) {
-                issue_mmas(sA[s], a_plane, sB[s], b_plane, tmem, acc, idesc, q == 0);
-                mma_commit(&pp.bar_mma[s]);
+            for (int i = 0; i < KQ; ++i) {
+                const int jj = KQ * sub + i;
+                const float fn = r[jj * BM + col], fs = r[(KC + jj) * BM + col];
+                vs[i] = fn + fs;
+                va[i] = fn - fs;
             }
+            store_quad_planes(sA[q & 1], a_plane, col, KQ * sub, vs);
+            store_quad_planes(sA[q & 1] + NPLANE * a_plane, a_plane, col, KQ * sub, va);
+            ws_planes_ready(ws, q, lane);
         }
+        cp_async_wait<0>();
+        ws_warp_wait(ws, &ws->acc_full, 0, lane);
     }
-    cp_async_wait<0>();
-    if (tid == 0) {
-        if (ok && nq > 0) ok = mbar_wait(&pp.bar_mma[(nq - 1) & 1], ((nq - 1) >> 1) & 1);
-        if (!ok) drain(pp);
-    }
-    ok = __syncthreads_and(ok);
+    __syncthreads();
     tc_fence_after();
-    if (ok) {
-        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-        for (int k0 = 32 * sub; k0 < nt; k0 += 128) {
-            float d0[32], d1[32];
-            tmem_ld32(tmem + lane_base + (uint32_t)k0, d0);
-            tmem_ld32(tmem + lane_base + (uint32_t)(acc + k0), d1);
-            if (cin) {
+    if (!ws->abort) {
+        if (conv) {
+            const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+            for (int k0 = 32 * sub; k0 < nt; k0 += 128) {
+                float d0[32], d1[32];
+                tmem_ld32(tmem + lane_base + (uint32_t)k0, d0);
+                tmem_ld32(tmem + lane_base + (uint32_t)(acc + k0), d1);
+                if (cin) {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int k = kt0 + k0 + i;
-                    const int r0 = 2 * k, r1 = 2 * k + 1;        // extended-row offsets of parities 0 / 1
-                    if (k0 + i < nt) {
-                        if (r0 < Kx) Y[(yrow0 + r0) * sh.ncol + c] = (double)d0[i];
-                        if (r1 < Kx) Y[(yrow0 + r1) * sh.ncol + c] = (double)d1[i];
+                    for (int i = 0; i < 32; ++i) {
+                        const int k = kt0 + k0 + i;
+                        const int r0 = 2 * k, r1 = 2 * k + 1;        // extended-row offsets of parities 0 / 1
+                        if (k0 + i < nt) {
+                            if (r0 < Kx) Y[(yrow0 + r0) * sh.ncol + c] = (double)d0[i];
+                            if (r1 < Kx) Y[(yrow0 + r1) * sh.ncol + c] = (double)d1[i];
+                        }
                     }
                 }
             }
@@ -583,14 +633,24 @@ struct SplitTables {
     int* fwd_nt = nullptr;
     int* err = nullptr;
     size_t smem_inv = 0, smem_fwd = 0;
+    int nb_inv = 2, nb_fwd = 2;               // table-tile ring depths
 };
 
 static int round16(int x) { return (x + 15) / 16 * 16; }
 
-// planes (2 stages) + table tiles (2 stages) + raw prefetch ring + barriers
-static size_t tc_smem(int nt, size_t raw_stage, int nr) {
+constexpr size_t SMEM_LIMIT = 227 * 1024;
+
+// planes (2 stages) + table tiles (nb stages) + raw prefetch ring + barriers
+static size_t tc_smem(int nt, size_t raw_stage, int nr, int nb) {
     size_t a_stage = 2 * NPLANE * BM * KC * 2, b_stage = 2 * NPLANE * (size_t)nt * KC * 2;
-    return 2 * a_stage + 2 * b_stage + (size_t)nr * raw_stage + 64;
+    return 2 * a_stage + (size_t)nb * b_stage + (size_t)nr * raw_stage + sizeof(WS) + 64;
+}
+
+// deepest table-tile ring (<= NB_MAX) that fits the shared-memory limit; 0 if even 2 do not
+static int tc_nb(int nt, size_t raw_stage, int nr) {
+    for (int nb = NB_MAX; nb >= 2; --nb)
+        if (tc_smem(nt, raw_stage, nr, nb) <= SMEM_LIMIT) return nb;
+    return 0;
 }
 
 swe_status split_tables_build(swe_plan* p) {
@@ -657,13 +717,15 @@ swe_status split_tables_build(swe_plan* p) {
     k_build_fwd_table<<<dim3(256, M + 1), 256>>>(p->P, t->fwd, t->fwd_off, t->fwd_ntiles, t->fwd_nt, M, p->nlat2);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    t->smem_inv = tc_smem(t->nt_inv, 2 * KC * BM * sizeof(double), NR_INV);
-    t->smem_fwd = tc_smem(t->nt_fwd, 2 * KC * BM * sizeof(float), NR_FWD);
-    if (t->smem_inv > 227 * 1024 || t->smem_fwd > 227 * 1024) {
+    t->nb_inv = tc_nb(t->nt_inv, 2 * KC * BM * sizeof(double), NR_INV);
+    t->nb_fwd = tc_nb(t->nt_fwd, 2 * KC * BM * sizeof(float), NR_FWD);
+    if (t->nb_inv == 0 || t->nb_fwd == 0) {
         p->Pbf = t;
-        swe_set_error("split tables: shared-memory footprint %zu / %zu B exceeds 227 KB", t->smem_inv, t->smem_fwd);
+        swe_set_error("split tables: shared-memory footprint of the tensor-core kernels exceeds 227 KB");
         return SWE_EINVAL;
     }
+    t->smem_inv = tc_smem(t->nt_inv, 2 * KC * BM * sizeof(double), NR_INV, t->nb_inv);
+    t->smem_fwd = tc_smem(t->nt_fwd, 2 * KC * BM * sizeof(float), NR_FWD, t->nb_fwd);
     // at least ~116 KB of shared memory so that a single CTA (holding all 512 TMEM columns) runs per SM
     const size_t one_per_sm = 116 * 1024;
     if (t->smem_inv < one_per_sm) t->smem_inv = one_per_sm;
@@ -704,7 +766,7 @@ swe_status leg_inverse_split(const swe_plan* p, const double2* X, float2* F, int
     SWE_CHECK_CUDA(cudaFuncSetAttribute(k_leg_inv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_inv));
     ProfToken tk = prof_begin("leg_inv_tc", st, fl, by);
     k_leg_inv_tc<<<grid, NTH, t->smem_inv, st>>>((const double*)X, (float*)F, t->inv, t->inv_off, t->inv_nq, sh,
-                                                t->err);
+                                                t->nb_inv, t->err);
     prof_end(tk, st);
     SWE_CHECK_LAUNCH("k_leg_inv_tc");
     return SWE_OK;
@@ -723,7 +785,7 @@ swe_status leg_forward_split(const swe_plan* p, const float2* F, double2* Y, int
     SWE_CHECK_CUDA(cudaFuncSetAttribute(k_leg_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_fwd));
     ProfToken tk = prof_begin("leg_fwd_tc", st, fl, by);
     k_leg_fwd_tc<<<grid, NTH, t->smem_fwd, st>>>((const float*)F, (double*)Y, t->fwd, t->fwd_off, t->fwd_ntiles,
-                                                t->fwd_nt, sh, t->err);
+                                                t->fwd_nt, sh, t->nb_fwd, t->err);
     prof_end(tk, st);
     SWE_CHECK_LAUNCH("k_leg_fwd_tc");
     return SWE_OK;
