@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_inv_tc(const double* __restrict_
             for (int par = 0; par < 2; ++par) {
                 float v[KQ];
 #pragma unroll
-                for (int i = 0; i < KQ; ++i) v[i] = (float)r[(par * KC + KQ * sub + i) * BM + col];
+                for (int i = 0; i < KQ; ++i) v[i] = d2f_fast(r[(par * KC + KQ * sub + i) * BM + col]);
                 store_quad_planes(sA[q & 1] + par * NPLANE * a_plane, a_plane, col, KQ * sub, v);
             }
             ws_planes_ready(ws, q, lane);
@@ -539,8 +539,8 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_fwd_tc(const float* __restrict__
                         const int k = kt0 + k0 + i;
                         const int r0 = 2 * k, r1 = 2 * k + 1;        // extended-row offsets of parities 0 / 1
                         if (k0 + i < nt) {
-                            if (r0 < Kx) Y[(yrow0 + r0) * sh.ncol + c] = (double)d0[i];
-                            if (r1 < Kx) Y[(yrow0 + r1) * sh.ncol + c] = (double)d1[i];
+                            if (r0 < Kx) Y[(yrow0 + r0) * sh.ncol + c] = f2d_fast(d0[i]);
+                            if (r1 < Kx) Y[(yrow0 + r1) * sh.ncol + c] = f2d_fast(d1[i]);
                         }
                     }
                 }

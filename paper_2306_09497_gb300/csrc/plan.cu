@@ -130,7 +130,7 @@ __global__ void k_row_m(int M, int* row_m, int* srow_m) {
     for (int n = m; n <= M; ++n) srow_m[so + (n - m)] = m;
 }
 
-__global__ void k_row_coef(int M, double a, double* rc) {
+__global__ void k_row_coef(int M, double a, double* rc, float* rcf) {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m > M) return;
     auto il = [&](int n) { return (n >= 1 && n <= M && n >= m) ? -a * a / ((double)n * (n + 1.0)) : 0.0; };
@@ -145,6 +145,7 @@ __global__ void k_row_coef(int M, double a, double* rc) {
         c[RC_P] = n >= 1 ? (n + 1.0) / n * en : 0.0;
         c[RC_Q] = n >= 1 ? n / (n + 1.0) * en1 : 0.0;
         c[RC_R] = n >= 1 ? (double)m / ((double)n * (n + 1.0)) : 0.0;
+        for (int k = 0; k < RC_NUM; ++k) rcf[(ex_off(m, M) + (n - m)) * RC_NUM + k] = (float)c[k];
     }
 }
 
@@ -213,6 +214,7 @@ extern "C" swe_status swe_plan_create(const swe_plan_desc* d, swe_plan_t* out) {
     ALLOC(p->twf, sizeof(float2) * p->nlon);
     ALLOC(p->flags, sizeof(int) * 4);
     ALLOC(p->rc, sizeof(double) * RC_NUM * p->ncx);
+    ALLOC(p->rcf, sizeof(float) * RC_NUM * p->ncx);
 #undef ALLOC
     cudaMemset(p->flags, 0, sizeof(int) * 4);
     k_gauss<<<(p->nlat2 + 63) / 64, 64>>>(p->nlat, p->mu, p->w);
@@ -222,7 +224,7 @@ extern "C" swe_status swe_plan_create(const swe_plan_desc* d, swe_plan_t* out) {
     }
     k_twiddle<<<(p->nlon + 255) / 256, 256>>>(p->nlon, p->tw, p->twf);
     k_row_m<<<(p->M + 1 + 127) / 128, 128>>>(p->M, p->row_m, p->srow_m);
-    k_row_coef<<<(p->M + 1 + 127) / 128, 128>>>(p->M, p->a, p->rc);
+    k_row_coef<<<(p->M + 1 + 127) / 128, 128>>>(p->M, p->a, p->rc, p->rcf);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -252,8 +254,12 @@ extern "C" swe_status swe_plan_destroy(swe_plan_t p) {
     cudaFree(p->flags);
     cudaFree(p->thx);
     cudaFree(p->rc);
+    cudaFree(p->rcf);
     split_tables_free(p);
-    for (int i = 0; i < p->ncn; ++i) cudaFree(p->cn[i].fac);
+    for (int i = 0; i < p->ncn; ++i) {
+        cudaFree(p->cn[i].fac);
+        cudaFree(p->cn[i].fac32);
+    }
     if (p->ws.base) cudaFree(p->ws.base);
     delete p;
     return SWE_OK;

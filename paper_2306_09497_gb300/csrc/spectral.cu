@@ -455,6 +455,226 @@ __global__ void k_cn_solve_warp(const double2* __restrict__ fac, const double2* 
     }
 }
 
+// ------------------------------------------------------------------ mixed-precision variants
+// On split-precision plans the spectral kernels compute in FP32 on integer-pipe conversions
+// of their FP64 operands (GB300 runs FP64 arithmetic and conversions at a small fraction of
+// its FP32 rate).  Whatever feeds the FP32 transforms is produced in FP32; an update of the
+// FP64 state adds an FP32 increment with one FP64 addition per real number, so the state
+// keeps its FP64 resolution and only the increment carries FP32 rounding.
+__global__ void k_to_f32(const double2* __restrict__ in, float2* __restrict__ out, int64_t n) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n) out[t] = d2f2(in[t]);
+}
+
+__device__ __forceinline__ float2 fz() { return make_float2(0.f, 0.f); }
+__device__ __forceinline__ double2 dadd_f(double2 a, float2 inc) {
+    return make_double2(a.x + f2d_fast(inc.x), a.y + f2d_fast(inc.y));
+}
+
+struct StateViewF {
+    const double2* a;
+    const double2* b;
+    float beta;
+    int64_t nc;
+    int S;
+    int M;
+    __device__ __forceinline__ float2 get(int f, int m, int n, int s) const {
+        if (n < m || n > M) return fz();
+        if (n == 0 && f > 0) return fz();
+        int64_t i = ((int64_t)f * nc + st_off(m, M) + (n - m)) * S + s;
+        float2 v = d2f2(a[i]);
+        if (b) {
+            const float2 w = d2f2(b[i]);
+            v = make_float2(fmaf(beta, w.x, v.x), fmaf(beta, w.y, v.y));
+        }
+        return v;
+    }
+};
+
+__global__ void k_nl_pre_f32(StateViewF U, double2* __restrict__ X, const int* __restrict__ row_m, int64_t ncx,
+                             const float* __restrict__ rcf) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int S = U.S, M = U.M;
+    if (t >= ncx * S) return;
+    int s = (int)(t % S);
+    int64_t rx = t / S;
+    int m = row_m[rx];
+    int n = m + (int)(rx - ex_off(m, M));
+    const float* c = rcf + rx * RC_NUM;
+    const float uc0 = c[RC_UC0], ucm = c[RC_UCM], ucp = c[RC_UCP];
+    const float2 xi0 = U.get(1, m, n, s), de0 = U.get(2, m, n, s);
+    const float2 xim = U.get(1, m, n - 1, s), dem = U.get(2, m, n - 1, s);
+    const float2 xip = U.get(1, m, n + 1, s), dep = U.get(2, m, n + 1, s);
+    float2 Uh, Vh;
+    Uh.x = fmaf(ucm, xim.x, fmaf(-ucp, xip.x, -uc0 * de0.y));
+    Uh.y = fmaf(ucm, xim.y, fmaf(-ucp, xip.y, uc0 * de0.x));
+    Vh.x = fmaf(-ucm, dem.x, fmaf(ucp, dep.x, -uc0 * xi0.y));
+    Vh.y = fmaf(-ucm, dem.y, fmaf(ucp, dep.y, uc0 * xi0.x));
+    double2* row = X + rx * 4 * (int64_t)S + s;
+    row[0] = f2d2(U.get(0, m, n, s));
+    row[S] = f2d2(xi0);
+    row[2 * S] = f2d2(Uh);
+    row[3 * S] = f2d2(Vh);
+}
+
+__device__ __forceinline__ void flag_nonfinite_f(int* flags, float2 v) {
+    if (!isfinite(v.x) || !isfinite(v.y)) atomicOr(flags, 1);
+}
+
+__global__ void k_nl_post_f32(const double2* __restrict__ Y, int mode, float dt, const double2* __restrict__ in0,
+                              const double2* __restrict__ in1, double2* __restrict__ out0,
+                              double2* __restrict__ out1, const int* __restrict__ srow_m, int M, int64_t nc, int S,
+                              float ia, const float* __restrict__ rcf, int* flags) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nc * S) return;
+    int s = (int)(t % S);
+    int64_t r = t / S;
+    int m = srow_m[r];
+    int n = m + (int)(r - st_off(m, M));
+    const int64_t rx = ex_off(m, M) + (n - m);
+    const int64_t C5 = 5 * (int64_t)S;
+    const double2* y0 = Y + rx * C5 + s;
+    const double2* yp = y0 + C5;
+    const bool hm = (n - 1 >= m);
+    const double2* ym = y0 - C5;
+    const float2 A1 = d2f2(y0[0]), B1 = d2f2(y0[S]), A2 = d2f2(y0[2 * S]), KE = d2f2(y0[4 * S]);
+    const float2 A1p = d2f2(yp[0]), B1p = d2f2(yp[S]), B2p = d2f2(yp[3 * S]);
+    const float2 A1m = hm ? d2f2(ym[0]) : fz(), B1m = hm ? d2f2(ym[S]) : fz(), B2m = hm ? d2f2(ym[3 * S]) : fz();
+    const float* c = rcf + rx * RC_NUM;
+    const float cp = c[RC_DCP], cm = c[RC_DCM], ma = (float)m * ia;
+    float2 N[3];
+    N[0] = make_float2(-fmaf(cp, B2p.x, fmaf(-cm, B2m.x, -ma * A2.y)), -fmaf(cp, B2p.y, fmaf(-cm, B2m.y, ma * A2.x)));
+    N[1] = make_float2(-fmaf(cp, B1p.x, fmaf(-cm, B1m.x, -ma * A1.y)), -fmaf(cp, B1p.y, fmaf(-cm, B1m.y, ma * A1.x)));
+    const float ke = (float)(n * (n + 1)) * ia * ia;
+    N[2] = make_float2(fmaf(cm, A1m.x, fmaf(-cp, A1p.x, fmaf(ke, KE.x, -ma * B1.y))),
+                       fmaf(cm, A1m.y, fmaf(-cp, A1p.y, fmaf(ke, KE.y, ma * B1.x))));
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        int64_t i = ((int64_t)f * nc + r) * S + s;
+        flag_nonfinite_f(flags, N[f]);
+        if (mode == POST_N) {
+            out0[i] = f2d2(N[f]);
+        } else if (mode == POST_STAGE1) {
+            const float2 ub = make_float2(N[f].x * dt, N[f].y * dt);
+            out0[i] = f2d2(ub);
+            out1[i] = dadd_f(in0[i], ub);
+        } else {
+            const float2 b = d2f2(in1[i]);
+            out0[i] = dadd_f(in0[i], make_float2(0.5f * fmaf(N[f].x, dt, b.x), 0.5f * fmaf(N[f].y, dt, b.y)));
+        }
+    }
+}
+
+// Implicit solve in increment form, one thread per (m, parity, slice):
+//   kappa = 1:  (I - alpha L) X = U       ->  X = U + D,  (I - alpha L) D = alpha L U
+//   kappa = 2:  (I - alpha L) X = (I + alpha L) U (Crank-Nicolson)  ->  X = U + D,  (I - alpha L) D = 2 alpha L U
+// then backward-Euler viscosity X <- X v_n written as U + [D - (U + D) w_n], w_n = 1 - v_n.
+// The right-hand side kappa alpha L U, the elimination (the FP32 copy of the Thomas
+// factors of k_cn_factor) and the increment are FP32; X = U + increment is one FP64 add.
+// U and X must not alias; D of delta is parked in X between the two sweeps.
+__global__ void k_cn_inc_f32(const float2* __restrict__ fac, const double2* __restrict__ U, double2* __restrict__ X,
+                             int M, int64_t nc, int S, float kalpha, float w2, float phibar, float ia2,
+                             const float* __restrict__ rcf, float vdn, int vq) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)2 * (M + 1) * S) return;
+    const int s = (int)(t % S);
+    const int mp = (int)(t / S);
+    const int m = mp >> 1, par = mp & 1;
+    const int64_t base = st_off(m, M), xbase = ex_off(m, M);
+    auto idx = [&](int f, int n) { return ((int64_t)f * nc + base + (n - m)) * S + s; };
+    auto u = [&](int f, int n) -> float2 {   // U with xi_00 = delta_00 = 0 and zero outside the triangle
+        if (n < m || n > M || (n == 0 && f > 0)) return fz();
+        return d2f2(U[idx(f, n)]);
+    };
+    auto coef = [&](int n, int k) { return rcf[(xbase + (n - m)) * RC_NUM + k]; };
+    // kappa alpha (L U) rows: Phi (n = par), delta (n = par), xi (other parity)
+    auto rhs_phi = [&](int n) { const float2 d = u(2, n); return make_float2(-kalpha * phibar * d.x, -kalpha * phibar * d.y); };
+    auto rhs_de = [&](int n) -> float2 {
+        if (n == 0) return fz();
+        const float p = w2 * coef(n, RC_P), q = w2 * coef(n, RC_Q), r = w2 * coef(n, RC_R);
+        const float lap = (float)(n * (n + 1)) * ia2;
+        const float2 ph = u(0, n), de = u(2, n), xm = u(1, n - 1), xp = u(1, n + 1);
+        return make_float2(kalpha * (lap * ph.x + p * xm.x + q * xp.x - r * de.y),
+                           kalpha * (lap * ph.y + p * xm.y + q * xp.y + r * de.x));
+    };
+    auto rhs_xi = [&](int n) -> float2 {
+        if (n < m || n > M || n == 0) return fz();
+        const float p = w2 * coef(n, RC_P), q = w2 * coef(n, RC_Q), r = w2 * coef(n, RC_R);
+        const float2 xi = u(1, n), dm = u(2, n - 1), dp = u(2, n + 1);
+        return make_float2(kalpha * (-(p * dm.x + q * dp.x) - r * xi.y), kalpha * (-(p * dm.y + q * dp.y) + r * xi.x));
+    };
+    auto cm = [](float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); };
+    auto visc_w = [&](int n) -> float {   // w_n = 1 - 1/(1 + dt nu (n(n+1)/a^2)^(q/2)), vdn = dt nu
+        if (vdn <= 0.f) return 0.f;
+        const float l = (float)(n * (n + 1)) * ia2;
+        float lq = 1.f;
+        for (int i = 0; i < vq / 2; ++i) lq *= l;
+        const float g = vdn * lq;
+        return g / (1.f + g);
+    };
+    // forward elimination over delta_n, n = m + par + 2k (d' parked in X[delta])
+    float2 dprev = fz();
+    float2 rx_lo = rhs_xi(m + par - 1);
+    int nlast = m + par - 2;
+    for (int n = m + par; n <= M; n += 2) {
+        const float2* f = fac + (base + (n - m)) * 8;
+        const float2 rx_hi = rhs_xi(n + 1);
+        float2 rhs = rhs_de(n);
+        const float2 rp = rhs_phi(n);
+        rhs.x += rp.x * f[7].x;
+        rhs.y += rp.y * f[7].x;
+        const float2 e3 = cm(f[3], rx_lo), e4 = cm(f[4], rx_hi), e0 = cm(f[0], dprev);
+        rhs = make_float2(rhs.x + e3.x + e4.x - e0.x, rhs.y + e3.y + e4.y - e0.y);
+        const float2 dp = cm(rhs, f[1]);
+        X[idx(2, n)] = f2d2(dp);
+        dprev = dp;
+        rx_lo = rx_hi;
+        nlast = n;
+    }
+    // back substitution (descending n): D_delta, D_Phi = rhs_phi - alpha Phi_bar D_delta, and the
+    // xi of the other parity just above: D_xi(n+1) = [rhs_xi(n+1) - c p D_delta(n) - c q D_delta(n+2)] / d
+    float2 dnext = fz();
+    for (int n = nlast; n >= m + par; n -= 2) {
+        const float2* f = fac + (base + (n - m)) * 8;
+        const float2 dpark = d2f2(X[idx(2, n)]);
+        const float2 e2 = cm(f[2], dnext);
+        float2 dn = make_float2(dpark.x - e2.x, dpark.y - e2.y);
+        if (n == 0) dn = fz();
+        const float2 rp = rhs_phi(n);
+        const float2 dphi = make_float2(rp.x - dn.x * f[7].y, rp.y - dn.y * f[7].y);
+        const float w = visc_w(n);
+        const float2 ud = u(2, n), up = u(0, n);
+        X[idx(2, n)] = dadd_f(U[idx(2, n)], make_float2(dn.x - (ud.x + dn.x) * w, dn.y - (ud.y + dn.y) * w));
+        X[idx(0, n)] = dadd_f(U[idx(0, n)], make_float2(dphi.x - (up.x + dphi.x) * w, dphi.y - (up.y + dphi.y) * w));
+        const int nx = n + 1;
+        if (nx <= M) {
+            const float2* fx = fac + (base + (nx - m)) * 8;
+            const float2 rxv = rhs_xi(nx);
+            const float2 num = make_float2(rxv.x - (fx[6].x * dn.x + fx[6].y * dnext.x),
+                                           rxv.y - (fx[6].x * dn.y + fx[6].y * dnext.y));
+            const float2 dxi = cm(num, fx[5]);
+            const float wx = visc_w(nx);
+            const float2 ux = u(1, nx);
+            X[idx(1, nx)] = dadd_f(U[idx(1, nx)], make_float2(dxi.x - (ux.x + dxi.x) * wx, dxi.y - (ux.y + dxi.y) * wx));
+        }
+        dnext = dn;
+    }
+    // the xi just below the first delta (parity 1: xi_m, whose lower neighbour is outside)
+    if (par == 1) {
+        const int nx = m;
+        const float2* fx = fac + (base + (nx - m)) * 8;
+        const float2 rxv = rhs_xi(nx);
+        const float2 num = make_float2(rxv.x - fx[6].y * dnext.x, rxv.y - fx[6].y * dnext.y);
+        float2 dxi = cm(num, fx[5]);
+        if (nx == 0) dxi = fz();
+        const float wx = visc_w(nx);
+        const float2 ux = u(1, nx);
+        if (nx <= M)
+            X[idx(1, nx)] = dadd_f(nx == 0 ? make_double2(0.0, 0.0) : U[idx(1, nx)],
+                                   make_float2(dxi.x - (ux.x + dxi.x) * wx, dxi.y - (ux.y + dxi.y) * wx));
+    }
+}
+
 __global__ void k_balance(const double2* __restrict__ xi, const double2* __restrict__ N,
                           const double2* __restrict__ add, double2* __restrict__ U, const int* __restrict__ srow_m,
                           int M, int64_t nc, int S, double a, double omega) {
@@ -528,23 +748,29 @@ swe_status k_unpack_scalar(const swe_plan* p, const double2* Y, double2* spec, i
 }
 swe_status k_nl_pre(const swe_plan* p, const double2* Ua, const double2* Ub, double beta, double2* X, int S,
                     cudaStream_t st) {
-    StateView v{Ua, Ub, beta, p->nc, S, p->M};
-    {
-        ProfToken tk_ = prof_begin("nl_pre", st, 0.0, 16.0 * S * (3.0 * p->nc * (beta != 0.0 ? 2.0 : 1.0) + 4.0 * p->ncx));
+    ProfToken tk_ = prof_begin("nl_pre", st, 0.0, 16.0 * S * (3.0 * p->nc * (Ub ? 2.0 : 1.0) + 4.0 * p->ncx));
+    if (p->prec == SWE_FP64) {
+        StateView v{Ua, Ub, beta, p->nc, S, p->M};
         k_nl_pre_kernel<<<nblk(p->ncx * S), 256, 0, st>>>(v, X, p->row_m, p->ncx, p->rc);
-        prof_end(tk_, st);
+    } else {
+        StateViewF v{Ua, Ub, (float)beta, p->nc, S, p->M};
+        k_nl_pre_f32<<<nblk(p->ncx * S), 256, 0, st>>>(v, X, p->row_m, p->ncx, p->rcf);
     }
+    prof_end(tk_, st);
     SWE_CHECK_LAUNCH("k_nl_pre");
     return SWE_OK;
 }
 swe_status k_nl_post(const swe_plan* p, const double2* Y, int mode, double dt, const double2* in0, const double2* in1,
                      double2* out0, double2* out1, int S, cudaStream_t st) {
-    {
-        ProfToken tk_ = prof_begin("nl_post", st, 0.0, 16.0 * S * (5.0 * p->ncx + 3.0 * p->nc * (in1 ? 4.0 : 3.0)));
+    ProfToken tk_ = prof_begin("nl_post", st, 0.0, 16.0 * S * (5.0 * p->ncx + 3.0 * p->nc * (in1 ? 4.0 : 3.0)));
+    if (p->prec == SWE_FP64) {
         k_nl_post_kernel<<<nblk(p->nc * S), 256, 0, st>>>(Y, mode, dt, in0, in1, out0, out1, p->srow_m, p->M, p->nc, S,
                                                           1.0 / p->a, p->rc, p->flags);
-        prof_end(tk_, st);
+    } else {
+        k_nl_post_f32<<<nblk(p->nc * S), 256, 0, st>>>(Y, mode, (float)dt, in0, in1, out0, out1, p->srow_m, p->M,
+                                                       p->nc, S, (float)(1.0 / p->a), p->rcf, p->flags);
     }
+    prof_end(tk_, st);
     SWE_CHECK_LAUNCH("k_nl_post");
     return SWE_OK;
 }
@@ -556,32 +782,55 @@ swe_status k_linear(const swe_plan* p, const double2* U, double2* LU, int S, cud
     return SWE_OK;
 }
 
-swe_status plan_cn_factor(swe_plan* p, double alpha, const double2** fac, cudaStream_t st) {
+swe_status plan_cn_factor(swe_plan* p, double alpha, const double2** fac, cudaStream_t st, const float2** fac32) {
     for (int i = 0; i < p->ncn; ++i)
         if (p->cn[i].alpha == alpha) {
             *fac = p->cn[i].fac;
+            if (fac32) *fac32 = p->cn[i].fac32;
             return SWE_OK;
         }
     int slot = p->ncn < 16 ? p->ncn++ : 15;
     if (p->ncn == 16 && slot == 15 && p->cn[15].fac) {
         SWE_CHECK_CUDA(cudaStreamSynchronize(st));
         cudaFree(p->cn[15].fac);
+        cudaFree(p->cn[15].fac32);
         p->cn[15].fac = nullptr;
+        p->cn[15].fac32 = nullptr;
     }
     double2* f;
     SWE_CHECK_CUDA(cudaMalloc((void**)&f, sizeof(double2) * 8 * p->nc));
     k_cn_factor<<<nblk(2 * (p->M + 1), 64), 64, 0, st>>>(p->M, alpha, p->a, p->omega, p->phibar, f);
     SWE_CHECK_LAUNCH("k_cn_factor");
+    float2* f32 = nullptr;
+    if (p->prec != SWE_FP64) {
+        SWE_CHECK_CUDA(cudaMalloc((void**)&f32, sizeof(float2) * 8 * p->nc));
+        k_to_f32<<<nblk(8 * p->nc), 256, 0, st>>>(f, f32, 8 * p->nc);
+        SWE_CHECK_LAUNCH("k_to_f32");
+    }
     p->cn[slot].alpha = alpha;
     p->cn[slot].fac = f;
+    p->cn[slot].fac32 = f32;
     *fac = f;
+    if (fac32) *fac32 = f32;
     return SWE_OK;
 }
 
 swe_status k_implicit(swe_plan* p, double alpha, int with_rhs, const double2* in, double2* out, double visc_dt,
                       double visc_nu, int visc_q, int S, cudaStream_t st) {
     const double2* fac;
-    SWE_CHECK(plan_cn_factor(p, alpha, &fac, st));
+    const float2* fac32 = nullptr;
+    SWE_CHECK(plan_cn_factor(p, alpha, &fac, st, &fac32));
+    if (p->prec != SWE_FP64 && fac32 && S > 4 && in != out) {
+        // split-precision plans, batched: FP32 increment form (right-hand side fused for CN)
+        const float kap = with_rhs ? 2.0f : 1.0f;
+        ProfToken tk = prof_begin("cn_step_f32", st, 0.0, 16.0 * p->nc * (6.0 * S + 8.0));
+        k_cn_inc_f32<<<nblk((int64_t)2 * (p->M + 1) * S, 128), 128, 0, st>>>(
+            fac32, in, out, p->M, p->nc, S, (float)(kap * alpha), (float)(2.0 * p->omega), (float)p->phibar,
+            (float)(1.0 / (p->a * p->a)), p->rcf, visc_nu > 0.0 ? (float)(visc_dt * visc_nu) : 0.f, visc_q);
+        prof_end(tk, st);
+        SWE_CHECK_LAUNCH("k_cn_inc_f32");
+        return SWE_OK;
+    }
     const double2* R = in;
     if (with_rhs) {
         if (in == out) {

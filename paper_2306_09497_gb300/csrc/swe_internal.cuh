@@ -62,6 +62,32 @@ enum RowCoef {
     RC_NUM = 8
 };
 
+// FP64 <-> FP32 conversions on the integer pipe.  GB300 executes the hardware conversion
+// instructions at its (low) FP64 rate; these bit-level versions round to nearest (ties
+// away from zero), flush results below the FP32 normal range to zero and map
+// out-of-range magnitudes to infinity (NaN stays NaN).  Used on the mixed-precision path.
+__device__ __forceinline__ float d2f_fast(double x) {
+    const unsigned long long o = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long b = o + (1ull << 28);                   // round at bit 29
+    const unsigned hi = (unsigned)(b >> 32);
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    unsigned f = sign | ((unsigned)(e - 896) << 23) | (unsigned)((b >> 29) & 0x7fffffu);
+    if (e < 897) f = sign;                                           // zero / below FP32 normals
+    if (e > 1150) f = sign | 0x7f800000u | (((o >> 52 & 0x7ffu) == 0x7ffu && (o & 0xfffffffffffffull)) ? 0x400000u : 0u);
+    return __uint_as_float(f);
+}
+__device__ __forceinline__ double f2d_fast(float v) {
+    const unsigned u = __float_as_uint(v);
+    const unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    unsigned hi = sign | ((e + 896u) << 20) | (m >> 3), lo = m << 29;
+    if (e == 0) hi = sign, lo = 0;                                   // zero (FP32 subnormals flushed)
+    if (e == 255) hi = sign | 0x7ff00000u | (m >> 3);                // inf / NaN
+    return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ float2 d2f2(double2 v) { return make_float2(d2f_fast(v.x), d2f_fast(v.y)); }
+__device__ __forceinline__ double2 f2d2(float2 v) { return make_double2(f2d_fast(v.x), f2d_fast(v.y)); }
+
 __host__ __device__ inline double eps_nm(int m, int n) {
     if (n <= m) return 0.0;
     double nn = (double)n, mm = (double)m;
@@ -72,7 +98,8 @@ __host__ __device__ inline double eps_nm(int m, int n) {
 // CN / implicit-solve factorisation for one alpha (see spectral.cu)
 struct CNFactor {
     double alpha;
-    double2* fac;   // [NC][8] complex coefficients per (m, n)
+    double2* fac;             // [NC][8] complex coefficients per (m, n)
+    float2* fac32 = nullptr;  // FP32 copy (mixed-precision plans)
 };
 
 struct Workspace {
@@ -105,8 +132,9 @@ struct swe_plan {
     Workspace ws;
     // device flags: [0] non-finite seen
     int* flags = nullptr;
-    // row coefficients [ncx][RC_NUM] (see RowCoef)
+    // row coefficients [ncx][RC_NUM] (see RowCoef), and an FP32 copy
     double* rc = nullptr;
+    float* rcf = nullptr;
     // semi-Lagrangian geometry in the grid type (extended latitudes, sin and cos of the
     // Gaussian latitudes; built on first use)
     void* thx = nullptr;
@@ -122,7 +150,8 @@ int split_tables_error(const swe_plan* p, cudaStream_t st);
 
 // plan helpers (plan.cu)
 swe_status plan_workspace(swe_plan* p, size_t bytes, char** out);
-swe_status plan_cn_factor(swe_plan* p, double alpha, const double2** fac, cudaStream_t st);
+swe_status plan_cn_factor(swe_plan* p, double alpha, const double2** fac, cudaStream_t st,
+                          const float2** fac32 = nullptr);
 
 // workspace layout of a nonlinear evaluation / stepper for S columns
 struct NLBuffers {
