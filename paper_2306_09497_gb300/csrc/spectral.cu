@@ -565,16 +565,176 @@ __global__ void k_nl_post_f32(const double2* __restrict__ Y, int mode, float dt,
     }
 }
 
-// Implicit solve in increment form, one thread per (m, parity, slice):
+// Implicit solve in increment form on split-precision plans:
 //   kappa = 1:  (I - alpha L) X = U       ->  X = U + D,  (I - alpha L) D = alpha L U
 //   kappa = 2:  (I - alpha L) X = (I + alpha L) U (Crank-Nicolson)  ->  X = U + D,  (I - alpha L) D = 2 alpha L U
 // then backward-Euler viscosity X <- X v_n written as U + [D - (U + D) w_n], w_n = 1 - v_n.
 // The right-hand side kappa alpha L U, the elimination (the FP32 copy of the Thomas
 // factors of k_cn_factor) and the increment are FP32; X = U + increment is one FP64 add.
-// U and X must not alias; D of delta is parked in X between the two sweeps.
-__global__ void k_cn_inc_f32(const float2* __restrict__ fac, const double2* __restrict__ U, double2* __restrict__ X,
-                             int M, int64_t nc, int S, float kalpha, float w2, float phibar, float ia2,
-                             const float* __restrict__ rcf, float vdn, int vq) {
+// U and X must not alias.  The two Thomas recurrences run as affine scans (as in
+// k_cn_solve_warp): one warp per (m, parity, group of 4 slices); lane = 4 kl + sl, with sl
+// the slice within the group (4 consecutive slices: 64-byte runs) and kl the position in a
+// chunk of 8 consecutive unknowns of the chain.  Passes: forward scan (d' parked in
+// X[delta]), backward scan (D_delta parked in X[delta], Phi final), xi of the other parity
+// (final), delta (final).
+__device__ __forceinline__ float2 cmf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 shfl_up_f2(float2 v, int d) {
+    return make_float2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+}
+// inclusive scan of the maps x -> A x + B over kl = 0..7 (lane stride 4)
+__device__ __forceinline__ void affine_scan8(float2& A, float2& B, int kl) {
+#pragma unroll
+    for (int d = 1; d < 8; d <<= 1) {
+        const float2 Ap = shfl_up_f2(A, 4 * d), Bp = shfl_up_f2(B, 4 * d);
+        if (kl >= d) {
+            const float2 nb = cmf(A, Bp);
+            B = make_float2(nb.x + B.x, nb.y + B.y);
+            A = cmf(A, Ap);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) k_cn_inc_scan_f32(const float2* __restrict__ fac, const double2* __restrict__ U,
+                                                         double2* __restrict__ X, int M, int64_t nc, int S,
+                                                         float kalpha, float w2, float phibar, float ia2,
+                                                         const float* __restrict__ rcf, float vdn, int vq) {
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31, sl = lane & 3, kl = lane >> 2;
+    const int SG = (S + 3) >> 2;
+    if (wid >= (int64_t)2 * (M + 1) * SG) return;          // whole warps exit together
+    const int g = (int)(wid % SG);
+    const int mp = (int)(wid / SG);
+    const int m = mp >> 1, par = mp & 1;
+    const int s = 4 * g + sl;
+    const bool sok = s < S;
+    const int64_t base = st_off(m, M), xbase = ex_off(m, M);
+    auto idx = [&](int f, int n) { return ((int64_t)f * nc + base + (n - m)) * S + s; };
+    auto coef = [&](int n, int k) { return rcf[(xbase + (n - m)) * RC_NUM + k]; };
+    auto ld = [&](int f, int n, double2& raw) -> float2 {
+        if (!sok || n < m || n > M || (n == 0 && f > 0)) {
+            raw = make_double2(0.0, 0.0);
+            return fz();
+        }
+        raw = U[idx(f, n)];
+        return d2f2(raw);
+    };
+    auto visc_w = [&](int n) -> float {
+        if (vdn <= 0.f) return 0.f;
+        const float l = (float)(n * (n + 1)) * ia2;
+        float lq = 1.f;
+        for (int i = 0; i < vq / 2; ++i) lq *= l;
+        const float gg = vdn * lq;
+        return gg / (1.f + gg);
+    };
+    auto rde = [&](int n, float2 ph, float2 de, float2 xm, float2 xp) -> float2 {
+        if (n == 0) return fz();
+        const float p = w2 * coef(n, RC_P), q = w2 * coef(n, RC_Q), r = w2 * coef(n, RC_R);
+        const float lap = (float)(n * (n + 1)) * ia2;
+        return make_float2(kalpha * (lap * ph.x + p * xm.x + q * xp.x - r * de.y),
+                           kalpha * (lap * ph.y + p * xm.y + q * xp.y + r * de.x));
+    };
+    auto rxi = [&](int n, float2 xi, float2 dm, float2 dp) -> float2 {
+        if (n < m || n > M || n == 0) return fz();
+        const float p = w2 * coef(n, RC_P), q = w2 * coef(n, RC_Q), r = w2 * coef(n, RC_R);
+        return make_float2(kalpha * (-(p * dm.x + q * dp.x) - r * xi.y), kalpha * (-(p * dm.y + q * dp.y) + r * xi.x));
+    };
+    const float kp = -kalpha * phibar;
+    const int n0 = m + par;
+    const int K = (n0 <= M) ? (M - n0) / 2 + 1 : 0;
+    double2 rw;
+    // forward elimination: d'_k = (rhs_k - a_k d'_{k-1}) g_k = A_k d'_{k-1} + B_k
+    float2 carry = fz();
+    for (int k0 = 0; k0 < K; k0 += 8) {
+        const int k = k0 + kl, n = n0 + 2 * k;
+        float2 A = fz(), B = fz();
+        if (k < K) {
+            const float2* f = fac + (base + (n - m)) * 8;
+            const float2 ph = ld(0, n, rw), de = ld(2, n, rw), dem = ld(2, n - 2, rw), dep = ld(2, n + 2, rw);
+            const float2 xm = ld(1, n - 1, rw), xp = ld(1, n + 1, rw);
+            float2 rhs = rde(n, ph, de, xm, xp);
+            const float f7 = f[7].x;
+            const float2 e3 = cmf(f[3], rxi(n - 1, xm, dem, de)), e4 = cmf(f[4], rxi(n + 1, xp, de, dep));
+            rhs = make_float2(rhs.x + kp * de.x * f7 + e3.x + e4.x, rhs.y + kp * de.y * f7 + e3.y + e4.y);
+            const float2 g1 = f[1], na = cmf(f[0], g1);
+            A = make_float2(-na.x, -na.y);
+            B = cmf(rhs, g1);
+        }
+        affine_scan8(A, B, kl);
+        const float2 ca = cmf(A, carry);
+        const float2 v = make_float2(ca.x + B.x, ca.y + B.y);
+        if (k < K && sok) X[idx(2, n)] = f2d2(v);
+        carry = make_float2(__shfl_sync(0xffffffffu, v.x, 28 + sl), __shfl_sync(0xffffffffu, v.y, 28 + sl));
+    }
+    __syncwarp();
+    // back substitution from the top: D_k = -c'_k D_{k+1} + d'_k; then Phi (final)
+    carry = fz();
+    for (int k0 = 0; k0 < K; k0 += 8) {
+        const int k = K - 1 - (k0 + kl), n = n0 + 2 * k;
+        float2 A = fz(), B = fz();
+        if (k >= 0) {
+            const float2* f = fac + (base + (n - m)) * 8;
+            const float2 c2 = f[2];
+            A = make_float2(-c2.x, -c2.y);
+            B = sok ? d2f2(X[idx(2, n)]) : fz();
+        }
+        affine_scan8(A, B, kl);
+        const float2 ca = cmf(A, carry);
+        float2 dn = make_float2(ca.x + B.x, ca.y + B.y);
+        carry = make_float2(__shfl_sync(0xffffffffu, dn.x, 28 + sl), __shfl_sync(0xffffffffu, dn.y, 28 + sl));
+        if (k >= 0 && sok) {
+            if (n == 0) dn = fz();
+            const float2* f = fac + (base + (n - m)) * 8;
+            double2 up_raw;
+            const float2 up = ld(0, n, up_raw), ud = ld(2, n, rw);
+            const float2 dphi = make_float2(kp * ud.x - dn.x * f[7].y, kp * ud.y - dn.y * f[7].y);
+            const float w = visc_w(n);
+            X[idx(2, n)] = f2d2(dn);
+            X[idx(0, n)] = dadd_f(up_raw, make_float2(dphi.x - (up.x + dphi.x) * w, dphi.y - (up.y + dphi.y) * w));
+        }
+    }
+    __syncwarp();
+    // xi on the other parity: D_xi = [rhs_xi - c p D_delta(n-1) - c q D_delta(n+1)] / d_n (final)
+    const int nx0 = m + (par ^ 1);
+    const int J = (nx0 <= M) ? (M - nx0) / 2 + 1 : 0;
+    for (int j0 = 0; j0 < J; j0 += 8) {
+        const int j = j0 + kl, n = nx0 + 2 * j;
+        if (j < J && sok) {
+            const float2* f = fac + (base + (n - m)) * 8;
+            double2 ux_raw;
+            const float2 ux = ld(1, n, ux_raw), dmu = ld(2, n - 1, rw), dpu = ld(2, n + 1, rw);
+            const float2 Dm = (n - 1 >= m) ? d2f2(X[idx(2, n - 1)]) : fz();
+            const float2 Dp = (n + 1 <= M) ? d2f2(X[idx(2, n + 1)]) : fz();
+            const float2 rxv = rxi(n, ux, dmu, dpu);
+            const float2 num = make_float2(rxv.x - (f[6].x * Dm.x + f[6].y * Dp.x), rxv.y - (f[6].x * Dm.y + f[6].y * Dp.y));
+            const float2 dxi = cmf(num, f[5]);
+            const float w = visc_w(n);
+            X[idx(1, n)] = n == 0 ? make_double2(0.0, 0.0)
+                                  : dadd_f(ux_raw, make_float2(dxi.x - (ux.x + dxi.x) * w, dxi.y - (ux.y + dxi.y) * w));
+        }
+    }
+    __syncwarp();
+    // delta (final) from the parked D_delta
+    for (int k0 = 0; k0 < K; k0 += 8) {
+        const int k = k0 + kl, n = n0 + 2 * k;
+        if (k < K && sok) {
+            double2 ud_raw;
+            const float2 ud = ld(2, n, ud_raw), dn = d2f2(X[idx(2, n)]);
+            const float w = visc_w(n);
+            X[idx(2, n)] = n == 0 ? make_double2(0.0, 0.0)
+                                  : dadd_f(ud_raw, make_float2(dn.x - (ud.x + dn.x) * w, dn.y - (ud.y + dn.y) * w));
+        }
+    }
+}
+
+// The same solve with one thread per (m, parity, slice) walking its chain sequentially
+// (rolling registers: every value of U is converted once per sweep).  Latency-bound for
+// moderate batches, but the cheapest per element once the batch alone fills the GPU.
+__global__ void __launch_bounds__(128) k_cn_inc_f32(const float2* __restrict__ fac, const double2* __restrict__ U,
+                                                    double2* __restrict__ X, int M, int64_t nc, int S, float kalpha,
+                                                    float w2, float phibar, float ia2, const float* __restrict__ rcf,
+                                                    float vdn, int vq) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= (int64_t)2 * (M + 1) * S) return;
     const int s = (int)(t % S);
@@ -582,29 +742,8 @@ __global__ void k_cn_inc_f32(const float2* __restrict__ fac, const double2* __re
     const int m = mp >> 1, par = mp & 1;
     const int64_t base = st_off(m, M), xbase = ex_off(m, M);
     auto idx = [&](int f, int n) { return ((int64_t)f * nc + base + (n - m)) * S + s; };
-    auto u = [&](int f, int n) -> float2 {   // U with xi_00 = delta_00 = 0 and zero outside the triangle
-        if (n < m || n > M || (n == 0 && f > 0)) return fz();
-        return d2f2(U[idx(f, n)]);
-    };
     auto coef = [&](int n, int k) { return rcf[(xbase + (n - m)) * RC_NUM + k]; };
-    // kappa alpha (L U) rows: Phi (n = par), delta (n = par), xi (other parity)
-    auto rhs_phi = [&](int n) { const float2 d = u(2, n); return make_float2(-kalpha * phibar * d.x, -kalpha * phibar * d.y); };
-    auto rhs_de = [&](int n) -> float2 {
-        if (n == 0) return fz();
-        const float p = w2 * coef(n, RC_P), q = w2 * coef(n, RC_Q), r = w2 * coef(n, RC_R);
-        const float lap = (float)(n * (n + 1)) * ia2;
-        const float2 ph = u(0, n), de = u(2, n), xm = u(1, n - 1), xp = u(1, n + 1);
-        return make_float2(kalpha * (lap * ph.x + p * xm.x + q * xp.x - r * de.y),
-                           kalpha * (lap * ph.y + p * xm.y + q * xp.y + r * de.x));
-    };
-    auto rhs_xi = [&](int n) -> float2 {
-        if (n < m || n > M || n == 0) return fz();
-        const float p = w2 * coef(n, RC_P), q = w2 * coef(n, RC_Q), r = w2 * coef(n, RC_R);
-        const float2 xi = u(1, n), dm = u(2, n - 1), dp = u(2, n + 1);
-        return make_float2(kalpha * (-(p * dm.x + q * dp.x) - r * xi.y), kalpha * (-(p * dm.y + q * dp.y) + r * xi.x));
-    };
-    auto cm = [](float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); };
-    auto visc_w = [&](int n) -> float {   // w_n = 1 - 1/(1 + dt nu (n(n+1)/a^2)^(q/2)), vdn = dt nu
+    auto visc_w = [&](int n) -> float {
         if (vdn <= 0.f) return 0.f;
         const float l = (float)(n * (n + 1)) * ia2;
         float lq = 1.f;
@@ -612,66 +751,96 @@ __global__ void k_cn_inc_f32(const float2* __restrict__ fac, const double2* __re
         const float g = vdn * lq;
         return g / (1.f + g);
     };
-    // forward elimination over delta_n, n = m + par + 2k (d' parked in X[delta])
+    auto ld = [&](int f, int n, double2& raw) -> float2 {
+        if (n < m || n > M || (n == 0 && f > 0)) {
+            raw = make_double2(0.0, 0.0);
+            return fz();
+        }
+        raw = U[idx(f, n)];
+        return d2f2(raw);
+    };
+    auto rde = [&](int n, float2 ph, float2 de, float2 xm, float2 xp) -> float2 {
+        if (n == 0) return fz();
+        const float p = w2 * coef(n, RC_P), q = w2 * coef(n, RC_Q), r = w2 * coef(n, RC_R);
+        const float lap = (float)(n * (n + 1)) * ia2;
+        return make_float2(kalpha * (lap * ph.x + p * xm.x + q * xp.x - r * de.y),
+                           kalpha * (lap * ph.y + p * xm.y + q * xp.y + r * de.x));
+    };
+    auto rxi = [&](int n, float2 xi, float2 dm, float2 dp) -> float2 {
+        if (n < m || n > M || n == 0) return fz();
+        const float p = w2 * coef(n, RC_P), q = w2 * coef(n, RC_Q), r = w2 * coef(n, RC_R);
+        return make_float2(kalpha * (-(p * dm.x + q * dp.x) - r * xi.y), kalpha * (-(p * dm.y + q * dp.y) + r * xi.x));
+    };
+    const float kp = -kalpha * phibar;
+    // forward elimination (d' parked in X[delta]); de0 = delta_n, de2 = delta_{n+2}, xlo/xhi = xi_{n-1}/xi_{n+1}
+    const int n0 = m + par;
+    double2 rw;
+    float2 de0 = ld(2, n0, rw), de2 = ld(2, n0 + 2, rw);
+    float2 xlo = ld(1, n0 - 1, rw), xhi = ld(1, n0 + 1, rw);
     float2 dprev = fz();
-    float2 rx_lo = rhs_xi(m + par - 1);
-    int nlast = m + par - 2;
-    for (int n = m + par; n <= M; n += 2) {
+    float2 rx_lo = rxi(n0 - 1, xlo, ld(2, n0 - 2, rw), de0);
+    int nlast = n0 - 2;
+    for (int n = n0; n <= M; n += 2) {
         const float2* f = fac + (base + (n - m)) * 8;
-        const float2 rx_hi = rhs_xi(n + 1);
-        float2 rhs = rhs_de(n);
-        const float2 rp = rhs_phi(n);
-        rhs.x += rp.x * f[7].x;
-        rhs.y += rp.y * f[7].x;
-        const float2 e3 = cm(f[3], rx_lo), e4 = cm(f[4], rx_hi), e0 = cm(f[0], dprev);
-        rhs = make_float2(rhs.x + e3.x + e4.x - e0.x, rhs.y + e3.y + e4.y - e0.y);
-        const float2 dp = cm(rhs, f[1]);
+        const float2 ph = ld(0, n, rw);
+        const float2 rx_hi = rxi(n + 1, xhi, de0, de2);
+        float2 rhs = rde(n, ph, de0, xlo, xhi);
+        const float2 e3 = cmf(f[3], rx_lo), e4 = cmf(f[4], rx_hi), e0 = cmf(f[0], dprev);
+        rhs = make_float2(rhs.x + kp * de0.x * f[7].x + e3.x + e4.x - e0.x,
+                          rhs.y + kp * de0.y * f[7].x + e3.y + e4.y - e0.y);
+        const float2 dp = cmf(rhs, f[1]);
         X[idx(2, n)] = f2d2(dp);
         dprev = dp;
         rx_lo = rx_hi;
         nlast = n;
+        xlo = xhi;
+        xhi = ld(1, n + 3, rw);
+        de0 = de2;
+        de2 = ld(2, n + 4, rw);
     }
-    // back substitution (descending n): D_delta, D_Phi = rhs_phi - alpha Phi_bar D_delta, and the
-    // xi of the other parity just above: D_xi(n+1) = [rhs_xi(n+1) - c p D_delta(n) - c q D_delta(n+2)] / d
+    // back substitution (descending): D_delta, Phi (final), and the xi just above (final);
+    // dup = delta_{n+2} of U, dnext = D_delta(n+2)
     float2 dnext = fz();
-    for (int n = nlast; n >= m + par; n -= 2) {
+    float2 dup = ld(2, nlast + 2, rw);
+    for (int n = nlast; n >= n0; n -= 2) {
         const float2* f = fac + (base + (n - m)) * 8;
+        double2 ud_raw, up_raw, ux_raw;
+        const float2 ud = ld(2, n, ud_raw), up = ld(0, n, up_raw);
         const float2 dpark = d2f2(X[idx(2, n)]);
-        const float2 e2 = cm(f[2], dnext);
+        const float2 e2 = cmf(f[2], dnext);
         float2 dn = make_float2(dpark.x - e2.x, dpark.y - e2.y);
         if (n == 0) dn = fz();
-        const float2 rp = rhs_phi(n);
-        const float2 dphi = make_float2(rp.x - dn.x * f[7].y, rp.y - dn.y * f[7].y);
+        const float2 dphi = make_float2(kp * ud.x - dn.x * f[7].y, kp * ud.y - dn.y * f[7].y);
         const float w = visc_w(n);
-        const float2 ud = u(2, n), up = u(0, n);
-        X[idx(2, n)] = dadd_f(U[idx(2, n)], make_float2(dn.x - (ud.x + dn.x) * w, dn.y - (ud.y + dn.y) * w));
-        X[idx(0, n)] = dadd_f(U[idx(0, n)], make_float2(dphi.x - (up.x + dphi.x) * w, dphi.y - (up.y + dphi.y) * w));
+        X[idx(2, n)] = n == 0 ? make_double2(0.0, 0.0)
+                              : dadd_f(ud_raw, make_float2(dn.x - (ud.x + dn.x) * w, dn.y - (ud.y + dn.y) * w));
+        X[idx(0, n)] = dadd_f(up_raw, make_float2(dphi.x - (up.x + dphi.x) * w, dphi.y - (up.y + dphi.y) * w));
         const int nx = n + 1;
         if (nx <= M) {
             const float2* fx = fac + (base + (nx - m)) * 8;
-            const float2 rxv = rhs_xi(nx);
+            const float2 ux = ld(1, nx, ux_raw);
+            const float2 rxv = rxi(nx, ux, ud, dup);
             const float2 num = make_float2(rxv.x - (fx[6].x * dn.x + fx[6].y * dnext.x),
                                            rxv.y - (fx[6].x * dn.y + fx[6].y * dnext.y));
-            const float2 dxi = cm(num, fx[5]);
+            const float2 dxi = cmf(num, fx[5]);
             const float wx = visc_w(nx);
-            const float2 ux = u(1, nx);
-            X[idx(1, nx)] = dadd_f(U[idx(1, nx)], make_float2(dxi.x - (ux.x + dxi.x) * wx, dxi.y - (ux.y + dxi.y) * wx));
+            X[idx(1, nx)] = dadd_f(ux_raw, make_float2(dxi.x - (ux.x + dxi.x) * wx, dxi.y - (ux.y + dxi.y) * wx));
         }
         dnext = dn;
+        dup = ud;
     }
     // the xi just below the first delta (parity 1: xi_m, whose lower neighbour is outside)
     if (par == 1) {
         const int nx = m;
         const float2* fx = fac + (base + (nx - m)) * 8;
-        const float2 rxv = rhs_xi(nx);
+        double2 ux_raw;
+        const float2 ux = ld(1, nx, ux_raw);
+        const float2 rxv = rxi(nx, ux, fz(), dup);
         const float2 num = make_float2(rxv.x - fx[6].y * dnext.x, rxv.y - fx[6].y * dnext.y);
-        float2 dxi = cm(num, fx[5]);
-        if (nx == 0) dxi = fz();
+        const float2 dxi = cmf(num, fx[5]);
         const float wx = visc_w(nx);
-        const float2 ux = u(1, nx);
-        if (nx <= M)
-            X[idx(1, nx)] = dadd_f(nx == 0 ? make_double2(0.0, 0.0) : U[idx(1, nx)],
-                                   make_float2(dxi.x - (ux.x + dxi.x) * wx, dxi.y - (ux.y + dxi.y) * wx));
+        X[idx(1, nx)] = nx == 0 ? make_double2(0.0, 0.0)
+                                : dadd_f(ux_raw, make_float2(dxi.x - (ux.x + dxi.x) * wx, dxi.y - (ux.y + dxi.y) * wx));
     }
 }
 
@@ -824,9 +993,17 @@ swe_status k_implicit(swe_plan* p, double alpha, int with_rhs, const double2* in
         // split-precision plans, batched: FP32 increment form (right-hand side fused for CN)
         const float kap = with_rhs ? 2.0f : 1.0f;
         ProfToken tk = prof_begin("cn_step_f32", st, 0.0, 16.0 * p->nc * (6.0 * S + 8.0));
-        k_cn_inc_f32<<<nblk((int64_t)2 * (p->M + 1) * S, 128), 128, 0, st>>>(
-            fac32, in, out, p->M, p->nc, S, (float)(kap * alpha), (float)(2.0 * p->omega), (float)p->phibar,
-            (float)(1.0 / (p->a * p->a)), p->rcf, visc_nu > 0.0 ? (float)(visc_dt * visc_nu) : 0.f, visc_q);
+        const float ka = (float)(kap * alpha), w2 = (float)(2.0 * p->omega), pb = (float)p->phibar;
+        const float ia2 = (float)(1.0 / (p->a * p->a)), vdn = visc_nu > 0.0 ? (float)(visc_dt * visc_nu) : 0.f;
+        if (S >= 512) {
+            // the batch alone fills the GPU with chains: one thread per chain
+            k_cn_inc_f32<<<nblk((int64_t)2 * (p->M + 1) * S, 128), 128, 0, st>>>(fac32, in, out, p->M, p->nc, S, ka,
+                                                                                w2, pb, ia2, p->rcf, vdn, visc_q);
+        } else {
+            const int64_t nwarps = (int64_t)2 * (p->M + 1) * ((S + 3) / 4);
+            k_cn_inc_scan_f32<<<nblk(nwarps * 32, 128), 128, 0, st>>>(fac32, in, out, p->M, p->nc, S, ka, w2, pb,
+                                                                       ia2, p->rcf, vdn, visc_q);
+        }
         prof_end(tk, st);
         SWE_CHECK_LAUNCH("k_cn_inc_f32");
         return SWE_OK;

@@ -57,29 +57,31 @@ def test_split_sht_forward(mixed):
         assert np.max(np.abs(got[b] - ref)) < 5e-6 * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("M,nlat,nlon,nsteps", [(63, 96, 192, 12), (255, 384, 768, 3)])
-def test_split_imex_propagation_height_bound(M, nlat, nlon, nsteps):
+# S = 2 runs the small-batch implicit solve (FP64), S = 6 the batched FP32 increment form
+# (one ragged group of four slices); the T63 S = 6 case adds 4th-order hyperviscosity
+@pytest.mark.parametrize("M,nlat,nlon,nsteps,S,q,nu", [(63, 96, 192, 12, 2, 2, 0.0), (63, 96, 192, 12, 6, 4, 1e15),
+                                                       (255, 384, 768, 3, 2, 2, 0.0), (255, 384, 768, 3, 6, 2, 0.0)])
+def test_split_imex_propagation_height_bound(M, nlat, nlon, nsteps, S, q, nu):
     from paper_2306_09497_gb300 import swe
     plan = swe.Plan(M, nlat, nlon, prec=swe.SWE_SPLIT_BF16X3)
     s = Sphere(M, nlat, nlon)
     sw = SWE(s)
-    S = 2
     U0 = []
-    for seed in (31, 32):
+    for seed in range(31, 31 + S):
         xi, noise = inputs.initial_fields(M, seed)
         xd = s.unpack(xi)
         U0.append(to_packed(s, (sw.balanced_geopotential(xd) + s.unpack(noise), xd, np.zeros_like(xd))))
     U0 = np.stack(U0)
     dt = 432000.0 / 7296.0 if M == 255 else 240.0
     out = torch.empty((S, 3, plan.nc * 2), dtype=torch.float64, device="cuda")
-    plan.propagate(swe.stepper(swe.SWE_IMEX, dt, nsteps), _dev(U0), out, S)
+    plan.propagate(swe.stepper(swe.SWE_IMEX, dt, nsteps, q, nu), _dev(U0), out, S)
     got = out.cpu().numpy().view(np.complex128).reshape(S, 3, -1)
     m, _ = inputs.mn_arrays(M)
     w = np.where(m == 0, 1.0, 2.0)
-    for b in range(1):
+    for b in sorted({0, S - 1}):
         U = to_dense(s, U0[b])
         for _ in range(nsteps):
-            U = sw.imex_step(U, dt)
+            U = sw.imex_step(U, dt, nu=nu, q=q)
         ref = to_packed(s, U)
         err = [np.sqrt(np.sum(w * np.abs(got[b, f] - ref[f]) ** 2) / np.sum(w * np.abs(ref[f]) ** 2)) for f in range(3)]
         assert err[0] < 1e-6, err
@@ -161,3 +163,57 @@ def test_split_nonlinear_matches_oracle(M, nlat, nlon):
         for f in range(3):
             err = np.sqrt(np.sum(w * np.abs(got[b, f] - ref[f]) ** 2) / np.sum(w * np.abs(ref[f]) ** 2))
             assert err < bound[f], (b, f, err)
+
+
+@pytest.mark.parametrize("M,nlat,nlon,S", [(63, 96, 192, 7), (127, 192, 384, 7), (31, 48, 96, 520)],
+                         ids=["T63-S7", "T127-S7", "T31-S520"])
+def test_split_implicit_solve_matches_oracle(M, nlat, nlon, S):
+    """(I - alpha L) X = R on the split path in the batched FP32 increment form X = R + D,
+    (I - alpha L) D = alpha L R (S = 7: warp-scan kernel; S = 520: one thread per chain).
+    D carries FP32 rounding relative to its own size, at most that of X: 1e-6 per field."""
+    from paper_2306_09497_gb300 import swe
+    plan = swe.Plan(M, nlat, nlon, prec=swe.SWE_SPLIT_BF16X3)
+    s = Sphere(M, nlat, nlon)
+    sw = SWE(s)
+    R = inputs.random_state(M, S, 9)
+    out = torch.empty((S, 3, plan.nc * 2), dtype=torch.float64, device="cuda")
+    alpha = 450.0
+    plan.implicit_solve(alpha, _dev(R), out, S)
+    got = out.cpu().numpy().view(np.complex128).reshape(S, 3, -1)
+    plan.close()
+    m, _ = inputs.mn_arrays(M)
+    w = np.where(m == 0, 1.0, 2.0)
+    for b in (0, 3, S // 2 + 1, S - 1):
+        Rd = list(to_dense(s, R[b]))
+        Rd[1][0, 0] = 0.0
+        Rd[2][0, 0] = 0.0
+        ref = to_packed(s, sw.implicit_solve(tuple(Rd), alpha))
+        for f in range(3):
+            err = np.sqrt(np.sum(w * np.abs(got[b, f] - ref[f]) ** 2) / np.sum(w * np.abs(ref[f]) ** 2))
+            assert err < 1e-6, (b, f, err)
+
+
+def test_split_imex_large_batch_matches_oracle():
+    """One IMEX step (CN in increment form, kappa = 2, with 4th-order hyperviscosity) on a
+    batch large enough (S = 520) for the one-thread-per-chain implicit kernel; sampled slices
+    against the oracle with the height bound."""
+    from paper_2306_09497_gb300 import swe
+    M, nlat, nlon, S = 31, 48, 96, 520
+    plan = swe.Plan(M, nlat, nlon, prec=swe.SWE_SPLIT_BF16X3)
+    s = Sphere(M, nlat, nlon)
+    sw = SWE(s)
+    U0 = inputs.random_state(M, S, 11)
+    dt, q, nu = 900.0, 4, 1e16
+    out = torch.empty((S, 3, plan.nc * 2), dtype=torch.float64, device="cuda")
+    plan.propagate(swe.stepper(swe.SWE_IMEX, dt, 1, q, nu), _dev(U0), out, S)
+    got = out.cpu().numpy().view(np.complex128).reshape(S, 3, -1)
+    plan.close()
+    m, _ = inputs.mn_arrays(M)
+    w = np.where(m == 0, 1.0, 2.0)
+    for b in (0, 257, S - 1):
+        Ud = list(to_dense(s, U0[b]))
+        Ud[1][0, 0] = 0.0
+        Ud[2][0, 0] = 0.0
+        ref = to_packed(s, sw.imex_step(tuple(Ud), dt, nu=nu, q=q))
+        err = [np.sqrt(np.sum(w * np.abs(got[b, f] - ref[f]) ** 2) / np.sum(w * np.abs(ref[f]) ** 2)) for f in range(3)]
+        assert err[0] < 1e-6 and err[1] < 1e-5 and err[2] < 1e-5, (b, err)

@@ -62,18 +62,20 @@ def test_sl_matches_oracle_fp64(M, nlat, nlon, scheme, nsteps):
     plan.close()
 
 
-def test_sl_mixed_height_bound():
+@pytest.mark.parametrize("S", [1, 6])
+def test_sl_mixed_height_bound(S):
+    """S = 1: small-batch implicit solve (FP64); S = 6: batched FP32 increment form."""
     from paper_2306_09497_gb300 import swe
     M, nlat, nlon = 63, 96, 192
     plan = swe.Plan(M, nlat, nlon, prec=swe.SWE_SPLIT_BF16X3)
     s = Sphere(M, nlat, nlon)
     sw = SWE(s)
-    U0 = _states(s, sw, (43,))
+    U0 = _states(s, sw, tuple(range(43, 43 + S)))
     dt, nsteps = 1800.0, 3
-    out = torch.empty((1, 3, plan.nc * 2), dtype=torch.float64, device="cuda")
-    plan.propagate(swe.stepper(swe.SWE_SLSI_SETTLS, dt, nsteps, 2, 1e5), _dev(U0), out, 1)
-    got = out.cpu().numpy().view(np.complex128).reshape(3, -1)
-    U, prev = to_dense(s, U0[0]), None
+    out = torch.empty((S, 3, plan.nc * 2), dtype=torch.float64, device="cuda")
+    plan.propagate(swe.stepper(swe.SWE_SLSI_SETTLS, dt, nsteps, 2, 1e5), _dev(U0), out, S)
+    got = out.cpu().numpy().view(np.complex128).reshape(S, 3, -1)[S - 1]
+    U, prev = to_dense(s, U0[S - 1]), None
     for k in range(nsteps):
         nxt = sw.sl_si_settls_step(U, prev if k > 0 else None, dt, nu=1e5, q=2)
         prev, U = U, nxt
