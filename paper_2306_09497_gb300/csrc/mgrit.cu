@@ -160,6 +160,16 @@ struct MGLevel {
     double2* x0 = nullptr;      // initial condition at this resolution
     bool g_on = false;
     bool two_step = false;
+    // serial coarsest-level solve, captured into a CUDA graph after one uncaptured pass
+    // (which sizes the plan's buffers); one graph per FAS right-hand-side state (g_on)
+    struct Graph {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        unsigned long long gen = 0;   // plan generation at capture
+        long long launches = 0;       // kernels per replay
+        int passes = 0;               // uncaptured passes so far
+        bool off = false;             // capture failed: stay uncaptured
+    } cg[2];
 };
 
 struct swe_mgrit {
@@ -233,7 +243,7 @@ static swe_status correct_level(swe_mgrit* g, int l) {
     return f_relax(g, l);
 }
 
-static swe_status solve_coarsest(swe_mgrit* g, int l) {
+static swe_status solve_coarsest_body(swe_mgrit* g, int l) {
     MGLevel& L = g->lv[l];
     if (L.g_on)
         SWE_CHECK_CUDA(cudaMemcpyAsync(L.u, L.g, sizeof(double2) * L.per, cudaMemcpyDeviceToDevice, g->cs));
@@ -251,6 +261,52 @@ static swe_status solve_coarsest(swe_mgrit* g, int l) {
             SWE_CHECK(mg_step_batch(g, l, L.u + (i - 1) * L.per, 1, out, 1, add, 1, 1));
         }
     }
+    return SWE_OK;
+}
+
+static void drop_graph(MGLevel::Graph& G) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.graph) cudaGraphDestroy(G.graph);
+    G.exec = nullptr;
+    G.graph = nullptr;
+}
+
+static swe_status solve_coarsest(swe_mgrit* g, int l) {
+    MGLevel& L = g->lv[l];
+    MGLevel::Graph& G = L.cg[L.g_on ? 1 : 0];
+    if (G.exec && G.gen != L.plan->gen) {
+        // a plan buffer the graph points into was reallocated since the capture
+        SWE_CHECK_CUDA(cudaStreamSynchronize(g->cs));
+        drop_graph(G);
+        G.passes = 0;
+    }
+    if (!G.exec && (G.off || G.passes < 1)) {
+        G.passes += 1;
+        return solve_coarsest_body(g, l);
+    }
+    if (!G.exec) {
+        const long long before = swe_launch_count();
+        const unsigned long long gen0 = L.plan->gen;
+        SWE_CHECK_CUDA(cudaStreamBeginCapture(g->cs, cudaStreamCaptureModeThreadLocal));
+        const swe_status st = solve_coarsest_body(g, l);
+        cudaGraph_t gr = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(g->cs, &gr);
+        // captured launches did not execute: they are counted at each replay instead
+        G.launches = swe_launch_count() - before;
+        prof_launch(-G.launches);
+        if (st != SWE_OK || e != cudaSuccess || L.plan->gen != gen0) {
+            // not capturable as it stands (e.g. a buffer had to grow): run it uncaptured from now on
+            if (gr) cudaGraphDestroy(gr);
+            cudaGetLastError();
+            G.off = true;
+            return solve_coarsest_body(g, l);
+        }
+        G.graph = gr;
+        SWE_CHECK_CUDA(cudaGraphInstantiate(&G.exec, gr, 0));
+        G.gen = L.plan->gen;
+    }
+    SWE_CHECK_CUDA(cudaGraphLaunch(G.exec, g->cs));
+    prof_launch(G.launches);
     return SWE_OK;
 }
 
@@ -335,7 +391,10 @@ extern "C" swe_status swe_mgrit_create(const swe_mgrit_desc* d, swe_mgrit_t* out
 
 extern "C" swe_status swe_mgrit_destroy(swe_mgrit_t g) {
     if (!g) return SWE_OK;
+    if (g->cs) cudaStreamSynchronize(g->cs);
     for (auto& L : g->lv) {
+        drop_graph(L.cg[0]);
+        drop_graph(L.cg[1]);
         cudaFree(L.u);
         cudaFree(L.g);
         cudaFree(L.v);

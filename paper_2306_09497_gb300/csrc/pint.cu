@@ -20,6 +20,7 @@ struct swe_pint {
     cudaGraphExec_t gexec = nullptr;
     long long graph_launches = 0;   // kernels per replay of the captured chain
     bool ready = false;
+    unsigned long long gen_f = 0, gen_c = 0;   // plan generations the graph was captured at
 };
 
 namespace {
@@ -202,6 +203,15 @@ extern "C" swe_status parareal_iterate(swe_pint_t p, int kmax, double tol, int* 
         // fine propagator on every slice at once
         SWE_CHECK(propagate_F(p->d.fine_plan, &p->d.fine, (const double*)p->U, (double*)p->Fo, S, p->cs));
         if (p->d.use_graphs) {
+            if (p->ready && (p->gen_f != p->d.fine_plan->gen || p->gen_c != p->d.coarse_plan->gen)) {
+                // a plan buffer the graph points into was reallocated: capture again
+                SWE_CHECK_CUDA(cudaStreamSynchronize(p->cs));
+                cudaGraphExecDestroy(p->gexec);
+                cudaGraphDestroy(p->graph);
+                p->gexec = nullptr;
+                p->graph = nullptr;
+                p->ready = false;
+            }
             if (!p->ready) {
                 const long long before = swe_launch_count();
                 SWE_CHECK_CUDA(cudaStreamBeginCapture(p->cs, cudaStreamCaptureModeThreadLocal));
@@ -216,6 +226,8 @@ extern "C" swe_status parareal_iterate(swe_pint_t p, int kmax, double tol, int* 
                 p->graph = g;
                 SWE_CHECK_CUDA(cudaGraphInstantiate(&p->gexec, g, 0));
                 p->ready = true;
+                p->gen_f = p->d.fine_plan->gen;
+                p->gen_c = p->d.coarse_plan->gen;
             }
             SWE_CHECK_CUDA(cudaGraphLaunch(p->gexec, p->cs));
             prof_launch(p->graph_launches);

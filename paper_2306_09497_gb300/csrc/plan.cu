@@ -286,6 +286,7 @@ swe_status plan_workspace(swe_plan* p, size_t bytes, char** out) {
             p->ws.bytes = 0;
         }
         size_t want = bytes + bytes / 8 + (1u << 20);
+        p->gen += 1;
         cudaError_t e = cudaMalloc((void**)&p->ws.base, want);
         if (e != cudaSuccess) return swe_cuda_status(e, "cudaMalloc(workspace)");
         p->ws.bytes = want;

@@ -345,6 +345,7 @@ static SLBuf sl_carve(const swe_plan* p, char* c, int S) {
 static swe_status ensure_thx(swe_plan* p) {
     if (p->thx) return SWE_OK;
     const size_t n = 3 * (size_t)p->nlat + 4;
+    p->gen += 1;
     if (p->prec == SWE_FP64) {
         SWE_CHECK_CUDA(cudaMalloc(&p->thx, sizeof(double) * n));
         k_sl_table<double><<<nb(p->nlat + 4, 64), 64>>>(p->mu, (double*)p->thx, p->nlat);

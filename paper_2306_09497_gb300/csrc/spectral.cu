@@ -959,6 +959,7 @@ swe_status plan_cn_factor(swe_plan* p, double alpha, const double2** fac, cudaSt
             return SWE_OK;
         }
     int slot = p->ncn < 16 ? p->ncn++ : 15;
+    p->gen += 1;
     if (p->ncn == 16 && slot == 15 && p->cn[15].fac) {
         SWE_CHECK_CUDA(cudaStreamSynchronize(st));
         cudaFree(p->cn[15].fac);

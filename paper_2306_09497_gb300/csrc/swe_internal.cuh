@@ -140,6 +140,10 @@ struct swe_plan {
     void* thx = nullptr;
     // launch configuration of the fused nonlinear ring kernel (autotuned on first large call)
     int ring_cfg = -1, ring_G = 1;
+    // bumped whenever a plan-owned device buffer is allocated, grown or freed after creation
+    // (workspace, implicit-solve factors, SL geometry): a CUDA graph that captured pointers
+    // into the plan is valid only while the generation it was captured at is current
+    unsigned long long gen = 0;
 };
 
 // ---------------------------------------------------------------------------

@@ -32,21 +32,39 @@ def _init(s, sw, seed):
     return (sw.balanced_geopotential(xd) + s.unpack(noise), xd, np.zeros_like(xd))
 
 
+# T63 IMEX level 0, SL-SI-SETTLS levels 1-2 on T31: the split-precision test case, also run in FP64
+CASE_MIXED = ([(63, 96, 192, 0, 240.0, 2, 0.0), (31, 48, 96, 2, 480.0, 2, 1e5), (31, 48, 96, 1, 960.0, 2, 1e5)],
+              32, 2, 0, 2)
 CASES = [
     # (levels: list of (M, nlat, nlon, scheme, dt, q, nu)), N0, cf, nu_relax, cycles
     ([(31, 48, 96, 0, 300.0, 2, 0.0), (31, 48, 96, 0, 600.0, 2, 1e5), (31, 48, 96, 0, 1200.0, 2, 1e5)], 16, 2, 0, 2),
     ([(31, 48, 96, 0, 300.0, 2, 0.0), (31, 48, 96, 0, 1200.0, 4, 1e15)], 16, 4, 1, 2),
     ([(31, 48, 96, 0, 300.0, 2, 0.0), (21, 32, 64, 2, 600.0, 2, 1e5), (21, 32, 64, 1, 1200.0, 2, 1e5)], 8, 2, 0, 2),
+    CASE_MIXED,
 ]
 
 
-@pytest.mark.parametrize("case", CASES, ids=["imex3", "imex2_fcf", "sl_coarse3"])
+@pytest.mark.parametrize("case", CASES, ids=["imex3", "imex2_fcf", "sl_coarse3", "t63_sl_coarse3"])
 def test_mgrit_matches_oracle(case):
+    _run_case(case, mixed=False)
+
+
+def test_mgrit_mixed_matches_oracle():
+    """Split-precision MGRIT (the benchmark's precision): T63 IMEX level 0 with batches of 16
+    intervals (the batched FP32 increment solve), SL-SI-SETTLS levels 1-2 on T31 (two-step on
+    the serial coarsest level, replayed from a CUDA graph from the second cycle on).  C-points
+    after every cycle against the FP64 oracle: 1e-6 on the full height field (measured 8e-8),
+    1e-5 for Phi' and xi (measured 5e-6), 1e-4 for delta (measured 2.5e-5)."""
+    _run_case(CASE_MIXED, mixed=True)
+
+
+def _run_case(case, mixed):
     from paper_2306_09497_gb300 import swe
     levels, N0, cf, nu, cycles = case
+    prec = swe.SWE_SPLIT_BF16X3 if mixed else swe.SWE_FP64
     plans, steps, sph, sws = [], [], [], []
     for (M, nlat, nlon, scheme, dt, q, visc) in levels:
-        plans.append(swe.Plan(M, nlat, nlon))
+        plans.append(swe.Plan(M, nlat, nlon, prec=prec))
         steps.append(swe.stepper(scheme, dt, 1, q, visc))
         s = Sphere(M, nlat, nlon)
         sph.append(s)
@@ -86,6 +104,7 @@ def test_mgrit_matches_oracle(case):
                    restrict_space=[transfer(l, l + 1) for l in range(L - 1)] + [None],
                    prolong_space=[transfer(l + 1, l) for l in range(L - 1)] + [None])
     hist = m.run(U0, cycles)
+    worst = [0.0, 0.0, 0.0, 0.0]
     for k in range(cycles + 1):
         if k > 0:
             kk, norms = g.cycle(1)
@@ -94,8 +113,21 @@ def test_mgrit_matches_oracle(case):
         got = out.cpu().numpy().view(np.complex128).reshape(Nc + 1, 3, -1)
         for i in range(Nc + 1):
             ref = to_packed(sph[0], hist[k][i])
+            if not mixed:
+                for f in range(3):
+                    assert _rel(got[i, f], ref[f]) < 1e-10, (k, i, f, _rel(got[i, f], ref[f]))
+                continue
+            full_g, full_r = got[i, 0].copy(), ref[0].copy()
+            full_g[0] += np.sqrt(2.0) * plans[0].phibar        # Phi_bar on P_0^0 = 1/sqrt(2)
+            full_r[0] += np.sqrt(2.0) * plans[0].phibar
+            worst[0] = max(worst[0], _rel(full_g, full_r))
             for f in range(3):
-                assert _rel(got[i, f], ref[f]) < 1e-10, (k, i, f, _rel(got[i, f], ref[f]))
+                if np.linalg.norm(ref[f]) > 0.0:
+                    worst[1 + f] = max(worst[1 + f], _rel(got[i, f], ref[f]))
+    if mixed:
+        # full height: the stated bound 1e-6; Phi' and xi 1e-5; delta starts at zero and stays
+        # far below xi, so the same absolute FP32 rounding is a larger fraction of it: 1e-4
+        assert worst[0] < 1e-6 and worst[1] < 1e-5 and worst[2] < 1e-5 and worst[3] < 1e-4, worst
     g.close()
     for p in plans:
         p.close()
