@@ -570,6 +570,10 @@ __device__ __forceinline__ void ring_forward_regs(float2 (&a)[EL], int M, const 
     }
 }
 
+// stride of the per-ring staging regions: n float2 rounded up to 1 mod 16, so that the rings
+// of a block (up to 16) fall on different shared-memory banks at the same offset
+__host__ __device__ constexpr int ring_stride(int n) { return n + (17 - n % 16) % 16; }
+
 __device__ __forceinline__ void cp_async8(void* dst, const void* src, bool pred) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
                  "l"(src), "r"(pred ? 8 : 0)
@@ -585,8 +589,8 @@ __global__ void __launch_bounds__(128, 3) k_ring_nl_lg(const float2* __restrict_
     float2* twN = reinterpret_cast<float2*>(smem_raw);     // 2H entries e^{-2 pi i k / (2H)}
     float2* tws = twN + 2 * H;                              // pass tables
     float2* fbuf = tws + RingTw<T>::n;                      // [G][HB]
-    float2* reg = fbuf + G * HB;                            // [G][5][M+1]
-    const int Mp = M + 1;
+    float2* reg = fbuf + G * HB;                            // [G][5][M+1], ring stride RS
+    const int Mp = M + 1, RS = ring_stride(5 * Mp);
     const int s0 = blockIdx.x * G;
     const int j = blockIdx.y;
     const int64_t C4 = 4 * (int64_t)S, C5 = 5 * (int64_t)S;
@@ -595,7 +599,7 @@ __global__ void __launch_bounds__(128, 3) k_ring_nl_lg(const float2* __restrict_
         const int g = q % G, fm = q / G;
         const int m = fm % Mp, f = fm / Mp;
         const bool ok = s0 + g < S;
-        cp_async8(&reg[(g * 5 + f) * Mp + m], ok ? (const void*)&Fin[((int64_t)m * nlat + j) * C4 + (int64_t)f * S + s0 + g]
+        cp_async8(&reg[g * RS + f * Mp + m], ok ? (const void*)&Fin[((int64_t)m * nlat + j) * C4 + (int64_t)f * S + s0 + g]
                                                   : (const void*)Fin,
                   ok);
     }
@@ -605,7 +609,7 @@ __global__ void __launch_bounds__(128, 3) k_ring_nl_lg(const float2* __restrict_
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     const int t = threadIdx.x & (T - 1), g = threadIdx.x / T;
-    float2* R = reg + g * 5 * Mp;
+    float2* R = reg + g * RS;
     float2* buf = fbuf + g * HB;
     const double muj = mu[j];
     const float ic2 = (float)(1.0 / ((1.0 - muj) * (1.0 + muj)));
@@ -657,7 +661,7 @@ __global__ void __launch_bounds__(128, 3) k_ring_nl_lg(const float2* __restrict_
         const int gg = q % G, fm = q / G;
         const int m = fm % Mp, f = fm / Mp;
         const int slot = f == 0 ? 1 : (f == 1 ? 4 : (f == 2 ? 0 : (f == 3 ? 3 : 2)));
-        if (s0 + gg < S) Fout[((int64_t)m * nlat + j) * C5 + (int64_t)f * S + s0 + gg] = reg[(gg * 5 + slot) * Mp + m];
+        if (s0 + gg < S) Fout[((int64_t)m * nlat + j) * C5 + (int64_t)f * S + s0 + gg] = reg[gg * RS + slot * Mp + m];
     }
 }
 
@@ -675,14 +679,14 @@ __global__ void __launch_bounds__(128) k_ring_inv_lg(const float2* __restrict__ 
     float2* twN = reinterpret_cast<float2*>(smem_raw);
     float2* tws = twN + 2 * H;
     float2* fbuf = tws + RingTw<T>::n;                      // [G][HB]
-    float2* reg = fbuf + G * HB;                            // [G][M+1]
-    const int Mp = M + 1;
+    float2* reg = fbuf + G * HB;                            // [G][M+1], ring stride RS
+    const int Mp = M + 1, RS = ring_stride(Mp);
     const int c0 = blockIdx.x * G;
     const int j = blockIdx.y;
     for (int q = threadIdx.x; q < Mp * G; q += blockDim.x) {
         const int g = q % G, m = q / G;
         const bool ok = c0 + g < C;
-        cp_async8(&reg[g * Mp + m], ok ? (const void*)&F[((int64_t)m * nlat + j) * C + c0 + g] : (const void*)F, ok);
+        cp_async8(&reg[g * RS + m], ok ? (const void*)&F[((int64_t)m * nlat + j) * C + c0 + g] : (const void*)F, ok);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
     for (int k = threadIdx.x; k < 2 * H; k += blockDim.x) twN[k] = twg[k];
@@ -691,7 +695,7 @@ __global__ void __launch_bounds__(128) k_ring_inv_lg(const float2* __restrict__ 
     __syncthreads();
     const int t = threadIdx.x & (T - 1), g = threadIdx.x / T;
     float2 a[EL];
-    ring_inverse_regs<T>(reg + g * Mp, M, twN, tws, fbuf + g * HB, t, a);
+    ring_inverse_regs<T>(reg + g * RS, M, twN, tws, fbuf + g * HB, t, a);
     if (c0 + g < C) {
         float2* row = reinterpret_cast<float2*>(grid + ((int64_t)(c0 + g) * nlat + j) * (2 * H));
         constexpr int RL = (T == 16) ? 4 : 2;               // radix of the last inverse pass
@@ -711,8 +715,8 @@ __global__ void __launch_bounds__(128) k_ring_fwd_lg(const float* __restrict__ g
     float2* twN = reinterpret_cast<float2*>(smem_raw);
     float2* tws = twN + 2 * H;
     float2* fbuf = tws + RingTw<T>::n;
-    float2* reg = fbuf + G * HB;                            // [G][M+1]
-    const int Mp = M + 1;
+    float2* reg = fbuf + G * HB;                            // [G][M+1], ring stride RS
+    const int Mp = M + 1, RS = ring_stride(Mp);
     const int c0 = blockIdx.x * G;
     const int j = blockIdx.y;
     const int t = threadIdx.x & (T - 1), g = threadIdx.x / T;
@@ -730,18 +734,18 @@ __global__ void __launch_bounds__(128) k_ring_fwd_lg(const float* __restrict__ g
     fill_ring_tw<T>(tws, twg);
     __syncthreads();
     const float scale = (float)(w[j] / (double)(2 * H));
-    ring_forward_regs<T>(a, M, twN, tws, fbuf + g * HB, t, scale, reg + g * Mp);
+    ring_forward_regs<T>(a, M, twN, tws, fbuf + g * HB, t, scale, reg + g * RS);
     __syncthreads();
     for (int q = threadIdx.x; q < Mp * G; q += blockDim.x) {
         const int gg = q % G, m = q / G;
-        if (c0 + gg < C) F[((int64_t)m * nlat + j) * C + c0 + gg] = reg[gg * Mp + m];
+        if (c0 + gg < C) F[((int64_t)m * nlat + j) * C + c0 + gg] = reg[gg * RS + m];
     }
 }
 
 template <int T>
 static swe_status ring_plain_lg(const swe_plan* p, const void* in, void* out, int C, bool inverse, cudaStream_t st) {
     constexpr int H = EL * T, G = 128 / T, HB = H + H / 16 + 1;
-    const size_t sm = (2 * (size_t)H + RingTw<T>::n + (size_t)G * HB + (size_t)G * (p->M + 1)) * sizeof(float2);
+    const size_t sm = (2 * (size_t)H + RingTw<T>::n + (size_t)G * HB + (size_t)G * ring_stride(p->M + 1)) * sizeof(float2);
     dim3 g((C + G - 1) / G, p->nlat);
     if (inverse) {
         SWE_CHECK_CUDA(cudaFuncSetAttribute(k_ring_inv_lg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -970,7 +974,8 @@ swe_status ring_run(const swe_plan* p, int id, int G, const void* Fin, void* Fou
 template <int T>
 static swe_status ring_lg_launch(const swe_plan* p, const void* Fin, void* Fout, int S, cudaStream_t st) {
     constexpr int H = EL * T, G = 128 / T, HB = H + H / 16 + 1;
-    const size_t sm = (2 * (size_t)H + RingTw<T>::n + (size_t)G * HB + (size_t)G * 5 * (p->M + 1)) * sizeof(float2);
+    const size_t sm =
+        (2 * (size_t)H + RingTw<T>::n + (size_t)G * HB + (size_t)G * ring_stride(5 * (p->M + 1))) * sizeof(float2);
     SWE_CHECK_CUDA(cudaFuncSetAttribute(k_ring_nl_lg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     dim3 g((S + G - 1) / G, p->nlat);
     k_ring_nl_lg<T><<<g, 128, sm, st>>>((const float2*)Fin, (float2*)Fout, p->M, p->nlat, S, p->twf, p->mu, p->w);
