@@ -45,7 +45,7 @@ constexpr int NPLANE = 3;        // bf16 split terms
 constexpr int NTERMS = 6;        // partial products kept
 constexpr uint32_t TMEM_COLS = 512;
 constexpr unsigned long long WAIT_LIMIT = 1ull << 22;   // bounded polling (about a second)
-constexpr int NR_INV = 2;        // raw data-operand prefetch depth, inverse (FP64 rows)
+constexpr int NR_INV = 4;        // raw data-operand prefetch depth, inverse (FP32 rows)
 constexpr int NR_FWD = 4;        // raw data-operand prefetch depth, forward (FP32 rows)
 constexpr int NT_MAX = 224;      // largest N tile (two parity accumulators + a 32-column read fit in 512)
 constexpr int NB_MAX = 4;        // table-tile ring depth (set per plan from the shared-memory budget)
@@ -76,10 +76,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 // per-thread asynchronous global -> shared copies (zero-filled when !pred)
 __device__ __forceinline__ void cp_async4(void* dst, const void* src, bool pred) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(pred ? 4 : 0)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool pred) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(pred ? 8 : 0)
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
@@ -329,7 +325,7 @@ __device__ __forceinline__ bool ws_warp_wait(WS* ws, uint64_t* bar, uint32_t par
 // ----------------------------------------------------------------------------- inverse
 // grid: (ceil(ncol/128), M+1, n-tiles over j).  Table Binv: for each m, chunk q, parity,
 // N-tile: a [nt x 16] bf16 tile x 3 planes, contiguous (offsets from inv_off[m]).
-__global__ void __launch_bounds__(NTH, 1) k_leg_inv_tc(const double* __restrict__ X, float* __restrict__ F,
+__global__ void __launch_bounds__(NTH, 1) k_leg_inv_tc(const float* __restrict__ X, float* __restrict__ F,
                                                        const unsigned char* __restrict__ Binv,
                                                        const long long* __restrict__ inv_off,
                                                        const int* __restrict__ inv_nq, TCShape sh, int NB, int* err) {
@@ -341,7 +337,7 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_inv_tc(const double* __restrict_
     const uint32_t b_stage = 2 * NPLANE * b_plane;
     unsigned char* sA[2] = {smem, smem + a_stage};
     unsigned char* sB0 = smem + 2 * a_stage;
-    double* raw = reinterpret_cast<double*>(sB0 + (size_t)NB * b_stage);   // [NR][2][KC][BM]
+    float* raw = reinterpret_cast<float*>(sB0 + (size_t)NB * b_stage);   // [NR][2][KC][BM]
     WS* ws = reinterpret_cast<WS*>(raw + NR_INV * 2 * KC * BM);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -361,7 +357,7 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_inv_tc(const double* __restrict_
     // column and quarter
     auto prefetch = [&](int qq) {
         if (qq < nq) {
-            double* r = raw + (qq % NR_INV) * (2 * KC * BM);
+            float* r = raw + (qq % NR_INV) * (2 * KC * BM);
 #pragma unroll
             for (int par = 0; par < 2; ++par)
 #pragma unroll
@@ -369,7 +365,7 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_inv_tc(const double* __restrict_
                     const int kk = KQ * sub + i;
                     const int rr = par + 2 * (KC * qq + kk);
                     const bool pr = cin && rr < Kx;
-                    cp_async8(&r[(par * KC + kk) * BM + col], pr ? (const void*)&X[(xrow0 + rr) * sh.ncol + c] : X,
+                    cp_async4(&r[(par * KC + kk) * BM + col], pr ? (const void*)&X[(xrow0 + rr) * sh.ncol + c] : X,
                               pr);
                 }
         }
@@ -392,12 +388,12 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_inv_tc(const double* __restrict_
             prefetch(q + NR_INV - 1);
             cp_async_wait<NR_INV - 1>();
             if (q >= 2 && !ws_warp_wait(ws, &ws->a_empty[q & 1], ((q - 2) >> 1) & 1, lane)) break;
-            const double* r = raw + (q % NR_INV) * (2 * KC * BM);
+            const float* r = raw + (q % NR_INV) * (2 * KC * BM);
 #pragma unroll
             for (int par = 0; par < 2; ++par) {
                 float v[KQ];
 #pragma unroll
-                for (int i = 0; i < KQ; ++i) v[i] = d2f_fast(r[(par * KC + KQ * sub + i) * BM + col]);
+                for (int i = 0; i < KQ; ++i) v[i] = r[(par * KC + KQ * sub + i) * BM + col];
                 store_quad_planes(sA[q & 1] + par * NPLANE * a_plane, a_plane, col, KQ * sub, v);
             }
             ws_planes_ready(ws, q, lane);
@@ -438,7 +434,7 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_inv_tc(const double* __restrict_
 // grid: (ceil(ncol/128), M+1, max n-tiles over k).  Table Bfwd: for each m, j-chunk q,
 // n-tile z, parity: a [nt_m x 16] tile x 3 planes (rows k = degree index within the
 // parity); nt_m = fwd_nt[m] follows the number of degrees of m (multiple of 16).
-__global__ void __launch_bounds__(NTH, 1) k_leg_fwd_tc(const float* __restrict__ F, double* __restrict__ Y,
+__global__ void __launch_bounds__(NTH, 1) k_leg_fwd_tc(const float* __restrict__ F, float* __restrict__ Y,
                                                        const unsigned char* __restrict__ Bfwd,
                                                        const long long* __restrict__ fwd_off,
                                                        const int* __restrict__ fwd_ntiles,
@@ -539,8 +535,8 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_fwd_tc(const float* __restrict__
                         const int k = kt0 + k0 + i;
                         const int r0 = 2 * k, r1 = 2 * k + 1;        // extended-row offsets of parities 0 / 1
                         if (k0 + i < nt) {
-                            if (r0 < Kx) Y[(yrow0 + r0) * sh.ncol + c] = f2d_fast(d0[i]);
-                            if (r1 < Kx) Y[(yrow0 + r1) * sh.ncol + c] = f2d_fast(d1[i]);
+                            if (r0 < Kx) Y[(yrow0 + r0) * sh.ncol + c] = d0[i];
+                            if (r1 < Kx) Y[(yrow0 + r1) * sh.ncol + c] = d1[i];
                         }
                     }
                 }
@@ -717,14 +713,14 @@ swe_status split_tables_build(swe_plan* p) {
     k_build_fwd_table<<<dim3(256, M + 1), 256>>>(p->P, t->fwd, t->fwd_off, t->fwd_ntiles, t->fwd_nt, M, p->nlat2);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    t->nb_inv = tc_nb(t->nt_inv, 2 * KC * BM * sizeof(double), NR_INV);
+    t->nb_inv = tc_nb(t->nt_inv, 2 * KC * BM * sizeof(float), NR_INV);
     t->nb_fwd = tc_nb(t->nt_fwd, 2 * KC * BM * sizeof(float), NR_FWD);
     if (t->nb_inv == 0 || t->nb_fwd == 0) {
         p->Pbf = t;
         swe_set_error("split tables: shared-memory footprint of the tensor-core kernels exceeds 227 KB");
         return SWE_EINVAL;
     }
-    t->smem_inv = tc_smem(t->nt_inv, 2 * KC * BM * sizeof(double), NR_INV, t->nb_inv);
+    t->smem_inv = tc_smem(t->nt_inv, 2 * KC * BM * sizeof(float), NR_INV, t->nb_inv);
     t->smem_fwd = tc_smem(t->nt_fwd, 2 * KC * BM * sizeof(float), NR_FWD, t->nb_fwd);
     // at least ~116 KB of shared memory so that a single CTA (holding all 512 TMEM columns) runs per SM
     const size_t one_per_sm = 116 * 1024;
@@ -752,7 +748,7 @@ void split_tables_free(swe_plan* p) {
     p->Pbf = nullptr;
 }
 
-swe_status leg_inverse_split(const swe_plan* p, const double2* X, float2* F, int C, cudaStream_t st) {
+swe_status leg_inverse_split(const swe_plan* p, const float2* X, float2* F, int C, cudaStream_t st) {
     const SplitTables* t = (const SplitTables*)p->Pbf;
     if (!t) {
         swe_set_error("split-precision tables missing");
@@ -761,18 +757,18 @@ swe_status leg_inverse_split(const swe_plan* p, const double2* X, float2* F, int
     TCShape sh{p->M, p->nlat, p->nlat2, 2 * C, t->nt_inv};
     dim3 grid((sh.ncol + BM - 1) / BM, p->M + 1, t->ntiles_inv);
     const double fl = (double)C * p->nlat * (p->M + 1.0) * (p->M + 2.0);
-    const double by = 16.0 * C * p->ncx + 8.0 * C * (p->M + 1.0) * p->nlat;
+    const double by = 8.0 * C * p->ncx + 8.0 * C * (p->M + 1.0) * p->nlat;
     // the dynamic shared-memory limit is a per-function attribute shared by all plans: set it per launch
     SWE_CHECK_CUDA(cudaFuncSetAttribute(k_leg_inv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_inv));
     ProfToken tk = prof_begin("leg_inv_tc", st, fl, by);
-    k_leg_inv_tc<<<grid, NTH, t->smem_inv, st>>>((const double*)X, (float*)F, t->inv, t->inv_off, t->inv_nq, sh,
+    k_leg_inv_tc<<<grid, NTH, t->smem_inv, st>>>((const float*)X, (float*)F, t->inv, t->inv_off, t->inv_nq, sh,
                                                 t->nb_inv, t->err);
     prof_end(tk, st);
     SWE_CHECK_LAUNCH("k_leg_inv_tc");
     return SWE_OK;
 }
 
-swe_status leg_forward_split(const swe_plan* p, const float2* F, double2* Y, int C, cudaStream_t st) {
+swe_status leg_forward_split(const swe_plan* p, const float2* F, float2* Y, int C, cudaStream_t st) {
     const SplitTables* t = (const SplitTables*)p->Pbf;
     if (!t) {
         swe_set_error("split-precision tables missing");
@@ -781,10 +777,10 @@ swe_status leg_forward_split(const swe_plan* p, const float2* F, double2* Y, int
     TCShape sh{p->M, p->nlat, p->nlat2, 2 * C, t->nt_fwd};
     dim3 grid((sh.ncol + BM - 1) / BM, p->M + 1, t->nz_fwd);
     const double fl = (double)C * p->nlat * (p->M + 1.0) * (p->M + 2.0);
-    const double by = 8.0 * C * (p->M + 1.0) * p->nlat + 16.0 * C * p->ncx;
+    const double by = 8.0 * C * (p->M + 1.0) * p->nlat + 8.0 * C * p->ncx;
     SWE_CHECK_CUDA(cudaFuncSetAttribute(k_leg_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_fwd));
     ProfToken tk = prof_begin("leg_fwd_tc", st, fl, by);
-    k_leg_fwd_tc<<<grid, NTH, t->smem_fwd, st>>>((const float*)F, (double*)Y, t->fwd, t->fwd_off, t->fwd_ntiles,
+    k_leg_fwd_tc<<<grid, NTH, t->smem_fwd, st>>>((const float*)F, (float*)Y, t->fwd, t->fwd_off, t->fwd_ntiles,
                                                 t->fwd_nt, sh, t->nb_fwd, t->err);
     prof_end(tk, st);
     SWE_CHECK_LAUNCH("k_leg_fwd_tc");

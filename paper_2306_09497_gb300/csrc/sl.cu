@@ -31,7 +31,14 @@ struct SV {   // SoA spectral state view
 // Transform operands, rows (m, n <= M+1), columns f*S + s.
 //   full = 1: f = 0..2 X = U + h L U (h = dt/2), 3 Phi', 4 delta, 5 U_cos, 6 V_cos   (7 fields)
 //   full = 0: f = 0 Phi', 1 delta, 2 U_cos, 3 V_cos                                 (4 fields)
-__global__ void k_sl_operands(SV U, double2* __restrict__ X, const int* __restrict__ row_m, int64_t ncx, int nf,
+// transform operands are complex128 on FP64 plans, complex64 on split-precision plans
+__device__ __forceinline__ void put(double2* p, double2 v) { *p = v; }
+__device__ __forceinline__ void put(float2* p, double2 v) { *p = d2f2(v); }
+__device__ __forceinline__ double2 get2(const double2* p) { return *p; }
+__device__ __forceinline__ double2 get2(const float2* p) { return f2d2(*p); }
+
+template <typename TX>
+__global__ void k_sl_operands(SV U, TX* __restrict__ X, const int* __restrict__ row_m, int64_t ncx, int nf,
                               int full, double h, double ia2, double omega, double phibar,
                               const double* __restrict__ rc) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -52,13 +59,13 @@ __global__ void k_sl_operands(SV U, double2* __restrict__ X, const int* __restri
     Uh.y = fma(ucm, xim.y, fma(-ucp, xip.y, uc0 * de.x));
     Vh.x = fma(-ucm, dem.x, fma(ucp, dep.x, -uc0 * xi.y));
     Vh.y = fma(-ucm, dem.y, fma(ucp, dep.y, uc0 * xi.x));
-    double2* row = X + rx * (int64_t)nf * S + s;
+    TX* row = X + rx * (int64_t)nf * S + s;
     if (n > M) {
         // the extended row n = M+1 carries only the velocity operands; every other field is
         // truncated at M (the Coriolis coupling of L U would otherwise leak into degree M+1)
-        for (int f = 0; f < nf - 2; ++f) row[(int64_t)f * S] = czero();
-        row[(int64_t)(nf - 2) * S] = Uh;
-        row[(int64_t)(nf - 1) * S] = Vh;
+        for (int f = 0; f < nf - 2; ++f) put(row + (int64_t)f * S, czero());
+        put(row + (int64_t)(nf - 2) * S, Uh);
+        put(row + (int64_t)(nf - 1) * S, Vh);
         return;
     }
     if (full) {
@@ -69,18 +76,18 @@ __global__ void k_sl_operands(SV U, double2* __restrict__ X, const int* __restri
                                         -fma(p, dem.y, fma(q, dep.y, -r * xi.x)));
         const double2 L2 = make_double2(fma(lap, ph.x, fma(p, xim.x, fma(q, xip.x, -r * de.y))),
                                         fma(lap, ph.y, fma(p, xim.y, fma(q, xip.y, r * de.x))));
-        row[0] = make_double2(fma(h, L0.x, ph.x), fma(h, L0.y, ph.y));
-        row[S] = make_double2(fma(h, L1.x, xi.x), fma(h, L1.y, xi.y));
-        row[2 * S] = make_double2(fma(h, L2.x, de.x), fma(h, L2.y, de.y));
-        row[3 * S] = ph;
-        row[4 * S] = de;
-        row[5 * S] = Uh;
-        row[6 * S] = Vh;
+        put(row, make_double2(fma(h, L0.x, ph.x), fma(h, L0.y, ph.y)));
+        put(row + S, make_double2(fma(h, L1.x, xi.x), fma(h, L1.y, xi.y)));
+        put(row + 2 * S, make_double2(fma(h, L2.x, de.x), fma(h, L2.y, de.y)));
+        put(row + 3 * S, ph);
+        put(row + 4 * S, de);
+        put(row + 5 * S, Uh);
+        put(row + 6 * S, Vh);
     } else {
-        row[0] = ph;
-        row[S] = de;
-        row[2 * S] = Uh;
-        row[3 * S] = Vh;
+        put(row, ph);
+        put(row + S, de);
+        put(row + 2 * S, Uh);
+        put(row + 3 * S, Vh);
     }
 }
 
@@ -263,7 +270,8 @@ __global__ void __launch_bounds__(128) k_sl_depart(const T* __restrict__ G, cons
     }
 }
 
-__global__ void k_sl_unpack(const double2* __restrict__ Y, double2* __restrict__ R, const int* __restrict__ srow_m,
+template <typename TY>
+__global__ void k_sl_unpack(const TY* __restrict__ Y, double2* __restrict__ R, const int* __restrict__ srow_m,
                             int M, int64_t nc, int S) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= nc * S) return;
@@ -271,9 +279,9 @@ __global__ void k_sl_unpack(const double2* __restrict__ Y, double2* __restrict__
     const int64_t r = t / S;
     const int m = srow_m[r];
     const int n = m + (int)(r - st_off(m, M));
-    const double2* y = Y + (ex_off(m, M) + (n - m)) * 3 * (int64_t)S + s;
+    const TY* y = Y + (ex_off(m, M) + (n - m)) * 3 * (int64_t)S + s;
 #pragma unroll
-    for (int f = 0; f < 3; ++f) R[((int64_t)f * nc + r) * S + s] = y[(int64_t)f * S];
+    for (int f = 0; f < 3; ++f) R[((int64_t)f * nc + r) * S + s] = get2(y + (int64_t)f * S);
 }
 
 template <typename T>
@@ -384,8 +392,12 @@ swe_status sl_step(swe_plan* p, double dt, double nu, int q, const double2* Upre
     SV v{U, p->nc, S, p->M};
     {
         ProfToken tk_ = prof_begin("sl_operands", st, 0.0, 16.0 * S * (3.0 * p->nc + 7.0 * p->ncx));
-        k_sl_operands<<<nb(p->ncx * S), 256, 0, st>>>(v, b.X, p->row_m, p->ncx, 7, 1, h, 1.0 / (p->a * p->a),
-                                                      p->omega, p->phibar, p->rc);
+        if (f64)
+            k_sl_operands<<<nb(p->ncx * S), 256, 0, st>>>(v, b.X, p->row_m, p->ncx, 7, 1, h, 1.0 / (p->a * p->a),
+                                                          p->omega, p->phibar, p->rc);
+        else
+            k_sl_operands<<<nb(p->ncx * S), 256, 0, st>>>(v, reinterpret_cast<float2*>(b.X), p->row_m, p->ncx, 7, 1,
+                                                          h, 1.0 / (p->a * p->a), p->omega, p->phibar, p->rc);
         prof_end(tk_, st);
     }
     SWE_CHECK_LAUNCH("k_sl_operands");
@@ -403,8 +415,12 @@ swe_status sl_step(swe_plan* p, double dt, double nu, int q, const double2* Upre
     } else if (Uprev) {
         // grid fields (Phi', delta, U_cos, V_cos) of the previous state -> previous velocity / N_R
         SV vp{Uprev, p->nc, S, p->M};
-        k_sl_operands<<<nb(p->ncx * S), 256, 0, st>>>(vp, b.X, p->row_m, p->ncx, 4, 0, h, 1.0 / (p->a * p->a), p->omega,
-                                                      p->phibar, p->rc);
+        if (f64)
+            k_sl_operands<<<nb(p->ncx * S), 256, 0, st>>>(vp, b.X, p->row_m, p->ncx, 4, 0, h, 1.0 / (p->a * p->a),
+                                                          p->omega, p->phibar, p->rc);
+        else
+            k_sl_operands<<<nb(p->ncx * S), 256, 0, st>>>(vp, reinterpret_cast<float2*>(b.X), p->row_m, p->ncx, 4,
+                                                          0, h, 1.0 / (p->a * p->a), p->omega, p->phibar, p->rc);
         SWE_CHECK_LAUNCH("k_sl_operands(prev)");
         SWE_CHECK(leg_inverse(p, b.X, b.Fq, 4 * S, st));
         SWE_CHECK(ring_inverse(p, b.Fq, b.Gp, 4 * S, st));
@@ -445,7 +461,11 @@ swe_status sl_step(swe_plan* p, double dt, double nu, int q, const double2* Upre
     SWE_CHECK(leg_forward(p, b.Fq, b.Y, 3 * S, st));
     {
         ProfToken tk_ = prof_begin("sl_unpack", st, 0.0, 16.0 * 6.0 * p->nc * S);
-        k_sl_unpack<<<nb(p->nc * S), 256, 0, st>>>(b.Y, b.Rs, p->srow_m, p->M, p->nc, S);
+        if (f64)
+            k_sl_unpack<<<nb(p->nc * S), 256, 0, st>>>(b.Y, b.Rs, p->srow_m, p->M, p->nc, S);
+        else
+            k_sl_unpack<<<nb(p->nc * S), 256, 0, st>>>(reinterpret_cast<const float2*>(b.Y), b.Rs, p->srow_m, p->M,
+                                                       p->nc, S);
         prof_end(tk_, st);
     }
     SWE_CHECK_LAUNCH("k_sl_unpack");

@@ -96,6 +96,28 @@ __global__ void k_pack(const double2* __restrict__ spec, double2* __restrict__ X
     X[t] = (n <= M) ? spec[(int64_t)b * nc + st_off(m, M) + (n - m)] : czero();
 }
 
+__global__ void k_pack_f32(const double2* __restrict__ spec, float2* __restrict__ X, const int* __restrict__ row_m,
+                           int M, int64_t nc, int64_t ncx, int B) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= ncx * B) return;
+    int b = (int)(t % B);
+    int64_t rx = t / B;
+    int m = row_m[rx];
+    int n = m + (int)(rx - ex_off(m, M));
+    X[t] = (n <= M) ? d2f2(spec[(int64_t)b * nc + st_off(m, M) + (n - m)]) : make_float2(0.f, 0.f);
+}
+
+__global__ void k_unpack_f32(const float2* __restrict__ Y, double2* __restrict__ spec, const int* __restrict__ srow_m,
+                             int M, int64_t nc, int B) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nc * B) return;
+    int64_t r = t % nc;
+    int b = (int)(t / nc);
+    int m = srow_m[r];
+    int n = m + (int)(r - st_off(m, M));
+    spec[t] = f2d2(Y[(ex_off(m, M) + (n - m)) * B + b]);
+}
+
 __global__ void k_unpack(const double2* __restrict__ Y, double2* __restrict__ spec, const int* __restrict__ srow_m,
                          int M, int64_t nc, int B) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -491,7 +513,7 @@ struct StateViewF {
     }
 };
 
-__global__ void k_nl_pre_f32(StateViewF U, double2* __restrict__ X, const int* __restrict__ row_m, int64_t ncx,
+__global__ void k_nl_pre_f32(StateViewF U, float2* __restrict__ X, const int* __restrict__ row_m, int64_t ncx,
                              const float* __restrict__ rcf) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int S = U.S, M = U.M;
@@ -510,18 +532,18 @@ __global__ void k_nl_pre_f32(StateViewF U, double2* __restrict__ X, const int* _
     Uh.y = fmaf(ucm, xim.y, fmaf(-ucp, xip.y, uc0 * de0.x));
     Vh.x = fmaf(-ucm, dem.x, fmaf(ucp, dep.x, -uc0 * xi0.y));
     Vh.y = fmaf(-ucm, dem.y, fmaf(ucp, dep.y, uc0 * xi0.x));
-    double2* row = X + rx * 4 * (int64_t)S + s;
-    row[0] = f2d2(U.get(0, m, n, s));
-    row[S] = f2d2(xi0);
-    row[2 * S] = f2d2(Uh);
-    row[3 * S] = f2d2(Vh);
+    float2* row = X + rx * 4 * (int64_t)S + s;
+    row[0] = U.get(0, m, n, s);
+    row[S] = xi0;
+    row[2 * S] = Uh;
+    row[3 * S] = Vh;
 }
 
 __device__ __forceinline__ void flag_nonfinite_f(int* flags, float2 v) {
     if (!isfinite(v.x) || !isfinite(v.y)) atomicOr(flags, 1);
 }
 
-__global__ void k_nl_post_f32(const double2* __restrict__ Y, int mode, float dt, const double2* __restrict__ in0,
+__global__ void k_nl_post_f32(const float2* __restrict__ Y, int mode, float dt, const double2* __restrict__ in0,
                               const double2* __restrict__ in1, double2* __restrict__ out0,
                               double2* __restrict__ out1, const int* __restrict__ srow_m, int M, int64_t nc, int S,
                               float ia, const float* __restrict__ rcf, int* flags) {
@@ -533,13 +555,13 @@ __global__ void k_nl_post_f32(const double2* __restrict__ Y, int mode, float dt,
     int n = m + (int)(r - st_off(m, M));
     const int64_t rx = ex_off(m, M) + (n - m);
     const int64_t C5 = 5 * (int64_t)S;
-    const double2* y0 = Y + rx * C5 + s;
-    const double2* yp = y0 + C5;
+    const float2* y0 = Y + rx * C5 + s;
+    const float2* yp = y0 + C5;
     const bool hm = (n - 1 >= m);
-    const double2* ym = y0 - C5;
-    const float2 A1 = d2f2(y0[0]), B1 = d2f2(y0[S]), A2 = d2f2(y0[2 * S]), KE = d2f2(y0[4 * S]);
-    const float2 A1p = d2f2(yp[0]), B1p = d2f2(yp[S]), B2p = d2f2(yp[3 * S]);
-    const float2 A1m = hm ? d2f2(ym[0]) : fz(), B1m = hm ? d2f2(ym[S]) : fz(), B2m = hm ? d2f2(ym[3 * S]) : fz();
+    const float2* ym = y0 - C5;
+    const float2 A1 = y0[0], B1 = y0[S], A2 = y0[2 * S], KE = y0[4 * S];
+    const float2 A1p = yp[0], B1p = yp[S], B2p = yp[3 * S];
+    const float2 A1m = hm ? ym[0] : fz(), B1m = hm ? ym[S] : fz(), B2m = hm ? ym[3 * S] : fz();
     const float* c = rcf + rx * RC_NUM;
     const float cp = c[RC_DCP], cm = c[RC_DCM], ma = (float)m * ia;
     float2 N[3];
@@ -906,24 +928,33 @@ swe_status k_soa_to_aos(const swe_plan* p, const double2* in, double2* out, int 
     return SWE_OK;
 }
 swe_status k_pack_scalar(const swe_plan* p, const double2* spec, double2* X, int B, cudaStream_t st) {
-    k_pack<<<nblk(p->ncx * B), 256, 0, st>>>(spec, X, p->row_m, p->M, p->nc, p->ncx, B);
+    if (p->prec == SWE_FP64)
+        k_pack<<<nblk(p->ncx * B), 256, 0, st>>>(spec, X, p->row_m, p->M, p->nc, p->ncx, B);
+    else
+        k_pack_f32<<<nblk(p->ncx * B), 256, 0, st>>>(spec, reinterpret_cast<float2*>(X), p->row_m, p->M, p->nc,
+                                                     p->ncx, B);
     SWE_CHECK_LAUNCH("k_pack");
     return SWE_OK;
 }
 swe_status k_unpack_scalar(const swe_plan* p, const double2* Y, double2* spec, int B, cudaStream_t st) {
-    k_unpack<<<nblk(p->nc * B), 256, 0, st>>>(Y, spec, p->srow_m, p->M, p->nc, B);
+    if (p->prec == SWE_FP64)
+        k_unpack<<<nblk(p->nc * B), 256, 0, st>>>(Y, spec, p->srow_m, p->M, p->nc, B);
+    else
+        k_unpack_f32<<<nblk(p->nc * B), 256, 0, st>>>(reinterpret_cast<const float2*>(Y), spec, p->srow_m, p->M,
+                                                      p->nc, B);
     SWE_CHECK_LAUNCH("k_unpack");
     return SWE_OK;
 }
 swe_status k_nl_pre(const swe_plan* p, const double2* Ua, const double2* Ub, double beta, double2* X, int S,
                     cudaStream_t st) {
-    ProfToken tk_ = prof_begin("nl_pre", st, 0.0, 16.0 * S * (3.0 * p->nc * (Ub ? 2.0 : 1.0) + 4.0 * p->ncx));
+    const double xe = (p->prec == SWE_FP64) ? 16.0 : 8.0;   // bytes per operand element
+    ProfToken tk_ = prof_begin("nl_pre", st, 0.0, S * (16.0 * 3.0 * p->nc * (Ub ? 2.0 : 1.0) + xe * 4.0 * p->ncx));
     if (p->prec == SWE_FP64) {
         StateView v{Ua, Ub, beta, p->nc, S, p->M};
         k_nl_pre_kernel<<<nblk(p->ncx * S), 256, 0, st>>>(v, X, p->row_m, p->ncx, p->rc);
     } else {
         StateViewF v{Ua, Ub, (float)beta, p->nc, S, p->M};
-        k_nl_pre_f32<<<nblk(p->ncx * S), 256, 0, st>>>(v, X, p->row_m, p->ncx, p->rcf);
+        k_nl_pre_f32<<<nblk(p->ncx * S), 256, 0, st>>>(v, reinterpret_cast<float2*>(X), p->row_m, p->ncx, p->rcf);
     }
     prof_end(tk_, st);
     SWE_CHECK_LAUNCH("k_nl_pre");
@@ -931,12 +962,14 @@ swe_status k_nl_pre(const swe_plan* p, const double2* Ua, const double2* Ub, dou
 }
 swe_status k_nl_post(const swe_plan* p, const double2* Y, int mode, double dt, const double2* in0, const double2* in1,
                      double2* out0, double2* out1, int S, cudaStream_t st) {
-    ProfToken tk_ = prof_begin("nl_post", st, 0.0, 16.0 * S * (5.0 * p->ncx + 3.0 * p->nc * (in1 ? 4.0 : 3.0)));
+    const double ye = (p->prec == SWE_FP64) ? 16.0 : 8.0;   // bytes per operand element
+    ProfToken tk_ = prof_begin("nl_post", st, 0.0, S * (ye * 5.0 * p->ncx + 16.0 * 3.0 * p->nc * (in1 ? 4.0 : 3.0)));
     if (p->prec == SWE_FP64) {
         k_nl_post_kernel<<<nblk(p->nc * S), 256, 0, st>>>(Y, mode, dt, in0, in1, out0, out1, p->srow_m, p->M, p->nc, S,
                                                           1.0 / p->a, p->rc, p->flags);
     } else {
-        k_nl_post_f32<<<nblk(p->nc * S), 256, 0, st>>>(Y, mode, (float)dt, in0, in1, out0, out1, p->srow_m, p->M,
+        k_nl_post_f32<<<nblk(p->nc * S), 256, 0, st>>>(reinterpret_cast<const float2*>(Y), mode, (float)dt, in0, in1,
+                                                       out0, out1, p->srow_m, p->M,
                                                        p->nc, S, (float)(1.0 / p->a), p->rcf, p->flags);
     }
     prof_end(tk_, st);

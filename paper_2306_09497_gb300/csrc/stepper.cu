@@ -7,17 +7,19 @@ static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 swe_status leg_inverse_f64(const swe_plan* p, const double2* X, double2* F, int C, cudaStream_t st);
 swe_status leg_forward_f64(const swe_plan* p, const double2* F, double2* Y, int C, cudaStream_t st);
-swe_status leg_inverse_split(const swe_plan* p, const double2* X, float2* F, int C, cudaStream_t st);
-swe_status leg_forward_split(const swe_plan* p, const float2* F, double2* Y, int C, cudaStream_t st);
+swe_status leg_inverse_split(const swe_plan* p, const float2* X, float2* F, int C, cudaStream_t st);
+swe_status leg_forward_split(const swe_plan* p, const float2* F, float2* Y, int C, cudaStream_t st);
 
+// The transform operands X (into the inverse contraction) and Y (out of the forward one) hold
+// complex128 on FP64 plans and complex64 on split-precision plans (the same buffers, half used).
 swe_status leg_inverse(const swe_plan* p, const double2* X, void* F, int C, cudaStream_t st) {
     if (p->prec == SWE_FP64) return leg_inverse_f64(p, X, (double2*)F, C, st);
-    return leg_inverse_split(p, X, (float2*)F, C, st);
+    return leg_inverse_split(p, reinterpret_cast<const float2*>(X), (float2*)F, C, st);
 }
 
 swe_status leg_forward(const swe_plan* p, const void* F, double2* Y, int C, cudaStream_t st) {
     if (p->prec == SWE_FP64) return leg_forward_f64(p, (const double2*)F, Y, C, st);
-    return leg_forward_split(p, (const float2*)F, Y, C, st);
+    return leg_forward_split(p, (const float2*)F, reinterpret_cast<float2*>(Y), C, st);
 }
 
 static size_t state_bytes(const swe_plan* p, int S) { return al256(sizeof(double2) * 3 * p->nc * S); }
