@@ -251,11 +251,13 @@ static swe_status solve_coarsest_body(swe_mgrit* g, int l) {
         double2* out = L.u + i * L.per;
         const double2* add = L.g_on ? L.g + i * L.per : nullptr;
         if (L.two_step && i >= 2) {
-            // two-step SL-SI-SETTLS: the state one step earlier is u_{i-2}
+            // two-step SL-SI-SETTLS: the state one step earlier is u_{i-2}.  Its grid velocity
+            // and N_R are exactly the current fields of step i-1, which sl_step keeps in the
+            // workspace (swap): only step 2 transforms u_0 explicitly.
             char* ws;
             SWE_CHECK(plan_workspace(L.plan, sl_bytes(L.plan, 1), &ws));
-            SWE_CHECK(sl_step(L.plan, L.sd.dt, L.sd.visc_nu, L.sd.visc_q, L.u + (i - 2) * L.per, false,
-                              L.u + (i - 1) * L.per, out, 1, ws, false, g->cs));
+            SWE_CHECK(sl_step(L.plan, L.sd.dt, L.sd.visc_nu, L.sd.visc_q, i == 2 ? L.u + (i - 2) * L.per : nullptr,
+                              i > 2, L.u + (i - 1) * L.per, out, 1, ws, true, g->cs));
             if (add) SWE_CHECK(k_axpy(out, add, 1.0, L.per, g->cs));
         } else {
             SWE_CHECK(mg_step_batch(g, l, L.u + (i - 1) * L.per, 1, out, 1, add, 1, 1));
