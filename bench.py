@@ -61,6 +61,9 @@ WORKLOAD_MGRIT = "t255_mgrit3_cf4"
 N0_MG, CF_MG, NU_RELAX = 7296, 4, 0
 VISC_SL = (2, 1.0e7)
 METRIC = "SWE slice-steps/s at T255"
+# DRAM bytes / algorithmic bytes of a kernel, from one ncu capture of that kernel (file under
+# profiles/); valid only while the kernel is unchanged since that capture
+NCU_TRAFFIC_RATIO = {"ring_nl_f32": (0.811, "profiles/ring_nl_lg_t255_s32.md (ncu, 32 slices, scaled per ring)")}
 FP64_PEAK_TFLOPS = 1.25           # nominal FP64 rate of GB300 (profiling recipe table)
 
 
@@ -502,7 +505,12 @@ def roofline(stats):
         ach = by / n / (avg / 1000.0) / 1e9
         roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
-    roof.update({"traffic": None, "avg_launch_ms": avg, "launches_timed": n})
+    traffic = None
+    if name in NCU_TRAFFIC_RATIO and by > 0:
+        ratio, src = NCU_TRAFFIC_RATIO[name]
+        traffic = {"bytes_per_launch": ratio * by / n, "dram_over_algorithmic": ratio, "source": src}
+    roof.update({"traffic": traffic, "algorithmic_bytes_per_launch": by / n if n else None, "avg_launch_ms": avg,
+                 "launches_timed": n})
     tot = sum(x[1] for x in stats.values())
     roof["kernels"] = {k: {"launches": v[0], "avg_ms": v[1] / max(v[0], 1), "share_of_timed": v[1] / tot}
                        for k, v in stats.items()}
