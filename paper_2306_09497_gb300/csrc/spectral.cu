@@ -594,9 +594,9 @@ __global__ void k_nl_post_f32(const float2* __restrict__ Y, int mode, float dt, 
 // The right-hand side kappa alpha L U, the elimination (the FP32 copy of the Thomas
 // factors of k_cn_factor) and the increment are FP32; X = U + increment is one FP64 add.
 // U and X must not alias.  The two Thomas recurrences run as affine scans (as in
-// k_cn_solve_warp): one warp per (m, parity, group of 4 slices); lane = 4 kl + sl, with sl
-// the slice within the group (4 consecutive slices: 64-byte runs) and kl the position in a
-// chunk of 8 consecutive unknowns of the chain.  Passes: forward scan (d' parked in
+// k_cn_solve_warp): one warp per (m, parity, group of 32/KL slices); lane = (32/KL) kl + sl,
+// with sl the slice within the group (KL = 8: 4 consecutive slices, 64-byte runs) and kl the
+// position in a chunk of KL consecutive unknowns of the chain.  Passes: forward scan (d' parked in
 // X[delta]), backward scan (D_delta parked in X[delta], Phi final), xi of the other parity
 // (final), delta (final).
 __device__ __forceinline__ float2 cmf(float2 a, float2 b) {
@@ -605,11 +605,12 @@ __device__ __forceinline__ float2 cmf(float2 a, float2 b) {
 __device__ __forceinline__ float2 shfl_up_f2(float2 v, int d) {
     return make_float2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
 }
-// inclusive scan of the maps x -> A x + B over kl = 0..7 (lane stride 4)
-__device__ __forceinline__ void affine_scan8(float2& A, float2& B, int kl) {
+// inclusive scan of the maps x -> A x + B over kl = 0..KL-1 (lane stride 32/KL)
+template <int KL>
+__device__ __forceinline__ void affine_scan_kl(float2& A, float2& B, int kl) {
 #pragma unroll
-    for (int d = 1; d < 8; d <<= 1) {
-        const float2 Ap = shfl_up_f2(A, 4 * d), Bp = shfl_up_f2(B, 4 * d);
+    for (int d = 1; d < KL; d <<= 1) {
+        const float2 Ap = shfl_up_f2(A, (32 / KL) * d), Bp = shfl_up_f2(B, (32 / KL) * d);
         if (kl >= d) {
             const float2 nb = cmf(A, Bp);
             B = make_float2(nb.x + B.x, nb.y + B.y);
@@ -618,18 +619,21 @@ __device__ __forceinline__ void affine_scan8(float2& A, float2& B, int kl) {
     }
 }
 
+// KL unknowns of a chain per chunk, 32/KL slices per warp (KL = 8 for batches, 32 for S <= 4)
+template <int KL>
 __global__ void __launch_bounds__(128) k_cn_inc_scan_f32(const float2* __restrict__ fac, const double2* __restrict__ U,
                                                          double2* __restrict__ X, int M, int64_t nc, int S,
                                                          float kalpha, float w2, float phibar, float ia2,
                                                          const float* __restrict__ rcf, float vdn, int vq) {
+    constexpr int SL = 32 / KL;                            // slices per warp
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31, sl = lane & 3, kl = lane >> 2;
-    const int SG = (S + 3) >> 2;
+    const int lane = threadIdx.x & 31, sl = lane % SL, kl = lane / SL;
+    const int SG = (S + SL - 1) / SL;
     if (wid >= (int64_t)2 * (M + 1) * SG) return;          // whole warps exit together
     const int g = (int)(wid % SG);
     const int mp = (int)(wid / SG);
     const int m = mp >> 1, par = mp & 1;
-    const int s = 4 * g + sl;
+    const int s = SL * g + sl;
     const bool sok = s < S;
     const int64_t base = st_off(m, M), xbase = ex_off(m, M);
     auto idx = [&](int f, int n) { return ((int64_t)f * nc + base + (n - m)) * S + s; };
@@ -668,7 +672,7 @@ __global__ void __launch_bounds__(128) k_cn_inc_scan_f32(const float2* __restric
     double2 rw;
     // forward elimination: d'_k = (rhs_k - a_k d'_{k-1}) g_k = A_k d'_{k-1} + B_k
     float2 carry = fz();
-    for (int k0 = 0; k0 < K; k0 += 8) {
+    for (int k0 = 0; k0 < K; k0 += KL) {
         const int k = k0 + kl, n = n0 + 2 * k;
         float2 A = fz(), B = fz();
         if (k < K) {
@@ -683,16 +687,16 @@ __global__ void __launch_bounds__(128) k_cn_inc_scan_f32(const float2* __restric
             A = make_float2(-na.x, -na.y);
             B = cmf(rhs, g1);
         }
-        affine_scan8(A, B, kl);
+        affine_scan_kl<KL>(A, B, kl);
         const float2 ca = cmf(A, carry);
         const float2 v = make_float2(ca.x + B.x, ca.y + B.y);
         if (k < K && sok) X[idx(2, n)] = f2d2(v);
-        carry = make_float2(__shfl_sync(0xffffffffu, v.x, 28 + sl), __shfl_sync(0xffffffffu, v.y, 28 + sl));
+        carry = make_float2(__shfl_sync(0xffffffffu, v.x, (KL - 1) * SL + sl), __shfl_sync(0xffffffffu, v.y, (KL - 1) * SL + sl));
     }
     __syncwarp();
     // back substitution from the top: D_k = -c'_k D_{k+1} + d'_k; then Phi (final)
     carry = fz();
-    for (int k0 = 0; k0 < K; k0 += 8) {
+    for (int k0 = 0; k0 < K; k0 += KL) {
         const int k = K - 1 - (k0 + kl), n = n0 + 2 * k;
         float2 A = fz(), B = fz();
         if (k >= 0) {
@@ -701,10 +705,10 @@ __global__ void __launch_bounds__(128) k_cn_inc_scan_f32(const float2* __restric
             A = make_float2(-c2.x, -c2.y);
             B = sok ? d2f2(X[idx(2, n)]) : fz();
         }
-        affine_scan8(A, B, kl);
+        affine_scan_kl<KL>(A, B, kl);
         const float2 ca = cmf(A, carry);
         float2 dn = make_float2(ca.x + B.x, ca.y + B.y);
-        carry = make_float2(__shfl_sync(0xffffffffu, dn.x, 28 + sl), __shfl_sync(0xffffffffu, dn.y, 28 + sl));
+        carry = make_float2(__shfl_sync(0xffffffffu, dn.x, (KL - 1) * SL + sl), __shfl_sync(0xffffffffu, dn.y, (KL - 1) * SL + sl));
         if (k >= 0 && sok) {
             if (n == 0) dn = fz();
             const float2* f = fac + (base + (n - m)) * 8;
@@ -720,7 +724,7 @@ __global__ void __launch_bounds__(128) k_cn_inc_scan_f32(const float2* __restric
     // xi on the other parity: D_xi = [rhs_xi - c p D_delta(n-1) - c q D_delta(n+1)] / d_n (final)
     const int nx0 = m + (par ^ 1);
     const int J = (nx0 <= M) ? (M - nx0) / 2 + 1 : 0;
-    for (int j0 = 0; j0 < J; j0 += 8) {
+    for (int j0 = 0; j0 < J; j0 += KL) {
         const int j = j0 + kl, n = nx0 + 2 * j;
         if (j < J && sok) {
             const float2* f = fac + (base + (n - m)) * 8;
@@ -738,7 +742,7 @@ __global__ void __launch_bounds__(128) k_cn_inc_scan_f32(const float2* __restric
     }
     __syncwarp();
     // delta (final) from the parked D_delta
-    for (int k0 = 0; k0 < K; k0 += 8) {
+    for (int k0 = 0; k0 < K; k0 += KL) {
         const int k = k0 + kl, n = n0 + 2 * k;
         if (k < K && sok) {
             double2 ud_raw;
@@ -1023,8 +1027,9 @@ swe_status k_implicit(swe_plan* p, double alpha, int with_rhs, const double2* in
     const double2* fac;
     const float2* fac32 = nullptr;
     SWE_CHECK(plan_cn_factor(p, alpha, &fac, st, &fac32));
-    if (p->prec != SWE_FP64 && fac32 && S > 4 && in != out) {
-        // split-precision plans, batched: FP32 increment form (right-hand side fused for CN)
+    if (p->prec != SWE_FP64 && fac32 && in != out) {
+        // split-precision plans: FP32 increment form (right-hand side fused for CN); also for
+        // single slices (the serial chains), where it replaces two FP64-bound launches
         const float kap = with_rhs ? 2.0f : 1.0f;
         ProfToken tk = prof_begin("cn_step_f32", st, 0.0, 16.0 * p->nc * (6.0 * S + 8.0));
         const float ka = (float)(kap * alpha), w2 = (float)(2.0 * p->omega), pb = (float)p->phibar;
@@ -1033,10 +1038,15 @@ swe_status k_implicit(swe_plan* p, double alpha, int with_rhs, const double2* in
             // the batch alone fills the GPU with chains: one thread per chain
             k_cn_inc_f32<<<nblk((int64_t)2 * (p->M + 1) * S, 128), 128, 0, st>>>(fac32, in, out, p->M, p->nc, S, ka,
                                                                                 w2, pb, ia2, p->rcf, vdn, visc_q);
-        } else {
+        } else if (S > 4) {
             const int64_t nwarps = (int64_t)2 * (p->M + 1) * ((S + 3) / 4);
-            k_cn_inc_scan_f32<<<nblk(nwarps * 32, 128), 128, 0, st>>>(fac32, in, out, p->M, p->nc, S, ka, w2, pb,
-                                                                       ia2, p->rcf, vdn, visc_q);
+            k_cn_inc_scan_f32<8><<<nblk(nwarps * 32, 128), 128, 0, st>>>(fac32, in, out, p->M, p->nc, S, ka, w2, pb,
+                                                                          ia2, p->rcf, vdn, visc_q);
+        } else {
+            // small batches (serial chains): 32 unknowns of one chain per chunk
+            const int64_t nwarps = (int64_t)2 * (p->M + 1) * S;
+            k_cn_inc_scan_f32<32><<<nblk(nwarps * 32, 128), 128, 0, st>>>(fac32, in, out, p->M, p->nc, S, ka, w2, pb,
+                                                                           ia2, p->rcf, vdn, visc_q);
         }
         prof_end(tk, st);
         SWE_CHECK_LAUNCH("k_cn_inc_f32");
