@@ -67,6 +67,17 @@ NCU_TRAFFIC_RATIO = {"ring_nl_f32": (0.811, "profiles/ring_nl_lg_t255_s32.md (nc
 FP64_PEAK_TFLOPS = 1.25           # nominal FP64 rate of GB300 (profiling recipe table)
 
 
+def slowest_rank(seconds: float, world: int, device=None) -> float:
+    """The slowest rank's time (max over ranks): whole-job throughput of N replicas is the
+    units all ranks processed divided by it."""
+    if world <= 1:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
         os.environ.get("LOCAL_RANK", "0"))
@@ -423,11 +434,7 @@ def measure(args, prec_name, rank, world, local, with_e2e=True):
     swe.prof_enable(False)
     stats = swe.prof_stats()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = slowest_rank(e0.elapsed_time(e1) / args.steps, world, dev)
     res = {"ms": ms, "value": world * fine_steps / (ms / 1000.0), "launches": launches, "stats": stats,
            "clocks": clk, "norms": norms, "fine_steps": fine_steps,
            "problem_steps_per_s": world * (S * NF if args.workload == "parareal" else N0_MG) / (ms / 1000.0)}
@@ -465,11 +472,7 @@ def measure(args, prec_name, rank, world, local, with_e2e=True):
         for _ in range(args.steps):
             e2e_step()
         torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / args.steps
-        if world > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = slowest_rank((time.perf_counter() - t0) / args.steps, world, dev)
         res["e2e"] = {"value": world * fine_steps / e2e_s, "unit": "slice-steps/s",
                       "h2d_bytes_per_step": nbytes_in, "d2h_bytes_per_step": nbytes_out}
         if args.workload != "parareal":
