@@ -152,17 +152,28 @@ __host__ __device__ __forceinline__ uint32_t tile_off(int row, int k) {
 
 // Writes one thread's 4 consecutive K values (k0..k0+3, k0 a multiple of 4) of its row
 // as three bf16 planes (8-byte stores).
+// (packed bf16x2 conversions: the same round-to-nearest split as split3, two values at a time)
+__device__ __forceinline__ void split3x2(float a, float b, uint32_t& h0, uint32_t& h1, uint32_t& h2) {
+    const __nv_bfloat162 p0 = __float22bfloat162_rn(make_float2(a, b));
+    const float2 q0 = __bfloat1622float2(p0);
+    const float2 r1 = make_float2(a - q0.x, b - q0.y);
+    const __nv_bfloat162 p1 = __float22bfloat162_rn(r1);
+    const float2 q1 = __bfloat1622float2(p1);
+    const __nv_bfloat162 p2 = __float22bfloat162_rn(make_float2(r1.x - q1.x, r1.y - q1.y));
+    memcpy(&h0, &p0, 4);
+    memcpy(&h1, &p1, 4);
+    memcpy(&h2, &p2, 4);
+}
+
 __device__ __forceinline__ void store_quad_planes(unsigned char* plane0, uint32_t plane_bytes, int row, int k0,
                                                   const float* v) {
-    __nv_bfloat16 h[NPLANE][KQ];
-#pragma unroll
-    for (int k = 0; k < KQ; ++k) split3(v[k], h[0][k], h[1][k], h[2][k]);
-#pragma unroll
-    for (int pl = 0; pl < NPLANE; ++pl) {
-        uint2 u;
-        memcpy(&u, &h[pl][0], 8);
-        *reinterpret_cast<uint2*>(plane0 + pl * plane_bytes + tile_off(row, k0)) = u;
-    }
+    uint32_t a0, a1, a2, b0, b1, b2;
+    split3x2(v[0], v[1], a0, a1, a2);
+    split3x2(v[2], v[3], b0, b1, b2);
+    const uint32_t off = tile_off(row, k0);
+    *reinterpret_cast<uint2*>(plane0 + off) = make_uint2(a0, b0);
+    *reinterpret_cast<uint2*>(plane0 + plane_bytes + off) = make_uint2(a1, b1);
+    *reinterpret_cast<uint2*>(plane0 + 2 * plane_bytes + off) = make_uint2(a2, b2);
 }
 
 struct TCShape {
@@ -266,7 +277,8 @@ __device__ __forceinline__ void tmem_release(uint32_t tmem, int tid) {
 
 // control lane: table-tile ring + MMA issue for chunks 0..nq-1 (see above)
 // (b_stride: byte distance of the ring's stages; b_bytes: bytes of one chunk's table tile)
-__device__ __forceinline__ void ws_control(WS* ws, unsigned char* const* sA, uint32_t a_plane, unsigned char* sB0,
+__device__ __forceinline__ void ws_control(WS* ws, unsigned char* sA0, uint32_t a_stage, uint32_t a_plane,
+                                           unsigned char* sB0,
                                            uint32_t b_stride, uint32_t b_bytes, uint32_t b_plane, int NB,
                                            const unsigned char* Bm, int64_t bchunk, int nq, uint32_t tmem,
                                            int acc_stride, uint32_t idesc) {
@@ -290,7 +302,8 @@ __device__ __forceinline__ void ws_control(WS* ws, unsigned char* const* sA, uin
         ok = ws_wait(&ws->a_full[q & 1], (q >> 1) & 1, ab) && ws_wait(&ws->b_full[q % NB], (q / NB) & 1, ab);
         if (!ok) break;
         tc_fence_after();
-        issue_mmas(sA[q & 1], a_plane, sB0 + (size_t)(q % NB) * b_stride, b_plane, tmem, acc_stride, idesc, q == 0);
+        issue_mmas(sA0 + (q & 1) * a_stage, a_plane, sB0 + (size_t)(q % NB) * b_stride, b_plane, tmem, acc_stride,
+                   idesc, q == 0);
         mma_commit(&ws->a_empty[q & 1]);
         mma_commit(&ws->b_empty[q % NB]);
         last_mma = q;
@@ -335,7 +348,7 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_inv_tc(const float* __restrict__
     const uint32_t b_plane = (uint32_t)nt * KC * 2;
     const uint32_t a_stage = 2 * NPLANE * a_plane;        // two parities
     const uint32_t b_stage = 2 * NPLANE * b_plane;
-    unsigned char* sA[2] = {smem, smem + a_stage};
+    unsigned char* const sA0 = smem;                       // bf16 stages: sA0 + (q & 1) a_stage
     unsigned char* sB0 = smem + 2 * a_stage;
     float* raw = reinterpret_cast<float*>(sB0 + (size_t)NB * b_stage);   // [NR][2][KC][BM]
     WS* ws = reinterpret_cast<WS*>(raw + NR_INV * 2 * KC * BM);
@@ -381,7 +394,8 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_inv_tc(const float* __restrict__
         if (lane == 0) {
             const unsigned char* Bm = Binv + inv_off[m] + (int64_t)blockIdx.z * 2 * NPLANE * b_plane;
             const int64_t bchunk = (int64_t)gridDim.z * 2 * NPLANE * b_plane;   // bytes per chunk, all n-tiles
-            ws_control(ws, sA, a_plane, sB0, b_stage, b_stage, b_plane, NB, Bm, bchunk, nq, tmem, nt, idesc);
+            ws_control(ws, sA0, a_stage, a_plane, sB0, b_stage, b_stage, b_plane, NB, Bm, bchunk, nq, tmem, nt,
+                       idesc);
         }
     } else {
         for (int q = 0; q < nq; ++q) {
@@ -394,7 +408,7 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_inv_tc(const float* __restrict__
                 float v[KQ];
 #pragma unroll
                 for (int i = 0; i < KQ; ++i) v[i] = r[(par * KC + KQ * sub + i) * BM + col];
-                store_quad_planes(sA[q & 1] + par * NPLANE * a_plane, a_plane, col, KQ * sub, v);
+                store_quad_planes(sA0 + (q & 1) * a_stage + par * NPLANE * a_plane, a_plane, col, KQ * sub, v);
             }
             ws_planes_ready(ws, q, lane);
         }
@@ -451,7 +465,7 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_fwd_tc(const float* __restrict__
     const uint32_t a_stage = 2 * NPLANE * a_plane;
     const uint32_t b_stage = 2 * NPLANE * b_plane;
     const uint32_t b_stage_max = 2 * NPLANE * (uint32_t)sh.nt * KC * 2;
-    unsigned char* sA[2] = {smem, smem + a_stage};
+    unsigned char* const sA0 = smem;                       // bf16 stages: sA0 + (q & 1) a_stage
     unsigned char* sB0 = smem + 2 * a_stage;               // NB stages of b_stage_max bytes
     float* raw = reinterpret_cast<float*>(sB0 + (size_t)NB * b_stage_max);   // [NR][2 KC][BM]
     WS* ws = reinterpret_cast<WS*>(raw + NR_FWD * 2 * KC * BM);
@@ -497,7 +511,8 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_fwd_tc(const float* __restrict__
             // the copies move this wavenumber's b_stage bytes
             const unsigned char* Bm = Bfwd + fwd_off[m] + (int64_t)blockIdx.z * b_stage;
             const int64_t bchunk = (int64_t)nz * b_stage;
-            ws_control(ws, sA, a_plane, sB0, b_stage_max, b_stage, b_plane, NB, Bm, bchunk, nq, tmem, acc, idesc);
+            ws_control(ws, sA0, a_stage, a_plane, sB0, b_stage_max, b_stage, b_plane, NB, Bm, bchunk, nq, tmem, acc,
+                       idesc);
         }
     } else {
         for (int q = 0; q < nq; ++q) {
@@ -513,8 +528,8 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_fwd_tc(const float* __restrict__
                 vs[i] = fn + fs;
                 va[i] = fn - fs;
             }
-            store_quad_planes(sA[q & 1], a_plane, col, KQ * sub, vs);
-            store_quad_planes(sA[q & 1] + NPLANE * a_plane, a_plane, col, KQ * sub, va);
+            store_quad_planes(sA0 + (q & 1) * a_stage, a_plane, col, KQ * sub, vs);
+            store_quad_planes(sA0 + (q & 1) * a_stage + NPLANE * a_plane, a_plane, col, KQ * sub, va);
             ws_planes_ready(ws, q, lane);
         }
         cp_async_wait<0>();
