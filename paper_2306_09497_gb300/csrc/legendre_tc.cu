@@ -28,6 +28,7 @@
 // coalesced rows.  Every mbarrier wait is bounded: on
 // timeout the kernel sets an error flag, stops issuing work, releases its tensor
 // memory and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <vector>
@@ -71,6 +72,15 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                      smem_u32(dst)),
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
+}
+
+// 2-D tensor tile (TMA) into shared memory, completion on an mbarrier's transaction count
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
 }
 
 // per-thread asynchronous global -> shared copies (zero-filled when !pred)
@@ -196,8 +206,11 @@ struct TCShape {
 // gives up raises a shared abort flag that makes every other wait return at once, the
 // control lane drains the copies and MMAs it has in flight (bounded), and the CTA
 // reports the timeout and releases its tensor memory.
+constexpr int NR_MAX = 4;
+
 struct WS {
     uint64_t a_full[2], a_empty[2], b_full[NB_MAX], b_empty[NB_MAX], acc_full;
+    uint64_t r_full[NR_MAX];          // raw data-operand stages filled by TMA
     int abort;
     uint32_t tmem_slot;
 };
@@ -253,6 +266,7 @@ __device__ __forceinline__ uint32_t ws_setup(WS* ws, int tid) {
             mbar_init(&ws->b_empty[i], 1);
         }
         mbar_init(&ws->acc_full, 1);
+        for (int i = 0; i < NR_MAX; ++i) mbar_init(&ws->r_full[i], 1);
         ws->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -276,13 +290,52 @@ __device__ __forceinline__ void tmem_release(uint32_t tmem, int tid) {
 }
 
 // control lane: table-tile ring + MMA issue for chunks 0..nq-1 (see above)
+// Data-operand producers for the control lane.  NoTma: the converter warps load their own
+// columns with cp.async.  TmaA: the control lane loads each chunk's raw FP32 rows as 2-D
+// tensor tiles (128 columns wide) into raw stage c mod NR; a stage is refilled once the
+// converters' a_full arrival for the chunk that used it has been observed.
+struct NoTma {
+    int issued = 0;
+    __device__ __forceinline__ void issue(int) {}
+    __device__ __forceinline__ int nr() const { return 0; }
+    __device__ __forceinline__ uint64_t* full(int) const { return nullptr; }
+};
+struct TmaA {
+    const CUtensorMap* map;
+    unsigned char* raw;
+    uint32_t stage_bytes;
+    uint64_t* r_full;
+    int NR, nq, x;
+    int fwd;                 // 0: inverse, one 32-row tile at y0 + 32 c; 1: forward, north + south 16-row tiles
+    int y0, nlat;
+    int issued = 0;
+    __device__ __forceinline__ int nr() const { return NR; }
+    __device__ __forceinline__ uint64_t* full(int c) const { return &r_full[c % NR]; }
+    __device__ __forceinline__ void issue(int c) {
+        if (c >= nq) return;
+        uint64_t* bar = &r_full[c % NR];
+        unsigned char* dst = raw + (size_t)(c % NR) * stage_bytes;
+        mbar_expect_tx(bar, stage_bytes);
+        if (!fwd) {
+            tma_load_2d(dst, map, x, y0 + 32 * c, bar);
+        } else {
+            tma_load_2d(dst, map, x, y0 + 16 * c, bar);
+            tma_load_2d(dst + stage_bytes / 2, map, x, y0 + nlat - 16 * (c + 1), bar);
+        }
+        issued = c + 1;
+    }
+};
+
 // (b_stride: byte distance of the ring's stages; b_bytes: bytes of one chunk's table tile)
+template <typename AProd>
 __device__ __forceinline__ void ws_control(WS* ws, unsigned char* sA0, uint32_t a_stage, uint32_t a_plane,
                                            unsigned char* sB0,
                                            uint32_t b_stride, uint32_t b_bytes, uint32_t b_plane, int NB,
                                            const unsigned char* Bm, int64_t bchunk, int nq, uint32_t tmem,
-                                           int acc_stride, uint32_t idesc) {
+                                           int acc_stride, uint32_t idesc, AProd& ap) {
     volatile int* ab = &ws->abort;
+    for (int c = 0; c < ap.nr(); ++c) ap.issue(c);          // data operand: the first NR chunks
+    int a_seen = 0;                                          // chunks whose converters have finished
     const int D = NB - 2;                                   // table chunks in flight ahead of the MMAs
     int issued_b = 0, last_mma = -1;
     auto copy_b = [&](int c) {
@@ -299,7 +352,11 @@ __device__ __forceinline__ void ws_control(WS* ws, unsigned char* sA0, uint32_t 
             if (!ok) break;
             copy_b(c);
         }
-        ok = ws_wait(&ws->a_full[q & 1], (q >> 1) & 1, ab) && ws_wait(&ws->b_full[q % NB], (q / NB) & 1, ab);
+        ok = ws_wait(&ws->a_full[q & 1], (q >> 1) & 1, ab);
+        if (!ok) break;
+        a_seen = q + 1;
+        if (ap.nr()) ap.issue(q + ap.nr());                  // raw stage of chunk q is free again
+        ok = ws_wait(&ws->b_full[q % NB], (q / NB) & 1, ab);
         if (!ok) break;
         tc_fence_after();
         issue_mmas(sA0 + (q & 1) * a_stage, a_plane, sB0 + (size_t)(q % NB) * b_stride, b_plane, tmem, acc_stride,
@@ -318,6 +375,7 @@ __device__ __forceinline__ void ws_control(WS* ws, unsigned char* sA0, uint32_t 
     volatile int zero = 0;
     if (last_mma >= 0) ws_wait(&ws->a_empty[last_mma & 1], (last_mma >> 1) & 1, &zero);
     for (int c = last_mma + 1; c < issued_b; ++c) ws_wait(&ws->b_full[c % NB], (c / NB) & 1, &zero);
+    for (int c = a_seen; c < ap.issued; ++c) ws_wait(ap.full(c), (c / ap.nr()) & 1, &zero);
 }
 
 // converter side of chunk q, after its planes are stored: make them visible to the
@@ -335,13 +393,25 @@ __device__ __forceinline__ bool ws_warp_wait(WS* ws, uint64_t* bar, uint32_t par
     return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
 }
 
+// converter warp: every lane waits for a TMA-filled raw stage (each lane then sees the
+// tile's bytes); the warp gives up together if any lane does
+__device__ __forceinline__ bool ws_raw_wait(WS* ws, uint64_t* bar, uint32_t parity) {
+    const bool ok = ws_wait(bar, parity, &ws->abort);
+    return __all_sync(0xffffffffu, ok) != 0;
+}
+
 // ----------------------------------------------------------------------------- inverse
 // grid: (ceil(ncol/128), M+1, n-tiles over j).  Table Binv: for each m, chunk q, parity,
 // N-tile: a [nt x 16] bf16 tile x 3 planes, contiguous (offsets from inv_off[m]).
+// TMA: the raw rows of a chunk arrive as one 32 x 128 tensor tile (rows xrow0 + 32 q ..,
+// raw row t = extended row 32 q + t) issued by the control lane; otherwise each converter
+// thread copies its own column with cp.async into [parity][k][column].
+template <bool TMA>
 __global__ void __launch_bounds__(NTH, 1) k_leg_inv_tc(const float* __restrict__ X, float* __restrict__ F,
                                                        const unsigned char* __restrict__ Binv,
                                                        const long long* __restrict__ inv_off,
-                                                       const int* __restrict__ inv_nq, TCShape sh, int NB, int* err) {
+                                                       const int* __restrict__ inv_nq, TCShape sh, int NB, int* err,
+                                                       const __grid_constant__ CUtensorMap tmX) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int nt = sh.nt;
     const uint32_t a_plane = BM * KC * 2;                 // 4 KB
@@ -369,7 +439,7 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_inv_tc(const float* __restrict__
     // raw prefetch of chunk qq (rows n = m + par + 2k, k in [16 qq, 16 qq + 16)): this thread's
     // column and quarter
     auto prefetch = [&](int qq) {
-        if (qq < nq) {
+        if (!TMA && qq < nq) {
             float* r = raw + (qq % NR_INV) * (2 * KC * BM);
 #pragma unroll
             for (int par = 0; par < 2; ++par)
@@ -384,7 +454,7 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_inv_tc(const float* __restrict__
         }
         cp_async_commit();
     };
-    if (conv) {
+    if (conv && !TMA) {
 #pragma unroll
         for (int qq = 0; qq < NR_INV - 1; ++qq) prefetch(qq);
     }
@@ -394,20 +464,41 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_inv_tc(const float* __restrict__
         if (lane == 0) {
             const unsigned char* Bm = Binv + inv_off[m] + (int64_t)blockIdx.z * 2 * NPLANE * b_plane;
             const int64_t bchunk = (int64_t)gridDim.z * 2 * NPLANE * b_plane;   // bytes per chunk, all n-tiles
-            ws_control(ws, sA0, a_stage, a_plane, sB0, b_stage, b_stage, b_plane, NB, Bm, bchunk, nq, tmem, nt,
-                       idesc);
+            if constexpr (TMA) {
+                TmaA ap{&tmX, reinterpret_cast<unsigned char*>(raw), 2 * KC * BM * 4, ws->r_full, NR_INV, nq, c0, 0,
+                        (int)xrow0, 0};
+                ws_control(ws, sA0, a_stage, a_plane, sB0, b_stage, b_stage, b_plane, NB, Bm, bchunk, nq, tmem, nt,
+                           idesc, ap);
+            } else {
+                NoTma ap;
+                ws_control(ws, sA0, a_stage, a_plane, sB0, b_stage, b_stage, b_plane, NB, Bm, bchunk, nq, tmem, nt,
+                           idesc, ap);
+            }
         }
     } else {
         for (int q = 0; q < nq; ++q) {
-            prefetch(q + NR_INV - 1);
-            cp_async_wait<NR_INV - 1>();
+            if constexpr (TMA) {
+                if (!ws_raw_wait(ws, &ws->r_full[q % NR_INV], (q / NR_INV) & 1)) break;
+            } else {
+                prefetch(q + NR_INV - 1);
+                cp_async_wait<NR_INV - 1>();
+            }
             if (q >= 2 && !ws_warp_wait(ws, &ws->a_empty[q & 1], ((q - 2) >> 1) & 1, lane)) break;
             const float* r = raw + (q % NR_INV) * (2 * KC * BM);
 #pragma unroll
             for (int par = 0; par < 2; ++par) {
                 float v[KQ];
 #pragma unroll
-                for (int i = 0; i < KQ; ++i) v[i] = r[(par * KC + KQ * sub + i) * BM + col];
+                for (int i = 0; i < KQ; ++i) {
+                    const int kk = KQ * sub + i;
+                    if constexpr (TMA) {
+                        // rows past this wavenumber's Kx belong to the next one (or are the tile's zero fill)
+                        const float x = r[(par + 2 * kk) * BM + col];
+                        v[i] = par + 2 * (KC * q + kk) < Kx ? x : 0.f;
+                    } else {
+                        v[i] = r[(par * KC + kk) * BM + col];
+                    }
+                }
                 store_quad_planes(sA0 + (q & 1) * a_stage + par * NPLANE * a_plane, a_plane, col, KQ * sub, v);
             }
             ws_planes_ready(ws, q, lane);
@@ -448,11 +539,16 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_inv_tc(const float* __restrict__
 // grid: (ceil(ncol/128), M+1, max n-tiles over k).  Table Bfwd: for each m, j-chunk q,
 // n-tile z, parity: a [nt_m x 16] tile x 3 planes (rows k = degree index within the
 // parity); nt_m = fwd_nt[m] follows the number of degrees of m (multiple of 16).
+// TMA: chunk q arrives as two 16 x 128 tensor tiles, the northern rows j = 16 q + t (raw
+// row t) and the southern rows nlat - 16 (q + 1) + t (raw row 16 + t, i.e. the mirror of
+// j = 16 q + 15 - t); otherwise each converter thread copies its own column with cp.async.
+template <bool TMA>
 __global__ void __launch_bounds__(NTH, 1) k_leg_fwd_tc(const float* __restrict__ F, float* __restrict__ Y,
                                                        const unsigned char* __restrict__ Bfwd,
                                                        const long long* __restrict__ fwd_off,
                                                        const int* __restrict__ fwd_ntiles,
-                                                       const int* __restrict__ fwd_nt, TCShape sh, int NB, int* err) {
+                                                       const int* __restrict__ fwd_nt, TCShape sh, int NB, int* err,
+                                                       const __grid_constant__ CUtensorMap tmF) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int M = sh.M;
     const int m = M - (int)blockIdx.y;
@@ -485,7 +581,7 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_fwd_tc(const float* __restrict__
     // raw prefetch of chunk qq: rows j = 16 qq + jj (north) and nlat-1-j (south), this thread's
     // column and quarter
     auto prefetch = [&](int qq) {
-        if (qq < nq) {
+        if (!TMA && qq < nq) {
             float* r = raw + (qq % NR_FWD) * (2 * KC * BM);
 #pragma unroll
             for (int i = 0; i < KQ; ++i) {
@@ -499,7 +595,7 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_fwd_tc(const float* __restrict__
         }
         cp_async_commit();
     };
-    if (conv) {
+    if (conv && !TMA) {
 #pragma unroll
         for (int qq = 0; qq < NR_FWD - 1; ++qq) prefetch(qq);
     }
@@ -511,20 +607,41 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_fwd_tc(const float* __restrict__
             // the copies move this wavenumber's b_stage bytes
             const unsigned char* Bm = Bfwd + fwd_off[m] + (int64_t)blockIdx.z * b_stage;
             const int64_t bchunk = (int64_t)nz * b_stage;
-            ws_control(ws, sA0, a_stage, a_plane, sB0, b_stage_max, b_stage, b_plane, NB, Bm, bchunk, nq, tmem, acc,
-                       idesc);
+            if constexpr (TMA) {
+                TmaA ap{&tmF, reinterpret_cast<unsigned char*>(raw), 2 * KC * BM * 4, ws->r_full, NR_FWD, nq, c0, 1,
+                        m * sh.nlat, sh.nlat};
+                ws_control(ws, sA0, a_stage, a_plane, sB0, b_stage_max, b_stage, b_plane, NB, Bm, bchunk, nq, tmem,
+                           acc, idesc, ap);
+            } else {
+                NoTma ap;
+                ws_control(ws, sA0, a_stage, a_plane, sB0, b_stage_max, b_stage, b_plane, NB, Bm, bchunk, nq, tmem,
+                           acc, idesc, ap);
+            }
         }
     } else {
         for (int q = 0; q < nq; ++q) {
-            prefetch(q + NR_FWD - 1);
-            cp_async_wait<NR_FWD - 1>();
+            if constexpr (TMA) {
+                if (!ws_raw_wait(ws, &ws->r_full[q % NR_FWD], (q / NR_FWD) & 1)) break;
+            } else {
+                prefetch(q + NR_FWD - 1);
+                cp_async_wait<NR_FWD - 1>();
+            }
             if (q >= 2 && !ws_warp_wait(ws, &ws->a_empty[q & 1], ((q - 2) >> 1) & 1, lane)) break;
             const float* r = raw + (q % NR_FWD) * (2 * KC * BM);
             float vs[KQ], va[KQ];
 #pragma unroll
             for (int i = 0; i < KQ; ++i) {
                 const int jj = KQ * sub + i;
-                const float fn = r[jj * BM + col], fs = r[(KC + jj) * BM + col];
+                float fn, fs;
+                if constexpr (TMA) {
+                    // rows j >= nlat/2 of the last chunk are the other hemisphere's: dropped
+                    const bool in = KC * q + jj < sh.nlat2;
+                    fn = in ? r[jj * BM + col] : 0.f;
+                    fs = in ? r[(2 * KC - 1 - jj) * BM + col] : 0.f;
+                } else {
+                    fn = r[jj * BM + col];
+                    fs = r[(KC + jj) * BM + col];
+                }
                 vs[i] = fn + fs;
                 va[i] = fn - fs;
             }
@@ -741,8 +858,14 @@ swe_status split_tables_build(swe_plan* p) {
     const size_t one_per_sm = 116 * 1024;
     if (t->smem_inv < one_per_sm) t->smem_inv = one_per_sm;
     if (t->smem_fwd < one_per_sm) t->smem_fwd = one_per_sm;
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_leg_inv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_inv);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_leg_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_fwd);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_leg_inv_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_inv);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_leg_inv_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_inv);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_leg_fwd_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_fwd);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_leg_fwd_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_fwd);
     p->Pbf = t;
     if (e != cudaSuccess) return swe_cuda_status(e, "split table kernels");
     return SWE_OK;
@@ -763,6 +886,42 @@ void split_tables_free(swe_plan* p) {
     p->Pbf = nullptr;
 }
 
+// ----------------------------------------------------------------------------- tensor maps
+// cuTensorMapEncodeTiled is a driver entry point; it is looked up once through the runtime so
+// that the library needs no link-time dependency on the driver library.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+// Row-major FP32 matrix [rows][ncol] read in boxes of 128 columns x box_rows rows.  Usable when
+// the row pitch and the base are multiples of 16 bytes (the tensor-map rules); out-of-range
+// rows and columns read as zero.  Returns false (map untouched) when TMA cannot be used.
+static bool encode_rows(CUtensorMap* map, const float* base, int ncol, long long rows, int box_rows) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn || ncol % 4 != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0 || rows <= 0 || rows >= (1LL << 31))
+        return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)ncol, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ncol * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)BM, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 swe_status leg_inverse_split(const swe_plan* p, const float2* X, float2* F, int C, cudaStream_t st) {
     const SplitTables* t = (const SplitTables*)p->Pbf;
     if (!t) {
@@ -773,11 +932,14 @@ swe_status leg_inverse_split(const swe_plan* p, const float2* X, float2* F, int 
     dim3 grid((sh.ncol + BM - 1) / BM, p->M + 1, t->ntiles_inv);
     const double fl = (double)C * p->nlat * (p->M + 1.0) * (p->M + 2.0);
     const double by = 8.0 * C * p->ncx + 8.0 * C * (p->M + 1.0) * p->nlat;
+    alignas(64) CUtensorMap tm{};
+    const bool tma = p->nlat2 >= KC && encode_rows(&tm, (const float*)X, sh.ncol, p->ncx, 2 * KC);
+    auto kern = tma ? k_leg_inv_tc<true> : k_leg_inv_tc<false>;
     // the dynamic shared-memory limit is a per-function attribute shared by all plans: set it per launch
-    SWE_CHECK_CUDA(cudaFuncSetAttribute(k_leg_inv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_inv));
+    SWE_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_inv));
     ProfToken tk = prof_begin("leg_inv_tc", st, fl, by);
-    k_leg_inv_tc<<<grid, NTH, t->smem_inv, st>>>((const float*)X, (float*)F, t->inv, t->inv_off, t->inv_nq, sh,
-                                                t->nb_inv, t->err);
+    kern<<<grid, NTH, t->smem_inv, st>>>((const float*)X, (float*)F, t->inv, t->inv_off, t->inv_nq, sh, t->nb_inv,
+                                         t->err, tm);
     prof_end(tk, st);
     SWE_CHECK_LAUNCH("k_leg_inv_tc");
     return SWE_OK;
@@ -793,10 +955,14 @@ swe_status leg_forward_split(const swe_plan* p, const float2* F, float2* Y, int 
     dim3 grid((sh.ncol + BM - 1) / BM, p->M + 1, t->nz_fwd);
     const double fl = (double)C * p->nlat * (p->M + 1.0) * (p->M + 2.0);
     const double by = 8.0 * C * (p->M + 1.0) * p->nlat + 8.0 * C * p->ncx;
-    SWE_CHECK_CUDA(cudaFuncSetAttribute(k_leg_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_fwd));
+    alignas(64) CUtensorMap tm{};
+    const bool tma =
+        p->nlat2 >= KC && encode_rows(&tm, (const float*)F, sh.ncol, (long long)(p->M + 1) * p->nlat, KC);
+    auto kern = tma ? k_leg_fwd_tc<true> : k_leg_fwd_tc<false>;
+    SWE_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_fwd));
     ProfToken tk = prof_begin("leg_fwd_tc", st, fl, by);
-    k_leg_fwd_tc<<<grid, NTH, t->smem_fwd, st>>>((const float*)F, (float*)Y, t->fwd, t->fwd_off, t->fwd_ntiles,
-                                                t->fwd_nt, sh, t->nb_fwd, t->err);
+    kern<<<grid, NTH, t->smem_fwd, st>>>((const float*)F, (float*)Y, t->fwd, t->fwd_off, t->fwd_ntiles, t->fwd_nt,
+                                         sh, t->nb_fwd, t->err, tm);
     prof_end(tk, st);
     SWE_CHECK_LAUNCH("k_leg_fwd_tc");
     return SWE_OK;
