@@ -99,6 +99,9 @@ __global__ void k_sl_operands(SV U, TX* __restrict__ X, const int* __restrict__ 
 //   tab[0 .. nlat+3]             extended latitudes (two halo rows beyond each pole)
 //   tab[nlat+4 .. 2 nlat+3]      sin(latitude) = mu
 //   tab[2 nlat+4 .. 3 nlat+3]    cos(latitude)
+//   tab[3 nlat+4 + 4 i + r]      1 / prod_{q != r} (y_r - y_q), y_r = tab[i - 1 + r]: the
+//                                Lagrange denominators of the stencil on extended rows
+//                                i-1 .. i+2 (i in [1, nlat+1]; zero elsewhere)
 __device__ __forceinline__ void sc_pi(double x, double* s, double* c) { sincospi(x, s, c); }
 __device__ __forceinline__ void sc_pi(float x, float* s, float* c) { sincospif(x, s, c); }
 
@@ -122,35 +125,44 @@ __global__ void k_sl_vel(const T* __restrict__ G, int fp, int fd, int fu, int fv
     NR[(int64_t)s * npt + p] = -at(fp) * at(fd);
 }
 
-// X_Phi += h (2 N_R^n - N_R^{n-1}) in place (field 0 of the 7-field block)
+// X_Phi += h (2 N_R^n - N_R^{n-1}) in place (field 0 of the 7-field block); when W is given,
+// also the extrapolated velocity W = 2 V^n - V^{n-1} of the SETTLS trajectory (§2.3.2, Eq. 6)
+// for its three Cartesian components (interpolation is linear, so interpolating W equals
+// 2 V^n(x) - V^{n-1}(x) up to rounding)
 template <typename T>
 __global__ void k_sl_xphi(T* __restrict__ G, const T* __restrict__ NRn, const T* __restrict__ NRm, T h, int S,
-                          int64_t npt) {
+                          int64_t npt, const T* __restrict__ Vn, const T* __restrict__ Vm, T* __restrict__ W) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= npt * S) return;
+    const int64_t n = npt * S;
+    if (t >= n) return;
     G[t] = G[t] + h * ((T)2 * NRn[t] - NRm[t]);
+    if (W) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) W[d * n + t] = (T)2 * Vn[d * n + t] - Vm[d * n + t];
+    }
 }
 
 template <typename T>
 struct Stencil {
-    int base[4];      // first of the four columns of each row, before wrapping (may be -1 or >= nlon)
-    int64_t row[4];   // row offsets (grid row * nlon)
+    int off[16];      // grid offset (row * nlon + wrapped column) of point (r, c) at 4 r + c
     T wl[4], wx[4];
 };
 
 // bracket + Lagrange weights of the departure point (latd, xd = longitude in grid
-// cells, in [0, nlon)); thx = extended latitudes (nlat+4, descending)
+// cells, in [0, nlon)); tab = the geometry table (extended latitudes first, descending)
 template <typename T>
-__device__ __forceinline__ void make_stencil(T latd, T xd, const T* __restrict__ thx, int nlat, int nlon,
+__device__ __forceinline__ void make_stencil(T latd, T xd, const T* __restrict__ tab, int nlat, int nlon,
                                              Stencil<T>& st) {
-    // i = (number of extended latitudes >= latd) - 1, clipped to [1, nlat+1]
-    int lo = 0, hi = nlat + 4;                 // count of entries >= latd lies in [lo, hi]
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (thx[mid] >= latd) lo = mid + 1; else hi = mid;
-    }
-    int i = lo - 1;
-    i = i < 1 ? 1 : (i > nlat + 1 ? nlat + 1 : i);
+    // i = (number of extended latitudes >= latd) - 1, clipped to [1, nlat+1].  Gaussian
+    // colatitudes sit close to pi (4 j + 3) / (4 nlat + 2), which gives the index to within a
+    // row or two; the walk below settles it (each loop is bounded by the table's ends).
+    const T* thx = tab;
+    const T colat = (T)(0.5 * M_PI) - latd;
+    int g = (int)floor(colat * (T)((4.0 * nlat + 2.0) / (4.0 * M_PI)) - (T)0.75) + 2;
+    g = g < 0 ? 0 : (g > nlat + 3 ? nlat + 3 : g);
+    while (g < nlat + 3 && thx[g + 1] >= latd) ++g;
+    while (g > 0 && thx[g] < latd) --g;
+    const int i = g < 1 ? 1 : (g > nlat + 1 ? nlat + 1 : g);
     int i0 = (int)floor(xd);
     const T t = xd - (T)i0;
     if (i0 >= nlon) i0 -= nlon;
@@ -169,20 +181,25 @@ __device__ __forceinline__ void make_stencil(T latd, T xd, const T* __restrict__
             rowi = nlat - 1 - (e - (nlat + 2));
             sh = nlon / 2;
         }
-        st.row[r] = (int64_t)rowi * nlon;
-        st.base[r] = i0 - 1 + sh;
+        const int b = i0 - 1 + sh;             // first column before wrapping, in [-1, 3 nlon / 2]
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            int col = b + c;
+            if (col < 0) col += nlon;
+            if (col >= nlon) col -= nlon;
+            st.off[4 * r + c] = rowi * nlon + col;
+        }
     }
-    // Lagrange weights: w_r = prod_{q != r} (latd - y_q) / prod_{q != r} (y_r - y_q)
+    // Lagrange weights: w_r = prod_{q != r} (latd - y_q) / prod_{q != r} (y_r - y_q), the
+    // reciprocal denominators from the table
+    const T* rden = tab + 3 * nlat + 4 + 4 * i;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-        T num = (T)1, den = (T)1;
+        T num = (T)1;
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            if (q != r) {
-                num *= latd - y[q];
-                den *= y[r] - y[q];
-            }
-        st.wl[r] = num / den;
+            if (q != r) num *= latd - y[q];
+        st.wl[r] = num * rden[r];
     }
     const T sixth = (T)1 / (T)6;
     st.wx[0] = -t * (t - (T)1) * (t - (T)2) * sixth;
@@ -192,19 +209,13 @@ __device__ __forceinline__ void make_stencil(T latd, T xd, const T* __restrict__
 }
 
 template <typename T>
-__device__ __forceinline__ T interp(const T* __restrict__ F, const Stencil<T>& st, int nlon) {
+__device__ __forceinline__ T interp(const T* __restrict__ F, const Stencil<T>& st) {
     T acc = (T)0;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-        const T* row = F + st.row[r];
         T a = (T)0;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            int col = st.base[r] + c;          // in [-1, 3 nlon / 2 + 1]
-            if (col < 0) col += nlon;
-            if (col >= nlon) col -= nlon;
-            a += st.wx[c] * row[col];
-        }
+        for (int c = 0; c < 4; ++c) a += st.wx[c] * F[st.off[4 * r + c]];
         acc += st.wl[r] * a;
     }
     return acc;
@@ -219,10 +230,11 @@ __device__ __forceinline__ void to_latlon(const T* xd, int nlon, T& latd, T& lon
     if (lonc >= (T)nlon) lonc -= (T)nlon;
 }
 
-// departure points + gather: R[f*S + s] = X_f(x_d) (+ h N_R^n(x_a) for f = 0)
+// departure points + gather: R[f*S + s] = X_f(x_d) (+ h N_R^n(x_a) for f = 0); W = the
+// extrapolated velocity 2 V^n - V^{n-1} (V^n itself in the one-step form)
 template <typename T>
 __global__ void __launch_bounds__(128) k_sl_depart(const T* __restrict__ G, const T* __restrict__ Vn,
-                                                   const T* __restrict__ Vm, const T* __restrict__ NRn,
+                                                   const T* __restrict__ W, const T* __restrict__ NRn,
                                                    T* __restrict__ R, const T* __restrict__ tab, T h, T a, int S,
                                                    int nlat, int nlon) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -235,14 +247,13 @@ __global__ void __launch_bounds__(128) k_sl_depart(const T* __restrict__ G, cons
     T sl, cl;
     sc_pi((T)(2 * k) / (T)nlon, &sl, &cl);
     const T xa[3] = {cp * cl, cp * sl, sp};
-    T va[3], vm[3];
+    T va[3], w[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         va[d] = Vn[((int64_t)d * S + s) * npt + p];
-        vm[d] = Vm[((int64_t)d * S + s) * npt + p];
+        w[d] = W[((int64_t)d * S + s) * npt + p];      // x_d^0 = x_a: grid values
     }
     const T sc = h / a;   // (dt/2) / a
-    T vn[3] = {va[0], va[1], va[2]};   // x_d^0 = x_a: grid values
     Stencil<T> st;
     T xd[3];
     for (int it = 0; it < 2; ++it) {
@@ -251,20 +262,17 @@ __global__ void __launch_bounds__(128) k_sl_depart(const T* __restrict__ G, cons
             to_latlon(xd, nlon, latd, lonc);
             make_stencil(latd, lonc, tab, nlat, nlon, st);
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                vn[d] = interp(Vn + ((int64_t)d * S + s) * npt, st, nlon);
-                vm[d] = interp(Vm + ((int64_t)d * S + s) * npt, st, nlon);
-            }
+            for (int d = 0; d < 3; ++d) w[d] = interp(W + ((int64_t)d * S + s) * npt, st);
         }
 #pragma unroll
-        for (int d = 0; d < 3; ++d) xd[d] = xa[d] - sc * ((T)2 * vn[d] - vm[d] + va[d]);
+        for (int d = 0; d < 3; ++d) xd[d] = xa[d] - sc * (w[d] + va[d]);
     }
     T latd, lonc;
     to_latlon(xd, nlon, latd, lonc);
     make_stencil(latd, lonc, tab, nlat, nlon, st);
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
-        T v = interp(G + ((int64_t)f * S + s) * npt, st, nlon);
+        T v = interp(G + ((int64_t)f * S + s) * npt, st);
         if (f == 0) v += h * NRn[(int64_t)s * npt + p];
         R[((int64_t)f * S + s) * npt + p] = v;
     }
@@ -284,15 +292,29 @@ __global__ void k_sl_unpack(const TY* __restrict__ Y, double2* __restrict__ R, c
     for (int f = 0; f < 3; ++f) R[((int64_t)f * nc + r) * S + s] = get2(y + (int64_t)f * S);
 }
 
+// extended latitude e (0..nlat+3): two rows mirrored over each pole around the Gaussian ones
+__device__ inline double ext_lat(const double* __restrict__ mu, int e, int nlat) {
+    if (e < 2) return M_PI - asin(mu[1 - e]);
+    if (e < nlat + 2) return asin(mu[e - 2]);
+    return -M_PI - asin(mu[nlat - 1 - (e - (nlat + 2))]);
+}
+
 template <typename T>
 __global__ void k_sl_table(const double* __restrict__ mu, T* __restrict__ tab, int nlat) {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e < nlat + 4) {
-        double v;
-        if (e < 2) v = M_PI - asin(mu[1 - e]);
-        else if (e < nlat + 2) v = asin(mu[e - 2]);
-        else v = -M_PI - asin(mu[nlat - 1 - (e - (nlat + 2))]);
-        tab[e] = (T)v;
+        tab[e] = (T)ext_lat(mu, e, nlat);
+        const bool ok = e >= 1 && e <= nlat + 1;
+        double y[4];
+        // the nodes exactly as the kernels see them (rounded to T), so that the weights are a
+        // Lagrange basis of one node set; products and reciprocal in FP64
+        for (int r = 0; r < 4; ++r) y[r] = ok ? (double)(T)ext_lat(mu, e - 1 + r, nlat) : 0.0;
+        for (int r = 0; r < 4; ++r) {
+            double den = 1.0;
+            for (int q = 0; q < 4; ++q)
+                if (q != r) den *= y[r] - y[q];
+            tab[3 * nlat + 4 + 4 * e + r] = ok ? (T)(1.0 / den) : (T)0;
+        }
     }
     if (e < nlat) {
         tab[nlat + 4 + e] = (T)mu[e];
@@ -352,7 +374,7 @@ static SLBuf sl_carve(const swe_plan* p, char* c, int S) {
 
 static swe_status ensure_thx(swe_plan* p) {
     if (p->thx) return SWE_OK;
-    const size_t n = 3 * (size_t)p->nlat + 4;
+    const size_t n = 3 * (size_t)p->nlat + 4 + 4 * ((size_t)p->nlat + 4);
     p->gen += 1;
     if (p->prec == SWE_FP64) {
         SWE_CHECK_CUDA(cudaMalloc(&p->thx, sizeof(double) * n));
@@ -429,20 +451,25 @@ swe_status sl_step(swe_plan* p, double dt, double nu, int q, const double2* Upre
         Vm = b.Vp;
         Nm = b.Np;
     }
-    // X_Phi += h (2 N_R^n - N_R^{n-1})
+    // X_Phi += h (2 N_R^n - N_R^{n-1}); W = 2 V^n - V^{n-1} into the (now free) previous-state
+    // grid block, or V^n itself in the one-step form
+    const bool two = Vm != b.Vc;
+    const void* W = two ? b.Gp : b.Vc;
     if (f64) {
         k_sl_xphi<double><<<nb(npt * S), 256, 0, st>>>((double*)b.G, (const double*)b.Nc, (const double*)Nm, h, S,
-                                                        npt);
+                                                        npt, (const double*)b.Vc, (const double*)Vm,
+                                                        two ? (double*)b.Gp : nullptr);
     } else {
         k_sl_xphi<float><<<nb(npt * S), 256, 0, st>>>((float*)b.G, (const float*)b.Nc, (const float*)Nm, (float)h, S,
-                                                       npt);
+                                                       npt, (const float*)b.Vc, (const float*)Vm,
+                                                       two ? (float*)b.Gp : nullptr);
     }
     SWE_CHECK_LAUNCH("k_sl_xphi");
     if (f64) {
         {
             ProfToken tk_ = prof_begin("sl_depart", st, 0.0, (f64 ? 8.0 : 4.0) * 13.0 * npt * S);
             k_sl_depart<double><<<nb(npt * S, 128), 128, 0, st>>>((const double*)b.G, (const double*)b.Vc,
-                                                              (const double*)Vm, (const double*)b.Nc, (double*)b.R,
+                                                              (const double*)W, (const double*)b.Nc, (double*)b.R,
                                                               (const double*)p->thx, h, p->a, S, p->nlat, p->nlon);
             prof_end(tk_, st);
         }
@@ -450,7 +477,7 @@ swe_status sl_step(swe_plan* p, double dt, double nu, int q, const double2* Upre
         {
             ProfToken tk_ = prof_begin("sl_depart", st, 0.0, (f64 ? 8.0 : 4.0) * 13.0 * npt * S);
             k_sl_depart<float><<<nb(npt * S, 128), 128, 0, st>>>((const float*)b.G, (const float*)b.Vc,
-                                                             (const float*)Vm, (const float*)b.Nc, (float*)b.R,
+                                                             (const float*)W, (const float*)b.Nc, (float*)b.R,
                                                              (const float*)p->thx, (float)h, (float)p->a, S,
                                                              p->nlat, p->nlon);
             prof_end(tk_, st);
