@@ -85,6 +85,59 @@ __global__ void k_soa_aos_strided(const double2* __restrict__ in, double2* __res
     out[(int64_t)s * stride + fr] = v;
 }
 
+// Tiled forms of the strided layout changes for batches of at least TT states: a TT x TT
+// tile of complex values passes through shared memory, so that the per-state side and the
+// batched side are both read / written as 512-byte rows (a plain element-per-thread
+// transpose makes one of the two sides a 16-byte gather).  n = 3 nc values per state.
+constexpr int TT = 32;
+
+__global__ void __launch_bounds__(256) k_aos_soa_tiled(const double2* __restrict__ in, int64_t stride,
+                                                       double2* __restrict__ out, int64_t n, int S) {
+    __shared__ double2 tile[TT][TT + 1];
+    const int64_t r0 = (int64_t)blockIdx.x * TT;
+    const int s0 = blockIdx.y * TT;
+    const int tx = threadIdx.x & (TT - 1), ty = threadIdx.x / TT;
+#pragma unroll
+    for (int i = ty; i < TT; i += 256 / TT) {
+        const int s = s0 + i;
+        const int64_t r = r0 + tx;
+        if (s < S && r < n) tile[i][tx] = in[(int64_t)s * stride + r];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = ty; i < TT; i += 256 / TT) {
+        const int64_t r = r0 + i;
+        const int s = s0 + tx;
+        if (s < S && r < n) out[r * S + s] = tile[tx][i];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_soa_aos_tiled(const double2* __restrict__ in, double2* __restrict__ out,
+                                                       int64_t stride, const double2* __restrict__ add,
+                                                       int64_t add_stride, int64_t n, int S) {
+    __shared__ double2 tile[TT][TT + 1];
+    const int64_t r0 = (int64_t)blockIdx.x * TT;
+    const int s0 = blockIdx.y * TT;
+    const int tx = threadIdx.x & (TT - 1), ty = threadIdx.x / TT;
+#pragma unroll
+    for (int i = ty; i < TT; i += 256 / TT) {
+        const int64_t r = r0 + i;
+        const int s = s0 + tx;
+        if (s < S && r < n) tile[i][tx] = in[r * S + s];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = ty; i < TT; i += 256 / TT) {
+        const int s = s0 + i;
+        const int64_t r = r0 + tx;
+        if (s < S && r < n) {
+            double2 v = tile[tx][i];
+            if (add) v = c_add(v, add[(int64_t)s * add_stride + r]);
+            out[(int64_t)s * stride + r] = v;
+        }
+    }
+}
+
 __global__ void k_pack(const double2* __restrict__ spec, double2* __restrict__ X, const int* __restrict__ row_m, int M,
                        int64_t nc, int64_t ncx, int B) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -921,13 +974,23 @@ inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// batches of at least TT states (and at most 65535 TT, the grid's y limit) take the tiled forms
+static bool tiled_ok(int S) { return S >= TT && S <= 65535 * TT; }
+static dim3 tiled_grid(int64_t n, int S) { return dim3((unsigned)((n + TT - 1) / TT), (unsigned)((S + TT - 1) / TT)); }
+
 swe_status k_aos_to_soa(const swe_plan* p, const double2* in, double2* out, int S, cudaStream_t st) {
-    k_aos_soa<<<nblk(3 * p->nc * S), 256, 0, st>>>(in, out, p->nc, S);
+    if (tiled_ok(S))
+        k_aos_soa_tiled<<<tiled_grid(3 * p->nc, S), 256, 0, st>>>(in, 3 * p->nc, out, 3 * p->nc, S);
+    else
+        k_aos_soa<<<nblk(3 * p->nc * S), 256, 0, st>>>(in, out, p->nc, S);
     SWE_CHECK_LAUNCH("k_aos_soa");
     return SWE_OK;
 }
 swe_status k_soa_to_aos(const swe_plan* p, const double2* in, double2* out, int S, cudaStream_t st) {
-    k_soa_aos<<<nblk(3 * p->nc * S), 256, 0, st>>>(in, out, p->nc, S);
+    if (tiled_ok(S))
+        k_soa_aos_tiled<<<tiled_grid(3 * p->nc, S), 256, 0, st>>>(in, out, 3 * p->nc, nullptr, 0, 3 * p->nc, S);
+    else
+        k_soa_aos<<<nblk(3 * p->nc * S), 256, 0, st>>>(in, out, p->nc, S);
     SWE_CHECK_LAUNCH("k_soa_aos");
     return SWE_OK;
 }
@@ -1106,7 +1169,10 @@ swe_status k_aos_to_soa_strided(const swe_plan* p, const double2* in, int64_t st
                                 cudaStream_t st) {
     {
         ProfToken tk_ = prof_begin("aos_soa", st, 0.0, 16.0 * 6.0 * p->nc * S);
-        k_aos_soa_strided<<<nblk(3 * p->nc * S), 256, 0, st>>>(in, stride, out, p->nc, S);
+        if (tiled_ok(S))
+            k_aos_soa_tiled<<<tiled_grid(3 * p->nc, S), 256, 0, st>>>(in, stride, out, 3 * p->nc, S);
+        else
+            k_aos_soa_strided<<<nblk(3 * p->nc * S), 256, 0, st>>>(in, stride, out, p->nc, S);
         prof_end(tk_, st);
     }
     SWE_CHECK_LAUNCH("k_aos_soa_strided");
@@ -1117,7 +1183,11 @@ swe_status k_soa_to_aos_strided(const swe_plan* p, const double2* in, double2* o
                                 int64_t add_stride, int S, cudaStream_t st) {
     {
         ProfToken tk_ = prof_begin("soa_aos", st, 0.0, 16.0 * (add ? 9.0 : 6.0) * p->nc * S);
-        k_soa_aos_strided<<<nblk(3 * p->nc * S), 256, 0, st>>>(in, out, stride, add, add_stride, p->nc, S);
+        if (tiled_ok(S))
+            k_soa_aos_tiled<<<tiled_grid(3 * p->nc, S), 256, 0, st>>>(in, out, stride, add, add_stride, 3 * p->nc,
+                                                                      S);
+        else
+            k_soa_aos_strided<<<nblk(3 * p->nc * S), 256, 0, st>>>(in, out, stride, add, add_stride, p->nc, S);
         prof_end(tk_, st);
     }
     SWE_CHECK_LAUNCH("k_soa_aos_strided");

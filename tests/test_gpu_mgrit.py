@@ -41,10 +41,14 @@ CASES = [
     ([(31, 48, 96, 0, 300.0, 2, 0.0), (31, 48, 96, 0, 1200.0, 4, 1e15)], 16, 4, 1, 2),
     ([(31, 48, 96, 0, 300.0, 2, 0.0), (21, 32, 64, 2, 600.0, 2, 1e5), (21, 32, 64, 1, 1200.0, 2, 1e5)], 8, 2, 0, 2),
     CASE_MIXED,
+    # batched relaxations of 128 (level 0) and 64 (level 1, with its FAS right-hand side)
+    # intervals: the tiled layout changes between per-interval and batched states
+    ([(21, 32, 64, 0, 300.0, 2, 0.0), (21, 32, 64, 0, 600.0, 2, 1e5), (21, 32, 64, 0, 1200.0, 2, 1e5)], 256, 2, 0,
+     1),
 ]
 
 
-@pytest.mark.parametrize("case", CASES, ids=["imex3", "imex2_fcf", "sl_coarse3", "t63_sl_coarse3"])
+@pytest.mark.parametrize("case", CASES, ids=["imex3", "imex2_fcf", "sl_coarse3", "t63_sl_coarse3", "imex3_wide"])
 def test_mgrit_matches_oracle(case):
     _run_case(case, mixed=False)
 
