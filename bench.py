@@ -384,7 +384,12 @@ def serve_measure(prec_name, local, n_req=16, load=0.8, seed=1000):
     rng = np.random.default_rng(seed + 7)
     gaps = rng.exponential(1.0 / (load * rate), size=len(subs))
     arrivals = list(np.cumsum(gaps) - gaps[0])
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = swe.launch_count()
     lat, wall = run(arrivals)
+    launches = swe.launch_count() - l0
+    clk = clocks.stop()
     for p in plans.values():
         p.close()
     v = sorted(lat.values())
@@ -395,7 +400,7 @@ def serve_measure(prec_name, local, n_req=16, load=0.8, seed=1000):
             "saturated_req_per_s": rate, "offered_load": load, "arrival_rate_per_s": load * rate,
             "p50_latency_s": q(50), "p99_latency_s": q(99), "max_latency_s": v[-1],
             "throughput_req_per_s": len(subs) / wall, "fine_slice_steps_per_s": work / wall,
-            "precision": prec_name}
+            "precision": prec_name, "gpu_launches": launches, "clocks": clk}
 
 
 def measure(args, prec_name, rank, world, local, with_e2e=True):
@@ -604,7 +609,7 @@ def run_serve(args):
             "vs_baseline": None, "dtype": "mixed", "data": "synthetic",
             "config": {"workload": "serve_t63_t341_mix", "requests": mixed["requests"], "mix": mixed["mix"],
                        "parallelism": "1 GPU" if world == 1 else f"replicas x{world}"},
-            "serving": mixed}
+            "serving": mixed, "gpu_launches": mixed["gpu_launches"], "clocks": mixed["clocks"]}
     if not args.no_fp64:
         line["serving_fp64"] = serve_measure("fp64", local, n_req=args.serve_requests)
     if rank == 0:
