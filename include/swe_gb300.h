@@ -52,9 +52,12 @@ typedef enum {
 typedef enum {
     SWE_FP64 = 0,          /* every step in double precision */
     SWE_SPLIT_BF16X3 = 1   /* Legendre GEMM on tcgen05 tensor cores with operands split
-                              into bf16 (hi, lo) pairs and FP32 accumulation; longitude
-                              FFT and grid products in FP32; spectral state, implicit
-                              solve and PinT correction in FP64 */
+                              into three bf16 terms (six partial products) and FP32
+                              accumulation; batches of at most 8 complex columns use an
+                              FP32 contraction with an FP32-rounded P table instead;
+                              longitude FFT, grid products, SL interpolation and the
+                              implicit-solve increments in FP32; Gauss nodes, P recurrence,
+                              spectral state and PinT correction in FP64 */
 } swe_precision;
 
 typedef enum {

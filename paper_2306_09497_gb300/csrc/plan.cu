@@ -233,6 +233,7 @@ extern "C" swe_status swe_plan_create(const swe_plan_desc* d, swe_plan_t* out) {
     }
     if (p->prec == SWE_SPLIT_BF16X3) {
         swe_status s2 = split_tables_build(p);
+        if (s2 == SWE_OK) s2 = small_tables_build(p);
         if (s2 != SWE_OK) {
             swe_plan_destroy(p);
             return s2;
@@ -256,6 +257,7 @@ extern "C" swe_status swe_plan_destroy(swe_plan_t p) {
     cudaFree(p->rc);
     cudaFree(p->rcf);
     split_tables_free(p);
+    small_tables_free(p);
     for (int i = 0; i < p->ncn; ++i) {
         cudaFree(p->cn[i].fac);
         cudaFree(p->cn[i].fac32);

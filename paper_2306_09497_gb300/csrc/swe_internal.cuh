@@ -123,8 +123,10 @@ struct swe_plan {
     float2* twf = nullptr;      // FP32 copy
     int nrad = 0;
     int rad[32];
-    // split-precision Legendre operands (bf16 hi/lo), built lazily
+    // split-precision Legendre operands: pre-split bf16 tiles for the tensor-core kernels,
+    // and an FP32 copy of P for narrow batches
     void* Pbf = nullptr;
+    float* Pf = nullptr;        // [ncx][nlat2]
     // implicit-solve factor cache
     CNFactor cn[16];
     int ncn = 0;
@@ -151,6 +153,12 @@ struct swe_plan {
 swe_status split_tables_build(swe_plan* p);
 void split_tables_free(swe_plan* p);
 int split_tables_error(const swe_plan* p, cudaStream_t st);
+// narrow batches (at most 8 complex columns) on split-precision plans (legendre_small.cu)
+swe_status small_tables_build(swe_plan* p);
+void small_tables_free(swe_plan* p);
+bool leg_small_ok(const swe_plan* p, int C);
+swe_status leg_inverse_small(const swe_plan* p, const float* X, float* F, int C, cudaStream_t st);
+swe_status leg_forward_small(const swe_plan* p, const float* F, float* Y, int C, cudaStream_t st);
 
 // plan helpers (plan.cu)
 swe_status plan_workspace(swe_plan* p, size_t bytes, char** out);

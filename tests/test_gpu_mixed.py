@@ -31,9 +31,11 @@ def mixed(request):
     plan.close()
 
 
-def test_split_sht_inverse(mixed):
+# 6 / 5 fields take the narrow-batch FP32 contraction (at most 8 complex columns), 20 the
+# tensor-core kernels
+@pytest.mark.parametrize("B", [6, 20])
+def test_split_sht_inverse(mixed, B):
     plan, s = mixed
-    B = 6
     coef = inputs.random_coeffs(s.M, B, seed=21)
     grid = torch.empty((B, s.nlat, s.nlon), dtype=torch.float32, device="cuda")
     plan.sht_inverse(_dev(coef), grid, B)
@@ -43,9 +45,9 @@ def test_split_sht_inverse(mixed):
         assert np.max(np.abs(got[b] - ref)) < 1e-6 * np.max(np.abs(ref))
 
 
-def test_split_sht_forward(mixed):
+@pytest.mark.parametrize("B", [5, 20])
+def test_split_sht_forward(mixed, B):
     plan, s = mixed
-    B = 5
     g = inputs.random_grid(s.nlat, s.nlon, B, seed=22)
     spec = torch.empty((B, plan.nc * 2), dtype=torch.float64, device="cuda")
     plan.sht_forward(torch.from_numpy(g.astype(np.float32)).cuda(), spec, B)
