@@ -18,9 +18,10 @@
 // Data movement: the Legendre operand (B) is pre-split and pre-tiled on the device
 // into the canonical no-swizzle K-major core-matrix layout and streamed into shared
 // memory by the bulk-copy engine (cp.async.bulk + mbarrier transaction counts);
-// the data operand (A) is prefetched a few chunks ahead by per-thread cp.async
-// (coalesced rows; 4 threads per column, each a quarter of the chunk), then split
-// in registers and stored in the same layout.  One elected thread issues
+// the FP32 rows of the data operand (A) arrive a few chunks ahead as 2-D TMA tensor
+// tiles issued by the control lane (per-thread cp.async when the row pitch is not a
+// multiple of 16 bytes), and the converter warps split them in registers (4 threads
+// per column, each a quarter of the chunk) and store the same layout.  One elected thread issues
 // tcgen05.mma (kind::f16, bf16 x bf16 -> f32, M = 128, K = 16) into two TMEM
 // accumulators (one per parity); a two-stage ring overlaps the split of chunk q+1
 // with the MMAs of chunk q; the epilogue reads TMEM with tcgen05.ld (16 warps,
@@ -192,15 +193,18 @@ struct TCShape {
 };
 
 // Both kernels run one warp-specialised pipeline over 16-deep K chunks q:
-//   converter warps 0-15 (4 threads per data column): cp.async their own column of chunk
-//     q + NR - 1 into the raw ring (only they read it back: no barrier), wait for the MMAs
-//     of chunk q - 2 to release bf16 stage q mod 2 (mbarrier "a_empty", signalled by
+//   converter warps 0-15 (4 threads per data column): wait for the raw FP32 rows of chunk
+//     q (TMA path: mbarrier "r_full" of raw stage q mod NR; cp.async path: each thread
+//     copies its own column NR - 1 chunks ahead, so only it reads it back), wait for the
+//     MMAs of chunk q - 2 to release bf16 stage q mod 2 (mbarrier "a_empty", signalled by
 //     tcgen05.commit), split chunk q into three bf16 planes there, fence the async proxy
 //     and arrive on "a_full" (one lane per warp);
-//   control warp 16, one lane: keeps the table tiles NB - 2 chunks ahead in an NB-deep ring
-//     (bulk copies on "b_full"; a stage is reused once "b_empty" says its MMAs are done),
-//     waits for "a_full" and "b_full" of chunk q, issues the 2 x 6 MMAs and commits them
-//     to "a_empty" and "b_empty"; after the last chunk it commits to "acc_full";
+//   control warp 16, one lane: on the TMA path issues the raw tiles of chunks 0 .. NR-1 and
+//     then those of chunk q + NR once "a_full" of chunk q shows stage q mod NR consumed;
+//     keeps the table tiles NB - 2 chunks ahead in an NB-deep ring (bulk copies on
+//     "b_full"; a stage is reused once "b_empty" says its MMAs are done), waits for
+//     "a_full" and "b_full" of chunk q, issues the 2 x 6 MMAs and commits them to
+//     "a_empty" and "b_empty"; after the last chunk it commits to "acc_full";
 //   then the converter warps read the accumulators (tcgen05.ld) and write the result.
 // There is no block barrier inside the loop.  Every wait is bounded; a thread that
 // gives up raises a shared abort flag that makes every other wait return at once, the
