@@ -63,7 +63,7 @@ VISC_SL = (2, 1.0e7)
 METRIC = "SWE slice-steps/s at T255"
 # DRAM bytes / algorithmic bytes of a kernel, from one ncu capture of that kernel (file under
 # profiles/); valid only while the kernel is unchanged since that capture
-NCU_TRAFFIC_RATIO = {"ring_nl_f32": (0.811, "profiles/ring_nl_lg_t255_s32.md (ncu, 32 slices, scaled per ring)")}
+NCU_TRAFFIC_RATIO = {"ring_nl_f32": (0.807, "profiles/ring_nl_lg_t255_s32.md (ncu, 32 slices, scaled per ring)")}
 FP64_PEAK_TFLOPS = 1.25           # nominal FP64 rate of GB300 (profiling recipe table)
 
 

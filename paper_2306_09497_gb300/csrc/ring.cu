@@ -594,15 +594,17 @@ __global__ void __launch_bounds__(128, 3) k_ring_nl_lg(const float2* __restrict_
     const int s0 = blockIdx.x * G;
     const int j = blockIdx.y;
     const int64_t C4 = 4 * (int64_t)S, C5 = 5 * (int64_t)S;
-    // stage the 4 input fields of the G rings: every copy in flight at once
-    for (int q = threadIdx.x; q < 4 * Mp * G; q += blockDim.x) {
-        const int g = q % G, fm = q / G;
-        const int m = fm % Mp, f = fm / Mp;
-        const bool ok = s0 + g < S;
-        cp_async8(&reg[g * RS + f * Mp + m], ok ? (const void*)&Fin[((int64_t)m * nlat + j) * C4 + (int64_t)f * S + s0 + g]
-                                                  : (const void*)Fin,
-                  ok);
-    }
+    // stage the 4 input fields of the G rings: every copy in flight at once (fields outermost,
+    // so that the mode index needs no division by M+1)
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+        for (int q = threadIdx.x; q < Mp * G; q += blockDim.x) {
+            const int g = q % G, m = q / G;
+            const bool ok = s0 + g < S;
+            cp_async8(&reg[g * RS + f * Mp + m],
+                      ok ? (const void*)&Fin[((int64_t)m * nlat + j) * C4 + (int64_t)f * S + s0 + g] : (const void*)Fin,
+                      ok);
+        }
     asm volatile("cp.async.commit_group;" ::: "memory");
     for (int k = threadIdx.x; k < 2 * H; k += blockDim.x) twN[k] = twg[k];
     fill_ring_tw<T>(tws, twg);
@@ -657,11 +659,14 @@ __global__ void __launch_bounds__(128, 3) k_ring_nl_lg(const float2* __restrict_
         }
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < 5 * Mp * G; q += blockDim.x) {
-        const int gg = q % G, fm = q / G;
-        const int m = fm % Mp, f = fm / Mp;
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
         const int slot = f == 0 ? 1 : (f == 1 ? 4 : (f == 2 ? 0 : (f == 3 ? 3 : 2)));
-        if (s0 + gg < S) Fout[((int64_t)m * nlat + j) * C5 + (int64_t)f * S + s0 + gg] = reg[gg * RS + slot * Mp + m];
+        for (int q = threadIdx.x; q < Mp * G; q += blockDim.x) {
+            const int gg = q % G, m = q / G;
+            if (s0 + gg < S)
+                Fout[((int64_t)m * nlat + j) * C5 + (int64_t)f * S + s0 + gg] = reg[gg * RS + slot * Mp + m];
+        }
     }
 }
 
