@@ -175,7 +175,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     per = max(5.0, 60.0 / max(1, args.steps + args.warmup))
-    vals = []
+    n_done, secs = 0, 0.0
     for _ in range(args.warmup):
         oracle_baseline(per / 2)
     for _ in range(args.steps):
@@ -183,11 +183,14 @@ def run_reference(args):
         if "error" in d:
             print(json.dumps({"impl": "reference", "unavailable": "oracle failed: " + d["error"][-200:]}))
             return 0
-        vals.append(d["value"])
-    v = sum(vals) / len(vals)
+        n_done += d["steps"]
+        secs += d["seconds"]
+    v = n_done / secs
+    # one bench step of this arm = one timed oracle sample of about `per` seconds
     line = {
-        "impl": "reference", "metric": METRIC, "value": v, "unit": "slice-steps/s", "n_gpus": 0,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v if v else None,
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "slice-steps/s", "n_gpus": world,
+        "hardware": "host CPU, one thread (the FP64 oracle); no GPU is used",
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_of(args),
         "cpu_baseline": {"value": v, "unit": "slice-steps/s", "cores": 1, "kind": "oracle",
