@@ -196,3 +196,47 @@ def test_sl_step_without_wind_is_crank_nicolson():
     b = sw.cn_step(U, 450.0)
     for f in range(3):
         assert np.max(np.abs(a[f] - b[f])) < 1e-12 * max(np.max(np.abs(b[f])), 1e-300) + 1e-300
+
+
+def test_nonlinear_terms_are_exactly_quadratic(t31):
+    """N of Eq. 1 (flux forms of N_Phi, N_xi, N_delta) is homogeneous of degree 2 in the state:
+    N(eps U) = eps^2 N(U).  A linear term left inside N (Phi_bar in the mass flux, f in the
+    vorticity flux; both belong to L) breaks this."""
+    s, sw = t31
+    U = (_rand_state(s, 41)[0], _rand_state(s, 42)[1], _rand_state(s, 43)[2])
+    N1 = sw.nonlinear(U)
+    for eps in (0.5, 3.0):
+        Ne = sw.nonlinear(tuple(eps * x for x in U))
+        for f in range(3):
+            assert np.max(np.abs(Ne[f] - eps ** 2 * N1[f])) <= 1e-12 * eps ** 2 * np.max(np.abs(N1[f]))
+
+
+def test_rigid_rotation_advects_geopotential_exactly(t31):
+    """u = u0 cos(lat), delta = 0: N_Phi = -div(Phi' V) = -(u0 / a) dPhi'/dlambda, i.e. -(i m u0 / a)
+    Phi'_mn, exactly on the 3/2 grid (Phi' u cos(lat) / cos^2(lat) = u0 Phi' is band-limited);
+    the zonal vorticity is not advected (N_xi = 0)."""
+    s, sw = t31
+    u0 = 20.0
+    xi = _solid_body(s, sw, u0)
+    phi = _rand_state(s, 44)[0]
+    N = sw.nonlinear((phi, xi, np.zeros_like(xi)))
+    ref = -1j * s.m * u0 / sw.p.a * phi * s.mask
+    assert np.max(np.abs(N[0] - ref)) <= 1e-12 * np.max(np.abs(ref))
+    assert np.max(np.abs(N[1])) <= 1e-12 * u0 / sw.p.a * np.max(np.abs(xi)) * s.M
+
+
+def test_zonal_flow_has_no_mass_or_vorticity_flux_divergence(t31):
+    """A zonal state (m = 0 only, delta = 0) has purely zonal fluxes Phi' V and xi V, whose
+    divergence is a lambda-derivative of a lambda-independent field: N_Phi = N_xi = 0, while
+    N_delta (the balance forcing) is not zero."""
+    s, sw = t31
+    R = _rand_state(s, 45)
+    phi = np.zeros_like(R[0])
+    xi = np.zeros_like(R[1])
+    phi[0, :] = R[0][0, :].real
+    xi[0, 1:] = R[1][0, 1:].real
+    N = sw.nonlinear((phi, xi, np.zeros_like(xi)))
+    scale = np.max(np.abs(N[2]))
+    assert scale > 0.0
+    assert np.max(np.abs(N[0])) <= 1e-12 * np.max(np.abs(phi)) * np.max(np.abs(xi)) * s.M
+    assert np.max(np.abs(N[1])) <= 1e-12 * scale
