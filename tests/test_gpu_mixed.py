@@ -219,3 +219,38 @@ def test_split_imex_large_batch_matches_oracle():
         ref = to_packed(s, sw.imex_step(tuple(Ud), dt, nu=nu, q=q))
         err = [np.sqrt(np.sum(w * np.abs(got[b, f] - ref[f]) ** 2) / np.sum(w * np.abs(ref[f]) ** 2)) for f in range(3)]
         assert err[0] < 1e-6 and err[1] < 1e-5 and err[2] < 1e-5, (b, err)
+
+
+def test_split_imex_bench_batch_sampled_slices():
+    """The benchmark's level-0 launch configuration: T255 (384 x 768), IMEX steps of
+    432000/7296 s on one 608-state chunk of the 1824-interval relaxation (tiled layout changes,
+    one-thread-per-chain implicit solve, lane-group ring kernel, TMA-fed tcgen05 GEMMs).
+    Slice s is the balanced base state shifted by s grid columns in longitude (f = 2 Omega mu
+    does not depend on longitude, and a shift by whole grid columns commutes with every grid
+    product), so the oracle runs once and each sampled slice is compared with the shifted
+    oracle result: Phi' 1e-6, xi and delta 1e-5 (Parseval-weighted relative L2)."""
+    from paper_2306_09497_gb300 import swe
+    M, nlat, nlon, S, nsteps = 255, 384, 768, 608, 3
+    dt = 432000.0 / 7296.0
+    s = Sphere(M, nlat, nlon)
+    sw = SWE(s)
+    xi, noise = inputs.initial_fields(M, 3)
+    xd = s.unpack(xi)
+    base = to_packed(s, (sw.balanced_geopotential(xd) + s.unpack(noise), xd, np.zeros_like(xd)))
+    m, _ = inputs.mn_arrays(M)
+    shift = lambda U, k: U * np.exp(-1j * m * (2.0 * np.pi * k / nlon))[None, :]
+    U0 = np.stack([shift(base, k) for k in range(S)])
+    plan = swe.Plan(M, nlat, nlon, prec=swe.SWE_SPLIT_BF16X3)
+    out = torch.empty((S, 3, plan.nc * 2), dtype=torch.float64, device="cuda")
+    plan.propagate(swe.stepper(swe.SWE_IMEX, dt, nsteps, 2, 0.0), _dev(U0), out, S)
+    got = out.cpu().numpy().view(np.complex128).reshape(S, 3, -1)
+    plan.close()
+    U = to_dense(s, base)
+    for _ in range(nsteps):
+        U = sw.imex_step(U, dt)
+    ref_base = to_packed(s, U)
+    w = np.where(m == 0, 1.0, 2.0)
+    for k in (0, 1, 307, S - 1):
+        ref = shift(ref_base, k)
+        err = [np.sqrt(np.sum(w * np.abs(got[k, f] - ref[f]) ** 2) / np.sum(w * np.abs(ref[f]) ** 2)) for f in range(3)]
+        assert err[0] < 1e-6 and err[1] < 1e-5 and err[2] < 1e-5, (k, err)
