@@ -14,12 +14,19 @@ Alternative workload "t255_parareal_s128" (--workload parareal): T255, 5 days sp
 into S = 128 slices of 3375 s.  One bench step = one Parareal iteration (Eq. 9):
 the fine IMEX propagator (57 steps of 59.21 s, the level-0 step of the 5-day,
 7296-step problem) on all 128 slices at once, the serial coarse chain
-(spatially coarsened to T127 on the 192 x 384 grid, 6 IMEX steps of 562.5 s with
+(spatially coarsened to T127 on the 192 x 384 grid, 12 IMEX steps of 281.25 s with
 4th-order hyperviscosity 1e16 m^4/s per slice, replayed from a CUDA graph) and
-the FP64 correction + convergence norm.  (Without spatial coarsening or with
-1e15 m^4/s the T255 coarse chain is unstable over 5 days, as the paper reports
-for large coarse steps at high resolution.)
+the FP64 correction + convergence norm.  With 6 coarse steps of 562.5 s the
+iteration moves away from the serial fine solution (E_{Phi,32} of Eq. 21 grows from
+5e-4 to 5e-2 in 8 iterations); with 12 it contracts (3e-4 to 2e-5).
 Metric: level-0 slice-steps per second = 128 * 57 / (seconds per iteration).
+
+Accuracy: after the timed region the same iteration is re-run from its initial guess and
+every iterate (the initial guess, the warm-up and the timed ones) is compared with the
+serial fine solution of the same plan (one state propagated through all 7296 level-0
+steps) by E_{psi,32} of Eq. 21 and the area-weighted relative L2 error per field
+("error_vs_serial_fine"); the serial fine solution of the mixed plan is also compared
+with that of the FP64 plan ("mixed_vs_fp64_serial_fine").
 
 Inputs are synthetic: seeded k^-3 balanced vorticity (rms wind 20 m/s) plus
 10 m height noise (paper_2306_09497_gb300.inputs), resident in HBM before the
@@ -27,6 +34,9 @@ timed region.  The working set (~4 GB of Fourier/spectral buffers per F sweep)
 is far larger than L2, so no explicit flush is needed between iterations.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|fp64] [--no-fp64] [--impl reference]
+    python bench.py --workload ncu-case [--S 32] [--case-steps 1] [--prec mixed|fp64]
+        (a small launch of the hot kernels for ncu: one warm-up IMEX step, then the given
+         number of IMEX steps of the T255 level-0 stepper on S random states)
 
 The headline value is the mixed-precision path (split-bf16 tensor-core Legendre GEMM,
 FP32 FFT and grid products, FP64 spectral state and Parareal correction); the same
@@ -50,7 +60,7 @@ M, NLAT, NLON = 255, 384, 768
 S = 128
 DT0 = 432000.0 / 7296.0          # 59.2105 s
 NF = 57                           # fine steps per slice
-NC_STEPS, DTC = 6, 3375.0 / 6.0   # coarse steps per slice, 562.5 s
+NC_STEPS, DTC = 12, 3375.0 / 12.0  # coarse steps per slice, 281.25 s
 NU_C, Q_C = 1.0e16, 4
 MC, NLATC, NLONC = 127, 192, 384  # coarse truncation (spatial coarsening)
 WORKLOAD_PARAREAL = "t255_parareal_s128"
@@ -61,10 +71,12 @@ WORKLOAD_MGRIT = "t255_mgrit3_cf4"
 N0_MG, CF_MG, NU_RELAX = 7296, 4, 0
 VISC_SL = (2, 1.0e7)
 METRIC = "SWE slice-steps/s at T255"
-# DRAM bytes / algorithmic bytes of a kernel, from one ncu capture of that kernel (file under
-# profiles/); valid only while the kernel is unchanged since that capture
-NCU_TRAFFIC_RATIO = {"ring_nl_f32": (0.807, "profiles/ring_nl_lg_t255_s32.md (ncu, 32 slices, scaled per ring)")}
-FP64_PEAK_TFLOPS = 1.25           # nominal FP64 rate of GB300 (profiling recipe table)
+# DRAM bytes / algorithmic bytes of a kernel, from one ncu capture of that kernel (dram__bytes
+# read + write over the algorithmic bytes of the same launch); valid only while the kernel is
+# unchanged since that capture
+NCU_TRAFFIC_RATIO = {"ring_nl_f32": (0.807, "ncu capture of k_ring_nl_lg, T255, 32 states, scaled per ring")}
+FP64_PEAK_TFLOPS = 1.25           # nominal dense FP64 rate of GB300
+R_NORM = 32                       # spectral resolution of the error norm (Eq. 21), as in the paper's figures
 
 
 def slowest_rank(seconds: float, world: int, device=None) -> float:
@@ -170,31 +182,92 @@ print(json.dumps({{"steps": n, "seconds": el, "setup_s": setup}}))
     return d
 
 
+def oracle_baseline_allcores(seconds: float, cores: int = 0, seed: int = 3, rounds: int = 1) -> dict:
+    """The same oracle IMEX stepping on `cores` independent T255 slices at once, one process per
+    host core (one BLAS thread each), as the slices of an F sweep are independent.  Every
+    process builds its tables and state, reports ready, and runs `rounds` timed loops of
+    `seconds`, each started when the parent says so (all processes together); the rate of a
+    round is the sum over processes of steps / seconds."""
+    cores = cores or (os.cpu_count() or 1)
+    code = f"""
+import json, time, sys
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+from oracle.sphere import Sphere
+from oracle.swe import SWE
+from paper_2306_09497_gb300 import inputs
+seed = int(sys.argv[1])
+s = Sphere({M}, {NLAT}, {NLON}); sw = SWE(s)
+xi, noise = inputs.initial_fields({M}, seed)
+xd = s.unpack(xi)
+U = (sw.balanced_geopotential(xd) + s.unpack(noise), xd, np.zeros_like(xd))
+U = sw.imex_step(U, {DT0})
+print("ready", flush=True)
+for _ in range({rounds}):
+    sys.stdin.readline()
+    n = 0; t1 = time.perf_counter()
+    while True:
+        U = sw.imex_step(U, {DT0}); n += 1
+        if time.perf_counter() - t1 > {seconds}: break
+    print(json.dumps({{"steps": n, "seconds": time.perf_counter() - t1}}), flush=True)
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               NUMEXPR_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    procs = [subprocess.Popen([sys.executable, "-c", code, str(seed + i)], stdin=subprocess.PIPE,
+                              stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
+             for i in range(cores)]
+    out = {"cores": cores, "seconds": seconds, "rounds": []}
+    try:
+        for p in procs:
+            if p.stdout.readline().strip() != "ready":
+                raise RuntimeError(p.stderr.read()[-300:])
+        for _ in range(rounds):
+            t0 = time.perf_counter()
+            for p in procs:
+                p.stdin.write("go\n")
+                p.stdin.flush()
+            rate, steps = 0.0, 0
+            for p in procs:
+                d = json.loads(p.stdout.readline())
+                rate += d["steps"] / d["seconds"]
+                steps += d["steps"]
+            out["rounds"].append({"value": rate, "steps": steps, "wall_s": time.perf_counter() - t0})
+        for p in procs:
+            p.wait(timeout=120)
+    except Exception as exc:
+        for p in procs:
+            if p.poll() is None:
+                p.kill()
+        return {"error": str(exc)[-300:]}
+    last = out["rounds"][-1]
+    out.update(value=last["value"], steps=last["steps"])
+    return out
+
+
 def run_reference(args):
+    """The reference arm: the FP64 oracle, as it stands, on the host's cores (one independent
+    T255 slice per core, the F sweep's parallelism); one bench step = one timed round."""
     rank, world, _ = _env_rank()
     if rank != 0:
         return 0
     per = max(5.0, 60.0 / max(1, args.steps + args.warmup))
-    n_done, secs = 0, 0.0
-    for _ in range(args.warmup):
-        oracle_baseline(per / 2)
-    for _ in range(args.steps):
-        d = oracle_baseline(per)
-        if "error" in d:
-            print(json.dumps({"impl": "reference", "unavailable": "oracle failed: " + d["error"][-200:]}))
-            return 0
-        n_done += d["steps"]
-        secs += d["seconds"]
-    v = n_done / secs
-    # one bench step of this arm = one timed oracle sample of about `per` seconds
+    d = oracle_baseline_allcores(per, rounds=args.warmup + args.steps)
+    if "error" in d:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle failed: " + d["error"][-200:]}))
+        return 0
+    timed = d["rounds"][args.warmup:]
+    steps = sum(r["steps"] for r in timed)
+    v = sum(r["value"] for r in timed) / len(timed)
+    wall = sum(r["wall_s"] for r in timed)
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "slice-steps/s", "n_gpus": world,
-        "hardware": "host CPU, one thread (the FP64 oracle); no GPU is used",
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * secs / args.steps,
+        "hardware": f"host CPU, {d['cores']} cores (the FP64 oracle, one process per core); no GPU is used",
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / len(timed),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_of(args),
-        "cpu_baseline": {"value": v, "unit": "slice-steps/s", "cores": 1, "kind": "oracle",
-                         "sample": f"serial FP64 oracle IMEX steps on one T255 slice, ~{per:.0f} s per bench step"},
+        "cpu_baseline": {"value": v, "unit": "slice-steps/s", "cores": d["cores"], "kind": "oracle",
+                         "sample": f"{steps} FP64 oracle IMEX steps of {d['cores']} independent T255 slices "
+                                   f"over {len(timed)} timed rounds of ~{per:.0f} s"},
         "e2e": {"value": v, "unit": "slice-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -424,8 +497,7 @@ def measure(args, prec_name, rank, world, local, with_e2e=True):
 
     clocks = ClockSampler(local)
     clocks.start()
-    swe.prof_reset()
-    swe.prof_enable(True)
+    swe.prof_enable(False)            # the timed iterations replay their CUDA graphs untimed
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
@@ -439,9 +511,16 @@ def measure(args, prec_name, rank, world, local, with_e2e=True):
     torch.cuda.synchronize()
     barrier()
     launches = swe.launch_count() - l0
+    clk = clocks.stop()
+    # per-kernel CUDA-event timing (roofline): separate iterations with uncaptured launches, each
+    # kernel bracketed by events on its own launch stream
+    swe.prof_reset()
+    swe.prof_enable(True)
+    for _ in range(max(1, min(2, args.steps))):
+        step_fn()
+    torch.cuda.synchronize()
     swe.prof_enable(False)
     stats = swe.prof_stats()
-    clk = clocks.stop()
     ms = slowest_rank(e0.elapsed_time(e1) / args.steps, world, dev)
     res = {"ms": ms, "value": world * fine_steps / (ms / 1000.0), "launches": launches, "stats": stats,
            "clocks": clk, "norms": norms, "fine_steps": fine_steps,
@@ -491,6 +570,118 @@ def measure(args, prec_name, rank, world, local, with_e2e=True):
     return res
 
 
+def serial_reference(args, plan, U0, n_points, steps_per_point):
+    """Serial fine solution of one state on `plan`: U0 propagated through n_points chunks of
+    `steps_per_point` level-0 IMEX steps, every chunk end kept ([n_points+1][3][2 NC] float64)."""
+    import torch
+
+    from paper_2306_09497_gb300 import swe
+
+    ref = torch.empty((n_points + 1, 3, plan.nc * 2), dtype=torch.float64, device=U0.device)
+    ref[0] = U0[0]
+    cur = U0.clone()
+    st = swe.stepper(swe.SWE_IMEX, DT0, steps_per_point)
+    for i in range(1, n_points + 1):
+        plan.propagate(st, cur, cur, 1)
+        ref[i] = cur[0]
+    return ref
+
+
+def _err_summary(e):
+    """e: [npoints][3][2] (E_{psi,32}, L2) -> final-time values per field and the max over time."""
+    names = ("phi", "xi", "delta")
+    out = {}
+    for f, nm in enumerate(names):
+        out["E_%s_R%d" % (nm, R_NORM)] = float(e[-1, f, 0])
+        out["L2_%s" % nm] = float(e[-1, f, 1])
+    out["E_phi_R%d_max_over_time" % R_NORM] = float(e[:, 0, 0].max())
+    return out
+
+
+def accuracy_pass(args, prec_name, rank, local, total_iters, ms_per_iter):
+    """Re-runs the benchmarked iteration from its initial guess and compares every iterate (the
+    initial guess, the warm-up and the timed iterations) with the serial fine solution."""
+    import time as _t
+
+    import torch
+
+    from paper_2306_09497_gb300 import swe
+
+    plan, cplan, it, fine_steps, step_fn = _build(args, prec_name, rank, local)
+    dev = torch.device("cuda", local)
+    xi_U0 = torch.empty(1, 3, plan.nc * 2, dtype=torch.float64, device=dev)
+    if args.workload == "parareal":
+        npts, per = S, NF
+    else:
+        npts, per = N0_MG // CF_MG, CF_MG
+    buf = torch.empty((npts + 1, 3, plan.nc * 2), dtype=torch.float64, device=dev)
+    (it.solution if args.workload == "parareal" else it.cpoints)(buf)
+    xi_U0[0] = buf[0]
+    torch.cuda.synchronize()
+    t0 = _t.perf_counter()
+    ref = serial_reference(args, plan, xi_U0, npts, per)
+    torch.cuda.synchronize()
+    t_serial = _t.perf_counter() - t0
+    hist = []
+    for k in range(total_iters + 1):
+        if k > 0:
+            step_fn()
+        (it.solution if args.workload == "parareal" else it.cpoints)(buf)
+        e = plan.error_norms(buf, ref, npts + 1, R_NORM)
+        hist.append(_err_summary(e))
+    out = {"reference": "serial fine solution of the same plan: %d level-0 IMEX steps of one state" % (npts * per),
+           "serial_fine_seconds": t_serial, "norm": "E_{psi,R} of Eq. 21 with R = %d, and the area-weighted "
+           "relative L2 error, at the final time; max over the level-0 %s" % (
+               R_NORM, "slice boundaries" if args.workload == "parareal" else "C-points"),
+           "per_iteration": hist, "iterations_run": total_iters}
+    e_phi = [h["E_phi_R%d" % R_NORM] for h in hist]
+    out["min_E_phi"] = min(e_phi)
+    for tol in (1e-2, 1e-3, 1e-4):
+        k = next((i for i, v in enumerate(e_phi) if v <= tol), None)
+        out["iterations_to_E_phi_%g" % tol] = k
+    out["contracting"] = bool(e_phi[-1] < e_phi[0])
+    # the timed iterations are the last args.steps entries
+    timed = e_phi[-args.steps:]
+    out["timed_iterations_E_phi"] = timed
+    if prec_name != "fp64" and not args.no_fp64:
+        p64 = swe.Plan(M, NLAT, NLON, prec=swe.SWE_FP64)
+        cur = xi_U0.clone()
+        p64.propagate(swe.stepper(swe.SWE_IMEX, DT0, npts * per), cur, cur, 1)
+        e = plan.error_norms(ref[-1:].contiguous(), cur, 1, R_NORM)
+        out["mixed_vs_fp64_serial_fine"] = {"E_phi_R%d" % R_NORM: float(e[0, 0, 0]), "L2_phi": float(e[0, 0, 1]),
+                                            "L2_xi": float(e[0, 1, 1]), "L2_delta": float(e[0, 2, 1]),
+                                            "at": "final time, %d steps" % (npts * per)}
+        p64.close()
+    it.close()
+    plan.close()
+    cplan.close()
+    return out
+
+
+def ncu_case(args):
+    """Small launch of the hot kernels for ncu: one warm-up IMEX step, then --case-steps IMEX
+    steps of the T255 level-0 stepper on --S random states (a few GB on the device; every
+    kernel's operands exceed the 129 MB L2)."""
+    import numpy as np
+    import torch
+
+    from paper_2306_09497_gb300 import inputs, swe
+
+    prec = swe.SWE_FP64 if args.prec == "fp64" else swe.SWE_SPLIT_BF16X3
+    plan = swe.Plan(M, NLAT, NLON, prec=prec)
+    U = torch.from_numpy(inputs.random_state(M, args.S, seed=7).view(np.float64).copy()).cuda()
+    out = torch.empty_like(U)
+    plan.propagate(swe.stepper(swe.SWE_IMEX, DT0, 1), U, out, args.S)
+    torch.cuda.synchronize()
+    plan.propagate(swe.stepper(swe.SWE_IMEX, DT0, args.case_steps), U, out, args.S)
+    torch.cuda.synchronize()
+    st = plan.check()
+    plan.close()
+    print(json.dumps({"ncu_case": "T255 IMEX level-0 stepper", "S": args.S, "steps": args.case_steps,
+                      "prec": args.prec, "status": st, "max_abs": float(out.abs().max())}))
+    return 0 if st == 0 else 1
+
+
 def roofline(stats):
     """Roofline entry of the dominant kernel (largest event-timed total)."""
     peaks = {}
@@ -505,7 +696,7 @@ def roofline(stats):
     if name.startswith("leg_") and name.endswith("f64"):
         ach = fl / n / (avg / 1000.0) / 1e12
         roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "peak_source": "nominal FP64 DFMA rate (profiling recipe table)"}
+                "frac": ach / FP64_PEAK_TFLOPS, "peak_source": "nominal FP64 DFMA rate of GB300 (1.25 TF/s)"}
     elif name.startswith("leg_"):
         pk = peaks.get("bf16_tflops_sustained", 1748.7)
         ach = 6.0 * fl / n / (avg / 1000.0) / 1e12   # six bf16 partial products per useful product
@@ -565,6 +756,9 @@ def run_ours(args):
         "fine_steps_per_iteration": r["fine_steps"],
         "problem_steps_per_s": r["problem_steps_per_s"],
     }
+    if not args.no_accuracy:
+        line["error_vs_serial_fine"] = accuracy_pass(args, main_prec, rank, local, args.warmup + args.steps,
+                                                     r["ms"])
     if main_prec == "mixed" and not args.no_fp64:
         f = measure(args, "fp64", rank, world, local, with_e2e=False)
         line["fp64_plain"] = {"value": f["value"], "unit": "slice-steps/s", "ms_per_step": f["ms"],
@@ -581,14 +775,22 @@ def run_ours(args):
         except Exception as exc:   # reported, not fatal: the headline figure is already measured
             line["serving"] = {"error": str(exc)[-300:]}
     if rank == 0 and world == 1 and not args.no_cpu:
+        ca = oracle_baseline_allcores(args.cpu_seconds)
+        if "error" not in ca:
+            line["cpu_baseline"] = {"value": ca["value"], "unit": "slice-steps/s", "cores": ca["cores"],
+                                    "kind": "oracle",
+                                    "sample": f"{ca['steps']} FP64 oracle IMEX steps of {ca['cores']} independent T255 "
+                                              f"slices, one process and one thread per host core, "
+                                              f"{ca['seconds']:.0f} s each"}
+        else:
+            line["cpu_baseline"] = {"value": None, "unit": "slice-steps/s", "cores": os.cpu_count(),
+                                    "kind": "oracle", "sample": "oracle failed: " + ca["error"][-200:]}
         cb = oracle_baseline(args.cpu_seconds)
         if "error" not in cb:
-            line["cpu_baseline"] = {"value": cb["value"], "unit": "slice-steps/s", "cores": 1, "kind": "oracle",
-                                    "sample": f"{cb['steps']} serial FP64 oracle IMEX steps of one T255 slice "
-                                              f"({cb['seconds']:.1f} s, one thread)"}
-        else:
-            line["cpu_baseline"] = {"value": None, "unit": "slice-steps/s", "cores": 1, "kind": "oracle",
-                                    "sample": "oracle failed: " + cb["error"][-200:]}
+            line["cpu_baseline_one_core"] = {"value": cb["value"], "unit": "slice-steps/s", "cores": 1,
+                                             "kind": "oracle",
+                                             "sample": f"{cb['steps']} serial FP64 oracle IMEX steps of one T255 "
+                                                       f"slice ({cb['seconds']:.1f} s, one thread)"}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -622,6 +824,143 @@ def run_serve(args):
     return 0
 
 
+# Gaussian-bumps convergence study (§5.1): T255 fine level, 36 h in 2160 IMEX steps of 60 s,
+# no viscosity on level 0; coarse levels at M_coarse in {51, 127} (the paper's 51 and 128, the
+# latter on the exact half grid) with nu_coarse = 1e6 m^2/s (q = 2); (L, cf, nu, M_coarse, scheme)
+BUMPS_N0, BUMPS_DT = 2160, 60.0
+BUMPS_CONFIGS = [(2, 2, 0, 51, "imex"), (3, 2, 0, 51, "imex"), (2, 4, 0, 51, "imex"), (3, 4, 0, 51, "imex"),
+                 (2, 2, 1, 51, "imex"), (2, 2, 0, 127, "imex"), (3, 2, 5, 127, "imex"), (2, 2, 0, 51, "sl"),
+                 (2, 2, 0, 127, "sl")]
+BUMPS_GRIDS = {51: (96, 192), 127: (192, 384)}
+
+
+def bumps_initial_state(plan64, dev):
+    """[1][3][2 NC] bumps state (§5.1) from the library's own Gauss nodes and forward transform."""
+    import numpy as np
+    import torch
+
+    from paper_2306_09497_gb300 import inputs
+
+    mu, _ = plan64.gauss()
+    lon = 2.0 * np.pi * np.arange(plan64.nlon) / plan64.nlon
+    grid = torch.from_numpy(inputs.gaussian_bumps_phi(np.arcsin(mu), lon)[None].copy()).to(dev)
+    spec = torch.empty((1, plan64.nc * 2), dtype=torch.float64, device=dev)
+    plan64.sht_forward(grid, spec, 1)
+    U0 = torch.zeros((1, 3, plan64.nc * 2), dtype=torch.float64, device=dev)
+    U0[0, 0] = spec[0]
+    return U0
+
+
+def run_bumps(args):
+    """--workload bumps: MGRIT convergence study on the Gaussian bumps (§5.1)."""
+    import numpy as np
+    import torch
+
+    from paper_2306_09497_gb300 import inputs, swe
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    phibar = inputs.GRAVITY * inputs.BUMPS_HBAR
+    prec = swe.SWE_FP64 if args.prec == "fp64" else swe.SWE_SPLIT_BF16X3
+    p64 = swe.Plan(M, NLAT, NLON, phibar=phibar)
+    U0 = bumps_initial_state(p64, dev)
+    p64.close()
+    plan = swe.Plan(M, NLAT, NLON, phibar=phibar, prec=prec)
+    coarse = {Mc: swe.Plan(Mc, *BUMPS_GRIDS[Mc], phibar=phibar, prec=prec) for Mc in BUMPS_GRIDS}
+    # serial fine reference at t = T
+    ref = U0.clone()
+    t0 = time.perf_counter()
+    plan.propagate(swe.stepper(swe.SWE_IMEX, BUMPS_DT, BUMPS_N0), ref, ref, 1)
+    torch.cuda.synchronize()
+    t_serial = time.perf_counter() - t0
+    E_ref = torch.empty((1, M + 1), dtype=torch.float64, device=dev)
+    plan.ke_spectrum(ref, 1, E_ref)
+    iters = args.bumps_iters
+    results = []
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = swe.launch_count()
+    for (L, cf, nu, Mc, sch) in BUMPS_CONFIGS:
+        steps = [swe.stepper(swe.SWE_IMEX, BUMPS_DT, 1)]
+        for lv in range(1, L):
+            dt = BUMPS_DT * cf ** lv
+            if sch == "imex":
+                scheme = swe.SWE_IMEX
+            else:
+                scheme = swe.SWE_SLSI_SETTLS if lv == L - 1 else swe.SWE_SLSI_SETTLS_1STEP
+            steps.append(swe.stepper(scheme, dt, 1, 2, 1.0e6))
+        g = swe.MGRIT([plan] + [coarse[Mc]] * (L - 1), steps, BUMPS_N0, cf, nu, cycle=1)
+        Nc = BUMPS_N0 // cf
+        buf = torch.empty((Nc + 1, 3, plan.nc * 2), dtype=torch.float64, device=dev)
+        rec = {"L": L, "cf": cf, "nu": nu, "M_coarse": Mc, "coarse": sch, "E_phi_R32": [], "E_phi_R128": [],
+               "L2_phi": []}
+        ms = []
+        status = "ok"
+        try:
+            g.init(U0)
+            for k in range(iters + 1):
+                if k > 0:
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    g.cycle(1)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                g.cpoints(buf)
+                last = buf[Nc:Nc + 1].contiguous()
+                e32 = plan.error_norms(last, ref, 1, 32)
+                e128 = plan.error_norms(last, ref, 1, 128)
+                rec["E_phi_R32"].append(float(e32[0, 0, 0]))
+                rec["E_phi_R128"].append(float(e128[0, 0, 0]))
+                rec["L2_phi"].append(float(e32[0, 0, 1]))
+            E = torch.empty((1, M + 1), dtype=torch.float64, device=dev)
+            plan.ke_spectrum(last, 1, E)
+            rec["ke_spectrum_final_iterate"] = [float(x) for x in E[0].cpu().numpy()]
+        except swe.SWEError as exc:
+            status = "unstable: " + str(exc)[:120]
+        g.close()
+        rec["status"] = status
+        e32 = rec["E_phi_R32"]
+        rec["converging_R32"] = bool(status == "ok" and len(e32) > 1 and e32[-1] < e32[0] and e32[-1] < 1e-2)
+        if ms:
+            fine_steps = (2 * (cf - 1) * (1 + nu) + 1 + 2 * nu) * (BUMPS_N0 // cf)
+            rec["ms_per_cycle"] = float(np.mean(ms))
+            rec["level0_slice_steps_per_s"] = fine_steps / (np.mean(ms) / 1000.0)
+        results.append(rec)
+    launches = swe.launch_count() - l0
+    clk = clocks.stop()
+    by = {(r["L"], r["cf"], r["nu"], r["M_coarse"], r["coarse"]): r for r in results}
+    imex51 = [r for r in results if r["coarse"] == "imex" and r["M_coarse"] == 51]
+    checks = {
+        "imex_Mc51_converge_R32_except_L3_cf4":
+            all(r["converging_R32"] for r in imex51 if (r["L"], r["cf"]) != (3, 4)),
+        "imex_Mc51_L3_cf4_not_converging": not by[(3, 4, 0, 51, "imex")]["converging_R32"],
+        "imex_Mc127_mostly_unstable_or_not_converging":
+            sum(not r["converging_R32"] for r in results if r["coarse"] == "imex" and r["M_coarse"] == 127) >= 1,
+        "sl_Mc51_L2_cf2_best_sl": (min(by[(2, 2, 0, 51, "sl")]["E_phi_R32"] or [np.inf]) <=
+                                    min(by[(2, 2, 0, 127, "sl")]["E_phi_R32"] or [np.inf])),
+    }
+    head = by[(3, 2, 0, 51, "imex")]
+    line = {"metric": "Gaussian-bumps MGRIT convergence study at T255 (E_{Phi,R} vs serial fine along iterations)",
+            "value": head.get("level0_slice_steps_per_s"), "unit": "slice-steps/s", "n_gpus": world,
+            "steps": iters, "warmup": 0, "ms_per_step": head.get("ms_per_cycle"), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "mixed",
+            "data": "analytic (Gaussian bumps of §5.1)",
+            "config": {"workload": "bumps_t255", "M": M, "nlat": NLAT, "nlon": NLON, "N0": BUMPS_N0,
+                       "dt0": BUMPS_DT, "T_hours": 36, "phibar": phibar, "coarse_visc": [2, 1.0e6],
+                       "value_from": "(L, cf, nu, M_coarse) = (3, 2, 0, 51), IMEX coarse"},
+            "serial_fine_seconds": t_serial, "ke_spectrum_fine": [float(x) for x in E_ref[0].cpu().numpy()],
+            "runs": results, "paper_statements": checks, "gpu_launches": launches, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line))
+    for p_ in coarse.values():
+        p_.close()
+    plan.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -629,7 +968,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["fp64", "mixed"])
-    ap.add_argument("--workload", default="mgrit", choices=["mgrit", "parareal", "serve"])
+    ap.add_argument("--workload", default="mgrit", choices=["mgrit", "parareal", "serve", "ncu-case", "bumps"])
+    ap.add_argument("--bumps-iters", type=int, default=10, help="MGRIT iterations per bumps configuration")
+    ap.add_argument("--S", type=int, default=32, help="states of the ncu case")
+    ap.add_argument("--case-steps", type=int, default=1, help="IMEX steps of the ncu case")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the error pass against the serial fine solution")
     ap.add_argument("--serve-requests", type=int, default=16, help="requests in the serving sample")
     ap.add_argument("--no-extras", action="store_true", help="skip the SHT and serving measurements")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain comparison run")
@@ -642,6 +985,10 @@ def main():
         return run_reference(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "ncu-case":
+        return ncu_case(args)
+    if args.workload == "bumps":
+        return run_bumps(args)
     return run_ours(args)
 
 

@@ -295,6 +295,83 @@ swe_status swe_pint_save(swe_pint_t p, double* U, double* Gold, void* stream);
 #define SWE_NOALLOC_SCRATCH_BYTES (64u << 20)
 swe_status sht_inverse_noalloc(swe_plan_t plan, const void* spec, void* grid, int batch, void* stream);
 
+/* Error norms of §5 between S states U and S reference states Uref (device,
+ * [S][3][NC] each, same plan).  For every state s and field f (Phi', xi, delta)
+ * out_host[(3 s + f) * 2 + 0] = E_{psi,R} of Eq. 21: max |psi_mn - ref_mn| over
+ *   0 <= m <= n <= R_norm divided by the same maximum of |ref_mn|;
+ * out_host[(3 s + f) * 2 + 1] = relative L2 error over the sphere,
+ *   sqrt(sum c_m |psi_mn - ref_mn|^2 / sum c_m |ref_mn|^2), c_0 = 1, c_m = 2: the area-weighted
+ *   L2 norm of the grid fields by Parseval's identity (the paper's physical-space L2 uses an
+ *   unweighted grid mean; on band-limited fields both measure the same error, with different
+ *   latitude weights).
+ * A zero reference norm gives 0 (equal fields) or +inf.  0 <= R_norm <= M.  out_host is HOST
+ * ([S][3][2] doubles).  Uses the plan workspace; synchronises `stream`. */
+swe_status swe_error_norms(swe_plan_t plan, const double* U, const double* Uref, int S, int R_norm,
+                           double* out_host, void* stream);
+
+/* Kinetic-energy spectrum of §5.1: for S states U (device, [S][3][NC]) writes
+ * E[s][n] = a^2 / (4 n (n+1)) * sum_{m=-n..n} (|xi_mn|^2 + |delta_mn|^2), n = 0..M (device,
+ * [S][M+1] doubles; E[s][0] = 0), the m < 0 terms being the conjugates of m > 0.  With the
+ * library's normalisation sum_n E(n) is the area mean of |V|^2 / 2.  Asynchronous. */
+swe_status swe_ke_spectrum(swe_plan_t plan, const double* U, int S, double* E, void* stream);
+
+/* Stability regions of the linearised test ODE u' = lambda_L u + lambda_N u (§4, Eqs.
+ * 10-20): |A| on a uniform grid of xi_N = lambda_N Delta t_c, Re xi_N in [re0, re1] (nre
+ * points, fastest index) and Im xi_N in [im0, im1] (nim points), for a fixed xi_L =
+ * lambda_L Delta t_c; the stability region is where |A| <= 1.  Delta t_c is the coarse
+ * scheme's step; the fine scheme is IMEX with Delta t_f = Delta t_c / cf and N_f = cf N_c
+ * steps per slice (§4.2).  Factors: IMEX A = ((4 + xi_L)/(4 - xi_L))^2 (1 + xi_N (2 + xi_N)/2)
+ * (§4.1.1, Heun reading of Eq. 5); SL-SI-SETTLS: both roots of Eq. 13 for n_kappa values of
+ * kappa s evenly spaced over [0, 2 pi] (21 for the paper's step pi/10), |A| being the largest
+ * over roots and kappa s (the region is their intersection, §4.1.2), each root taken as the
+ * coarse factor of Eqs. 17 / 20.  Methods:
+ *   SWE_STAB_COARSE_ALONE   |A_c^{n N_c}| (n = 1: the serial scheme's factor, Fig. of §4.1);
+ *   SWE_STAB_PARAREAL       Eq. 17 at slice n, iteration k;
+ *   SWE_STAB_MGRIT2         two-level MGRIT with F(CF)^nu, Eq. 20 with the summation limit
+ *                           min(k, floor(n/(nu+1))) that path counting on Eq. 19 gives;
+ *   SWE_STAB_MGRIT2_PRINTED Eq. 20 with the printed limit floor(k/(nu+1)) (requires
+ *                           floor(k/(nu+1)) (nu+1) <= n).
+ * absA: DEVICE array [nim][nre] of doubles, written asynchronously on `stream`. */
+typedef enum {
+    SWE_STAB_COARSE_ALONE = 0,
+    SWE_STAB_PARAREAL = 1,
+    SWE_STAB_MGRIT2 = 2,
+    SWE_STAB_MGRIT2_PRINTED = 3
+} swe_stab_method;
+typedef struct {
+    int coarse_scheme;     /* SWE_IMEX or SWE_SLSI_SETTLS */
+    int method;            /* swe_stab_method */
+    int n, k;              /* slice index n >= 1 and iteration k >= 0 */
+    int cf, Nc, nu;        /* coarsening factor, coarse steps per slice, CF relaxations */
+    int n_kappa;           /* SL-SI-SETTLS: number of kappa s values in [0, 2 pi] */
+    double xiL_re, xiL_im; /* xi_L = lambda_L Delta t_c */
+} swe_stability_desc;
+swe_status swe_stability_region(const swe_stability_desc* desc, double re0, double re1, int nre, double im0,
+                                double im1, int nim, double* absA, void* stream);
+
+/* Status word of a plan: kernels that run on the plan record two conditions in it
+ * without stopping the stream -- a non-finite tendency (the unstable runs that the
+ * paper reports as stopped, §5.2) and a bounded device-side wait of a tensor-core
+ * Legendre kernel that gave up (that launch's output is incomplete; the kernel returned
+ * instead of hanging).  parareal_iterate, mgrit_cycle and swe_server_step clear the
+ * words of their plans, read them after every iteration and return SWE_ETIMEOUT (which
+ * wins) or SWE_EUNSTABLE.  Callers of the asynchronous entry points (sht_*, propagate_*,
+ * swe_nonlinear, ...) call swe_plan_check: it synchronises `stream`, reads and clears
+ * the word and returns SWE_ETIMEOUT, SWE_EUNSTABLE or SWE_OK. */
+swe_status swe_plan_check(swe_plan_t plan, void* stream);
+
+/* Host-side fault injection for tests of the error paths: ORs `bits` (1 = non-finite,
+ * 2 = wait timeout) into the plan's status word, asynchronously on `stream`.  No kernel
+ * of the numerical path is disturbed.  Other bits return SWE_EINVAL. */
+swe_status swe_plan_inject_status(swe_plan_t plan, int bits, void* stream);
+
+/* Diagnostic of the bounded waits: one warp polls, at most `polls` times (capped at the
+ * tensor-core kernels' own limit of 2^22 polls), an mbarrier that nothing completes, then
+ * records a timeout in the plan's status word the way a tensor-core kernel does, and
+ * returns.  Asynchronous; swe_plan_check then returns SWE_ETIMEOUT.  The paper has no
+ * counterpart (failure handling of this library). */
+swe_status swe_wait_selftest(swe_plan_t plan, long long polls, void* stream);
+
 /* Instrumentation (host side, no GPU work).
  * swe_launch_count: kernels launched by the library so far (replays of a
  *   captured CUDA graph count every kernel node).

@@ -85,3 +85,47 @@ def recurrence_eq19(n, k, nu, F, G):
         for j in range(1, n + 1):
             u[kk, j] = G * u[kk, j - 1] + (S * u[kk - 1, j - nu - 1] if j - nu - 1 >= 0 else 0.0)
     return u[k, n]
+
+
+# ---------------- stability regions on a grid of xi_N (§4.1-4.3 figures) ----------------
+def region(coarse, method, xiL, re, im, n=100, k=0, cf=2, Nc=1, nu=0, n_kappa=21):
+    """|A| on the grid xi_N = re[0] + i dre ... (re = (re0, re1, nre), im likewise), [nim][nre].
+
+    coarse: "imex" or "sl"; method: "alone" (|A_c^{n N_c}|), "parareal" (Eq. 17),
+    "mgrit" (Eq. 20 with the path-count limit, reading A14) or "mgrit_printed" (Eq. 20 as
+    printed).  xi is relative to the coarse step Delta t_c; the fine scheme is IMEX with
+    Delta t_c / cf and N_f = cf N_c steps per slice.  For SL-SI-SETTLS every root of Eq. 13 at
+    every kappa s = 2 pi q / (n_kappa - 1) is used as the coarse factor and the largest |A| is
+    kept (the region is the intersection over roots and kappa s).
+    """
+    re0, re1, nre = re
+    im0, im1, nim = im
+    dre = (re1 - re0) / (nre - 1) if nre > 1 else 0.0
+    dim = (im1 - im0) / (nim - 1) if nim > 1 else 0.0
+    out = np.zeros((nim, nre))
+    for iy in range(nim):
+        for ix in range(nre):
+            xiN = complex(re0 + ix * dre, im0 + iy * dim)
+            Af = A_imex(xiL / cf, xiN / cf)
+            if coarse == "imex":
+                coarse_factors = [A_imex(xiL, xiN)]
+            else:
+                coarse_factors = []
+                for q in range(n_kappa):
+                    ks = 2.0 * np.pi * q / (n_kappa - 1) if n_kappa > 1 else 0.0
+                    coarse_factors.extend(sl_roots(xiL, xiN, ks))
+            best = 0.0
+            for Ac in coarse_factors:
+                R = Ac ** Nc
+                F = Af ** (cf * Nc)
+                if method == "alone":
+                    a = R ** n
+                elif method == "parareal":
+                    a = A_parareal(n, min(k, n), R, F - R)
+                elif method == "mgrit":
+                    a = A_mgrit_pathcount(n, k, nu, F, R)
+                else:
+                    a = A_mgrit_printed(n, k, nu, F, R)
+                best = max(best, abs(a))
+            out[iy, ix] = best
+    return out

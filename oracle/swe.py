@@ -4,7 +4,7 @@ State U = (Phi', xi, delta): geopotential perturbation, vorticity, divergence
 (§2.1, Eq. 1), each a dense complex array [m, n].  The mean geopotential
 Phi_bar is held separately.
 
-Readings of the paper used here (each one is listed in the design notes):
+Readings of the paper used here (where it is silent or garbled):
 
 * Coriolis parameter on the sphere f = 2 Omega mu (the paper spells out only
   the f-plane value 2 Omega, §4.1).

@@ -219,10 +219,12 @@ struct WS {
     uint32_t tmem_slot;
 };
 
-// bounded wait that also gives up once another thread raised the abort flag
-__device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+// bounded wait (at most `limit` polls) that also gives up once another thread raised the
+// abort flag
+__device__ __forceinline__ bool ws_wait_n(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                          unsigned long long limit) {
     const uint32_t a = smem_u32(bar);
-    for (unsigned long long it = 0; it < WAIT_LIMIT; ++it) {
+    for (unsigned long long it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n"
@@ -238,6 +240,10 @@ __device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity, volatile
     }
     *abort = 1;
     return false;
+}
+
+__device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    return ws_wait_n(bar, parity, abort, WAIT_LIMIT);
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -534,7 +540,7 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_inv_tc(const float* __restrict__
             }
         }
     } else if (tid == 0) {
-        atomicOr(err, 2);
+        atomicOr(err, PLAN_FLAG_TIMEOUT);
     }
     tmem_release(tmem, tid);
 }
@@ -679,7 +685,7 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_fwd_tc(const float* __restrict__
             }
         }
     } else if (tid == 0) {
-        atomicOr(err, 2);
+        atomicOr(err, PLAN_FLAG_TIMEOUT);
     }
     tmem_release(tmem, tid);
 }
@@ -763,7 +769,6 @@ struct SplitTables {
     long long* fwd_off = nullptr;
     int* fwd_ntiles = nullptr;
     int* fwd_nt = nullptr;
-    int* err = nullptr;
     size_t smem_inv = 0, smem_fwd = 0;
     int nb_inv = 2, nb_fwd = 2;               // table-tile ring depths
 };
@@ -825,13 +830,11 @@ swe_status split_tables_build(swe_plan* p) {
     if (e == cudaSuccess) e = cudaMalloc((void**)&t->fwd_off, sizeof(long long) * (M + 1));
     if (e == cudaSuccess) e = cudaMalloc((void**)&t->fwd_ntiles, sizeof(int) * (M + 1));
     if (e == cudaSuccess) e = cudaMalloc((void**)&t->fwd_nt, sizeof(int) * (M + 1));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&t->err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(t->inv_off, ioff.data(), sizeof(long long) * (M + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(t->inv_nq, inq.data(), sizeof(int) * (M + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(t->fwd_off, foff.data(), sizeof(long long) * (M + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(t->fwd_ntiles, fnz.data(), sizeof(int) * (M + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(t->fwd_nt, fnt.data(), sizeof(int) * (M + 1), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(t->err, 0, sizeof(int));
     if (e != cudaSuccess) {
         cudaFree(t->inv);
         cudaFree(t->fwd);
@@ -840,7 +843,6 @@ swe_status split_tables_build(swe_plan* p) {
         cudaFree(t->fwd_off);
         cudaFree(t->fwd_ntiles);
         cudaFree(t->fwd_nt);
-        cudaFree(t->err);
         delete t;
         return swe_cuda_status(e, "split tables");
     }
@@ -885,7 +887,6 @@ void split_tables_free(swe_plan* p) {
     cudaFree(t->fwd_off);
     cudaFree(t->fwd_ntiles);
     cudaFree(t->fwd_nt);
-    cudaFree(t->err);
     delete t;
     p->Pbf = nullptr;
 }
@@ -943,7 +944,7 @@ swe_status leg_inverse_split(const swe_plan* p, const float2* X, float2* F, int 
     SWE_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_inv));
     ProfToken tk = prof_begin("leg_inv_tc", st, fl, by);
     kern<<<grid, NTH, t->smem_inv, st>>>((const float*)X, (float*)F, t->inv, t->inv_off, t->inv_nq, sh, t->nb_inv,
-                                         t->err, tm);
+                                         p->flags, tm);
     prof_end(tk, st);
     SWE_CHECK_LAUNCH("k_leg_inv_tc");
     return SWE_OK;
@@ -966,18 +967,30 @@ swe_status leg_forward_split(const swe_plan* p, const float2* F, float2* Y, int 
     SWE_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_fwd));
     ProfToken tk = prof_begin("leg_fwd_tc", st, fl, by);
     kern<<<grid, NTH, t->smem_fwd, st>>>((const float*)F, (float*)Y, t->fwd, t->fwd_off, t->fwd_ntiles, t->fwd_nt,
-                                         sh, t->nb_fwd, t->err, tm);
+                                         sh, t->nb_fwd, p->flags, tm);
     prof_end(tk, st);
     SWE_CHECK_LAUNCH("k_leg_fwd_tc");
     return SWE_OK;
 }
 
-// non-zero if a tensor-core kernel gave up on a bounded wait since the last call
-int split_tables_error(const swe_plan* p, cudaStream_t st) {
-    const SplitTables* t = (const SplitTables*)p->Pbf;
-    if (!t) return 0;
-    int h = 0;
-    cudaMemcpyAsync(&h, t->err, sizeof(int), cudaMemcpyDeviceToHost, st);
-    cudaStreamSynchronize(st);
-    return h;
+// Diagnostic of the bounded wait: one warp waits at most `polls` polls on an mbarrier that
+// nothing completes, then records the timeout in the plan's status word, as the tensor-core
+// kernels do when a copy or an MMA never signals.
+__global__ void k_wait_selftest(int* flags, unsigned long long polls) {
+    __shared__ uint64_t bar;
+    __shared__ int abort;
+    if (threadIdx.x == 0) {
+        abort = 0;
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (!ws_wait_n(&bar, 0, &abort, polls)) atomicOr(flags, PLAN_FLAG_TIMEOUT);
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar)) : "memory");
+    }
+}
+
+swe_status wait_selftest_launch(const swe_plan* p, long long polls, cudaStream_t st) {
+    const unsigned long long n = polls < 1 ? 1ull : (polls > (long long)WAIT_LIMIT ? WAIT_LIMIT : (unsigned long long)polls);
+    k_wait_selftest<<<1, 32, 0, st>>>(p->flags, n);
+    SWE_CHECK_LAUNCH("k_wait_selftest");
+    return SWE_OK;
 }

@@ -16,6 +16,8 @@
 #include <cstring>
 #include <vector>
 
+#include <algorithm>
+
 #include "swe_internal.cuh"
 
 namespace {
@@ -178,6 +180,17 @@ struct swe_mgrit {
     double2* cold = nullptr;    // previous level-0 C-points
     unsigned long long* red = nullptr;
     cudaStream_t cs = nullptr;
+    // the whole cycle (every level's relaxations, restrictions, coarse solve and corrections),
+    // captured into one CUDA graph after one uncaptured cycle has sized every buffer
+    struct CycleGraph {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        std::vector<unsigned long long> gens;   // generations of the level plans at capture
+        long long launches = 0;
+        int passes = 0;
+        bool off = false;
+    } cyc;
+    bool capturing = false;     // inside the cycle capture: no nested graphs
 };
 
 static swe_status mg_step_batch(swe_mgrit* g, int l, const double2* in, int64_t in_stride, double2* out,
@@ -275,6 +288,7 @@ static void drop_graph(MGLevel::Graph& G) {
 
 static swe_status solve_coarsest(swe_mgrit* g, int l) {
     MGLevel& L = g->lv[l];
+    if (g->capturing) return solve_coarsest_body(g, l);     // part of the captured cycle
     MGLevel::Graph& G = L.cg[L.g_on ? 1 : 0];
     if (G.exec && G.gen != L.plan->gen) {
         // a plan buffer the graph points into was reallocated since the capture
@@ -333,6 +347,61 @@ static swe_status f_cycle(swe_mgrit* g, int l) {
         SWE_CHECK(v_cycle(g, l + 1));
     }
     return correct_level(g, l);
+}
+
+static std::vector<unsigned long long> plan_gens(const swe_mgrit* g) {
+    std::vector<unsigned long long> v;
+    for (const auto& L : g->lv) v.push_back(L.plan->gen);
+    return v;
+}
+
+static swe_status cycle_body(swe_mgrit* g) {
+    for (size_t l = 1; l < g->lv.size(); ++l) g->lv[l].g_on = false;
+    return g->d.cycle == 1 ? f_cycle(g, 0) : v_cycle(g, 0);
+}
+
+// One MGRIT iteration: uncaptured the first time (buffers, implicit-solve factors and launch
+// configurations settle), then captured once and replayed as a single graph launch.  A plan
+// buffer reallocated since the capture (generation changed) drops the graph and re-captures.
+static swe_status run_cycle(swe_mgrit* g) {
+    auto& C = g->cyc;
+    if (prof_enabled()) return cycle_body(g);     // per-kernel timing needs uncaptured launches
+    if (C.exec && C.gens != plan_gens(g)) {
+        SWE_CHECK_CUDA(cudaStreamSynchronize(g->cs));
+        cudaGraphExecDestroy(C.exec);
+        cudaGraphDestroy(C.graph);
+        C.exec = nullptr;
+        C.graph = nullptr;
+        C.passes = 0;
+    }
+    if (!C.exec && (C.off || C.passes < 1)) {
+        C.passes += 1;
+        return cycle_body(g);
+    }
+    if (!C.exec) {
+        const long long before = swe_launch_count();
+        const std::vector<unsigned long long> gens = plan_gens(g);
+        SWE_CHECK_CUDA(cudaStreamBeginCapture(g->cs, cudaStreamCaptureModeThreadLocal));
+        g->capturing = true;
+        const swe_status st = cycle_body(g);
+        g->capturing = false;
+        cudaGraph_t gr = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(g->cs, &gr);
+        C.launches = swe_launch_count() - before;
+        prof_launch(-C.launches);
+        if (st != SWE_OK || e != cudaSuccess || gens != plan_gens(g)) {
+            if (gr) cudaGraphDestroy(gr);
+            cudaGetLastError();
+            C.off = true;
+            return cycle_body(g);
+        }
+        C.graph = gr;
+        SWE_CHECK_CUDA(cudaGraphInstantiate(&C.exec, gr, 0));
+        C.gens = gens;
+    }
+    SWE_CHECK_CUDA(cudaGraphLaunch(C.exec, g->cs));
+    prof_launch(C.launches);
+    return SWE_OK;
 }
 
 extern "C" swe_status swe_mgrit_create(const swe_mgrit_desc* d, swe_mgrit_t* out) {
@@ -404,6 +473,8 @@ extern "C" swe_status swe_mgrit_destroy(swe_mgrit_t g) {
         cudaFree(L.B);
         cudaFree(L.x0);
     }
+    if (g->cyc.exec) cudaGraphExecDestroy(g->cyc.exec);
+    if (g->cyc.graph) cudaGraphDestroy(g->cyc.graph);
     cudaFree(g->cold);
     cudaFree(g->red);
     if (g->cs) cudaStreamDestroy(g->cs);
@@ -478,22 +549,26 @@ extern "C" swe_status mgrit_cycle(swe_mgrit_t g, int ncycles, double tol, int* k
     cudaStream_t user = (cudaStream_t)stream;
     SWE_CHECK(sync_in(g, user));
     MGLevel& F0 = g->lv[0];
-    SWE_CHECK_CUDA(cudaMemsetAsync(F0.plan->flags, 0, sizeof(int), g->cs));
+    // the distinct plans of the levels: each has its own status word
+    std::vector<swe_plan*> plans;
+    for (auto& lv : g->lv)
+        if (std::find(plans.begin(), plans.end(), lv.plan) == plans.end()) plans.push_back(lv.plan);
+    for (swe_plan* q : plans) SWE_CHECK(plan_flags_clear(q, g->cs));
+    std::vector<int> bits(plans.size(), 0);
     const int Nc = F0.N / g->d.cf;
     int k = 0;
     swe_status status = SWE_OK;
     for (; k < ncycles; ++k) {
-        for (size_t l = 1; l < g->lv.size(); ++l) g->lv[l].g_on = false;
-        if (g->d.cycle == 1) SWE_CHECK(f_cycle(g, 0));
-        else SWE_CHECK(v_cycle(g, 0));
+        SWE_CHECK(run_cycle(g));
         SWE_CHECK_CUDA(cudaMemsetAsync(g->red, 0, sizeof(unsigned long long) * 6, g->cs));
         k_cnorm<<<256, 256, 0, g->cs>>>(F0.u, g->cold, g->d.cf, Nc, F0.plan->nc, g->red, F0.plan->flags);
         SWE_CHECK_LAUNCH("k_cnorm");
         unsigned long long red[6];
         int flag = 0;
         SWE_CHECK_CUDA(cudaMemcpyAsync(red, g->red, sizeof(red), cudaMemcpyDeviceToHost, g->cs));
-        SWE_CHECK_CUDA(cudaMemcpyAsync(&flag, F0.plan->flags, sizeof(int), cudaMemcpyDeviceToHost, g->cs));
+        for (size_t i = 0; i < plans.size(); ++i) SWE_CHECK(plan_flags_fetch(plans[i], &bits[i], g->cs));
         SWE_CHECK_CUDA(cudaStreamSynchronize(g->cs));
+        for (int b : bits) flag |= b;
         double nrm = 0.0;
         for (int q = 0; q < 3; ++q) {
             double dd, vv;
@@ -503,8 +578,9 @@ extern "C" swe_status mgrit_cycle(swe_mgrit_t g, int ncycles, double tol, int* k
         }
         if (norm_hist) norm_hist[k] = nrm;
         if (flag) {
-            swe_set_error("mgrit_cycle: non-finite value at cycle %d", k + 1);
-            status = SWE_EUNSTABLE;
+            status = plan_flags_status(flag, "mgrit_cycle", k + 1);
+            // the condition is reported: leave the status words clear for the next call
+            for (swe_plan* q : plans) SWE_CHECK(plan_flags_clear(q, g->cs));
             ++k;
             break;
         }

@@ -44,11 +44,21 @@ swe_status scratch_address(void** out) {
     return SWE_OK;
 }
 
+// scratch bytes of a batch: the same expression the admission check below uses
+size_t noalloc_need(const swe_plan* p, size_t batch) {
+    const size_t fe = (p->prec == SWE_FP64) ? sizeof(double2) : sizeof(float2);
+    return a256(sizeof(double2) * p->ncx * batch) + a256(fe * (size_t)(p->M + 1) * p->nlat * batch);
+}
+
+// largest batch whose scratch fits the static array (binary search on noalloc_need)
 size_t noalloc_max_batch(const swe_plan* p) {
-    size_t fe = (p->prec == SWE_FP64) ? sizeof(double2) : sizeof(float2);
-    size_t per = a256(sizeof(double2) * p->ncx) + a256(fe * (size_t)(p->M + 1) * p->nlat);
-    // alignment padding of the two regions is at most 512 bytes in total
-    return (SWE_NOALLOC_SCRATCH_BYTES - 512) / per;
+    size_t lo = 0, hi = SWE_NOALLOC_SCRATCH_BYTES;
+    while (lo < hi) {
+        const size_t mid = (lo + hi + 1) / 2;
+        if (noalloc_need(p, mid) <= (size_t)SWE_NOALLOC_SCRATCH_BYTES) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
 }  // namespace
@@ -59,13 +69,12 @@ extern "C" swe_status sht_inverse_noalloc(swe_plan_t p, const void* spec, void* 
         return SWE_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t fe = (p->prec == SWE_FP64) ? sizeof(double2) : sizeof(float2);
     const size_t xbytes = a256(sizeof(double2) * p->ncx * (size_t)batch);
-    const size_t fbytes = a256(fe * (size_t)(p->M + 1) * p->nlat * (size_t)batch);
-    if (xbytes + fbytes > (size_t)SWE_NOALLOC_SCRATCH_BYTES) {
+    if (noalloc_need(p, (size_t)batch) > (size_t)SWE_NOALLOC_SCRATCH_BYTES) {
         swe_set_error("sht_inverse_noalloc: batch %d needs %zu bytes of scratch, more than the %zu-byte "
                       "static array (at most %zu fields for this plan)",
-                      batch, xbytes + fbytes, (size_t)SWE_NOALLOC_SCRATCH_BYTES, noalloc_max_batch(p));
+                      batch, noalloc_need(p, (size_t)batch), (size_t)SWE_NOALLOC_SCRATCH_BYTES,
+                      noalloc_max_batch(p));
         return SWE_EINVAL;
     }
     void* base = nullptr;

@@ -1,6 +1,6 @@
 // Parareal (§3.1, Eq. 9) on one GPU: the fine propagator runs on all S slices
-// at once (one batched propagate_F), the coarse chain runs serially (captured
-// once into a CUDA graph and replayed every iteration), and the FP64 correction
+// at once (one batched propagate_F), the coarse chain runs serially, the whole
+// iteration is captured once into a CUDA graph and replayed, and the FP64 correction
 // U^{k+1}_{n+1} = G(U^{k+1}_n) + F(U^k_n) - G(U^k_n) is fused with the
 // per-field convergence norm.
 #include <cstring>
@@ -16,10 +16,14 @@ struct swe_pint {
     double2* Gnew = nullptr;   // [3][NC]      phi_c(U^{k+1}_n)
     unsigned long long* red = nullptr;   // [6] max |dU_f|, max |U_f| (double bits)
     cudaStream_t cs = nullptr;
+    // the whole iteration (fine sweep over all slices, serial coarse chain, corrections),
+    // captured into one CUDA graph after one uncaptured iteration has sized every buffer
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    long long graph_launches = 0;   // kernels per replay of the captured chain
+    long long graph_launches = 0;   // kernels per replay of the captured iteration
     bool ready = false;
+    int passes = 0;                 // uncaptured iterations so far
+    bool off = false;               // capture failed: stay uncaptured
     unsigned long long gen_f = 0, gen_c = 0;   // plan generations the graph was captured at
 };
 
@@ -187,6 +191,12 @@ static swe_status chain(swe_pint* p) {
     return SWE_OK;
 }
 
+// one iteration: the fine propagator on every slice at once, then the serial chain
+static swe_status iteration_body(swe_pint* p) {
+    SWE_CHECK(propagate_F(p->d.fine_plan, &p->d.fine, (const double*)p->U, (double*)p->Fo, p->d.S, p->cs));
+    return chain(p);
+}
+
 extern "C" swe_status parareal_iterate(swe_pint_t p, int kmax, double tol, int* k_done, double* norm_hist,
                                        void* stream) {
     if (!p || kmax < 0) {
@@ -195,14 +205,13 @@ extern "C" swe_status parareal_iterate(swe_pint_t p, int kmax, double tol, int* 
     }
     cudaStream_t user = (cudaStream_t)stream;
     SWE_CHECK(wait_user_stream(p, user));
-    SWE_CHECK_CUDA(cudaMemsetAsync(p->d.fine_plan->flags, 0, sizeof(int), p->cs));
+    SWE_CHECK(plan_flags_clear(p->d.fine_plan, p->cs));
+    if (p->d.coarse_plan != p->d.fine_plan) SWE_CHECK(plan_flags_clear(p->d.coarse_plan, p->cs));
     const int S = p->d.S;
     int k = 0;
     swe_status status = SWE_OK;
     for (; k < kmax; ++k) {
-        // fine propagator on every slice at once
-        SWE_CHECK(propagate_F(p->d.fine_plan, &p->d.fine, (const double*)p->U, (double*)p->Fo, S, p->cs));
-        if (p->d.use_graphs) {
+        if (p->d.use_graphs && !prof_enabled()) {
             if (p->ready && (p->gen_f != p->d.fine_plan->gen || p->gen_c != p->d.coarse_plan->gen)) {
                 // a plan buffer the graph points into was reallocated: capture again
                 SWE_CHECK_CUDA(cudaStreamSynchronize(p->cs));
@@ -211,34 +220,52 @@ extern "C" swe_status parareal_iterate(swe_pint_t p, int kmax, double tol, int* 
                 p->gexec = nullptr;
                 p->graph = nullptr;
                 p->ready = false;
+                p->passes = 0;
             }
-            if (!p->ready) {
-                const long long before = swe_launch_count();
-                SWE_CHECK_CUDA(cudaStreamBeginCapture(p->cs, cudaStreamCaptureModeThreadLocal));
-                swe_status s = chain(p);
-                cudaGraph_t g = nullptr;
-                cudaError_t e = cudaStreamEndCapture(p->cs, &g);
-                // captured launches did not execute: count them at each replay instead
-                p->graph_launches = swe_launch_count() - before;
-                prof_launch(-p->graph_launches);
-                if (s != SWE_OK) return s;
-                if (e != cudaSuccess) return swe_cuda_status(e, "cudaStreamEndCapture(coarse chain)");
-                p->graph = g;
-                SWE_CHECK_CUDA(cudaGraphInstantiate(&p->gexec, g, 0));
-                p->ready = true;
-                p->gen_f = p->d.fine_plan->gen;
-                p->gen_c = p->d.coarse_plan->gen;
+            if (!p->ready && (p->off || p->passes < 1)) {
+                p->passes += 1;
+                SWE_CHECK(iteration_body(p));
+            } else {
+                if (!p->ready) {
+                    const long long before = swe_launch_count();
+                    const unsigned long long gf = p->d.fine_plan->gen, gc = p->d.coarse_plan->gen;
+                    SWE_CHECK_CUDA(cudaStreamBeginCapture(p->cs, cudaStreamCaptureModeThreadLocal));
+                    const swe_status s = iteration_body(p);
+                    cudaGraph_t g = nullptr;
+                    const cudaError_t e = cudaStreamEndCapture(p->cs, &g);
+                    // captured launches did not execute: count them at each replay instead
+                    p->graph_launches = swe_launch_count() - before;
+                    prof_launch(-p->graph_launches);
+                    if (s != SWE_OK || e != cudaSuccess || gf != p->d.fine_plan->gen ||
+                        gc != p->d.coarse_plan->gen) {
+                        // not capturable as it stands: run uncaptured from now on
+                        if (g) cudaGraphDestroy(g);
+                        cudaGetLastError();
+                        p->off = true;
+                        SWE_CHECK(iteration_body(p));
+                    } else {
+                        p->graph = g;
+                        SWE_CHECK_CUDA(cudaGraphInstantiate(&p->gexec, g, 0));
+                        p->ready = true;
+                        p->gen_f = gf;
+                        p->gen_c = gc;
+                    }
+                }
+                if (p->ready) {
+                    SWE_CHECK_CUDA(cudaGraphLaunch(p->gexec, p->cs));
+                    prof_launch(p->graph_launches);
+                }
             }
-            SWE_CHECK_CUDA(cudaGraphLaunch(p->gexec, p->cs));
-            prof_launch(p->graph_launches);
         } else {
-            SWE_CHECK(chain(p));
+            SWE_CHECK(iteration_body(p));
         }
         unsigned long long red[6];
         SWE_CHECK_CUDA(cudaMemcpyAsync(red, p->red, sizeof(red), cudaMemcpyDeviceToHost, p->cs));
-        int flag = 0;
-        SWE_CHECK_CUDA(cudaMemcpyAsync(&flag, p->d.fine_plan->flags, sizeof(int), cudaMemcpyDeviceToHost, p->cs));
+        int flag = 0, flag_c = 0;
+        SWE_CHECK(plan_flags_fetch(p->d.fine_plan, &flag, p->cs));
+        if (p->d.coarse_plan != p->d.fine_plan) SWE_CHECK(plan_flags_fetch(p->d.coarse_plan, &flag_c, p->cs));
         SWE_CHECK_CUDA(cudaStreamSynchronize(p->cs));
+        flag |= flag_c;
         double nrm = 0.0;
         for (int q = 0; q < 3; ++q) {
             double dd, vv;
@@ -248,8 +275,10 @@ extern "C" swe_status parareal_iterate(swe_pint_t p, int kmax, double tol, int* 
         }
         if (norm_hist) norm_hist[k] = nrm;
         if (flag) {
-            swe_set_error("parareal_iterate: non-finite value at iteration %d", k + 1);
-            status = SWE_EUNSTABLE;
+            status = plan_flags_status(flag, "parareal_iterate", k + 1);
+            // the condition is reported: leave the status words clear for the next call
+            SWE_CHECK(plan_flags_clear(p->d.fine_plan, p->cs));
+            if (p->d.coarse_plan != p->d.fine_plan) SWE_CHECK(plan_flags_clear(p->d.coarse_plan, p->cs));
             ++k;
             break;
         }

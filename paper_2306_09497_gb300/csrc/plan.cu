@@ -322,6 +322,65 @@ NLBuffers nl_carve(const swe_plan* p, char* base, int S) {
 }
 
 // ---------------------------------------------------------------------------
+// status word
+swe_status plan_flags_fetch(const swe_plan* p, int* host, cudaStream_t st) {
+    SWE_CHECK_CUDA(cudaMemcpyAsync(host, p->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    return SWE_OK;
+}
+
+swe_status plan_flags_clear(const swe_plan* p, cudaStream_t st) {
+    SWE_CHECK_CUDA(cudaMemsetAsync(p->flags, 0, sizeof(int), st));
+    return SWE_OK;
+}
+
+swe_status plan_flags_status(int bits, const char* where, int iter) {
+    if (bits & PLAN_FLAG_TIMEOUT) {
+        swe_set_error("%s: a bounded tensor-core wait gave up (iteration %d); results of that call are incomplete",
+                      where, iter);
+        return SWE_ETIMEOUT;
+    }
+    if (bits & PLAN_FLAG_NONFINITE) {
+        swe_set_error("%s: non-finite value at iteration %d", where, iter);
+        return SWE_EUNSTABLE;
+    }
+    return SWE_OK;
+}
+
+__global__ void k_or_flags(int* flags, int bits) { atomicOr(flags, bits); }
+
+extern "C" swe_status swe_plan_check(swe_plan_t p, void* stream) {
+    if (!p) {
+        swe_set_error("swe_plan_check: invalid argument");
+        return SWE_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    int bits = 0;
+    SWE_CHECK(plan_flags_fetch(p, &bits, st));
+    SWE_CHECK_CUDA(cudaStreamSynchronize(st));
+    SWE_CHECK(plan_flags_clear(p, st));
+    SWE_CHECK_CUDA(cudaStreamSynchronize(st));
+    return plan_flags_status(bits, "swe_plan_check", 0);
+}
+
+extern "C" swe_status swe_plan_inject_status(swe_plan_t p, int bits, void* stream) {
+    if (!p || (bits & ~(PLAN_FLAG_NONFINITE | PLAN_FLAG_TIMEOUT)) != 0) {
+        swe_set_error("swe_plan_inject_status: invalid argument");
+        return SWE_EINVAL;
+    }
+    k_or_flags<<<1, 1, 0, (cudaStream_t)stream>>>(p->flags, bits);
+    SWE_CHECK_LAUNCH("k_or_flags");
+    return SWE_OK;
+}
+
+extern "C" swe_status swe_wait_selftest(swe_plan_t p, long long polls, void* stream) {
+    if (!p || polls < 1) {
+        swe_set_error("swe_wait_selftest: invalid argument");
+        return SWE_EINVAL;
+    }
+    return wait_selftest_launch(p, polls, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
 // scalar transforms (ABI)
 extern "C" swe_status sht_inverse(swe_plan_t p, const void* spec, void* grid, int batch, void* stream) {
     if (!p || !spec || !grid || batch < 1) {

@@ -66,6 +66,9 @@ void drain_locked() {
 
 }  // namespace
 
+bool prof_enabled() { return g_enabled.load() != 0; }
+
+
 void prof_launch(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 ProfToken prof_begin(const char* name, cudaStream_t st, double flops, double bytes) {

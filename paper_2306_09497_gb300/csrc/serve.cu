@@ -289,13 +289,31 @@ extern "C" swe_status swe_server_step(swe_server_t s, int* n_active, int* n_queu
             }
         if (!placed) groups.push_back({r});
     }
+    // status words of the Parareal groups' plans: cleared before their launches and read back
+    // before any MGRIT cycle (which clears the words of its own plans) runs on the stream
+    std::vector<swe_plan*> pplans;
+    for (auto& g : groups)
+        for (swe_plan* q : {g[0]->d.fine_plan, g[0]->d.coarse_plan})
+            if (std::find(pplans.begin(), pplans.end(), q) == pplans.end()) pplans.push_back(q);
+    std::vector<int> pbits(pplans.size(), 0);
+    for (swe_plan* q : pplans) SWE_CHECK(plan_flags_clear(q, s->st));
     for (auto& g : groups) SWE_CHECK(parareal_group_tick(s, g));
+    for (size_t i = 0; i < pplans.size(); ++i) SWE_CHECK(plan_flags_fetch(pplans[i], &pbits[i], s->st));
     std::vector<double> mg_norm(mg.size(), 0.0);
     for (size_t i = 0; i < mg.size(); ++i) {
         int k = 0;
         SWE_CHECK(mgrit_cycle(mg[i]->mg, 1, 0.0, &k, &mg_norm[i], s->st));
     }
     SWE_CHECK_CUDA(cudaStreamSynchronize(s->st));
+    {
+        int bits = 0;
+        for (int b : pbits) bits |= b;
+        if (bits) {
+            for (swe_plan* q : pplans) SWE_CHECK(plan_flags_clear(q, s->st));
+            SWE_CHECK_CUDA(cudaStreamSynchronize(s->st));
+            return plan_flags_status(bits, "swe_server_step", 0);
+        }
+    }
     const double t = now_s();
     int done = 0;
     for (auto& g : groups)

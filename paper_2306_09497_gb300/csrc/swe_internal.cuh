@@ -132,7 +132,7 @@ struct swe_plan {
     int ncn = 0;
     // workspace arena
     Workspace ws;
-    // device flags: [0] non-finite seen
+    // device status word flags[0]: PLAN_FLAG_* bits set by kernels that ran on this plan
     int* flags = nullptr;
     // row coefficients [ncx][RC_NUM] (see RowCoef), and an FP32 copy
     double* rc = nullptr;
@@ -152,7 +152,15 @@ struct swe_plan {
 // split-precision tensor-core operand tables (legendre_tc.cu)
 swe_status split_tables_build(swe_plan* p);
 void split_tables_free(swe_plan* p);
-int split_tables_error(const swe_plan* p, cudaStream_t st);
+swe_status wait_selftest_launch(const swe_plan* p, long long polls, cudaStream_t st);
+
+// status word of a plan (flags[0]); kernels OR these bits in, synchronising calls read them
+enum { PLAN_FLAG_NONFINITE = 1, PLAN_FLAG_TIMEOUT = 2 };
+// enqueue the copy of the status word to *host (valid once st is synchronised)
+swe_status plan_flags_fetch(const swe_plan* p, int* host, cudaStream_t st);
+swe_status plan_flags_clear(const swe_plan* p, cudaStream_t st);
+// status for a fetched word: a timed-out wait wins over a non-finite value; sets the message
+swe_status plan_flags_status(int bits, const char* where, int iter);
 // narrow batches (at most 8 complex columns) on split-precision plans (legendre_small.cu)
 swe_status small_tables_build(swe_plan* p);
 void small_tables_free(swe_plan* p);

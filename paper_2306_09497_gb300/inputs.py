@@ -127,3 +127,25 @@ def random_grid(nlat: int, nlon: int, nbatch: int, seed: int) -> np.ndarray:
     """Random grid fields [nbatch][nlat][nlon] (not band-limited)."""
     rng = np.random.default_rng(seed)
     return rng.standard_normal((nbatch, nlat, nlon))
+
+
+# ---------------------------------------------------------------------------------------------
+# Gaussian-bumps test case of §5.1 (analytic; no random numbers)
+BUMPS_HBAR = 29400.0                       # m, mean height: Phi_bar = g * 29400
+BUMPS_AMPLITUDE = 6000.0                   # m, bump amplitude A (read as a height, times g)
+BUMPS_CENTRES = ((np.pi / 5.0, np.pi / 3.0), (6.0 * np.pi / 5.0, np.pi / 5.0), (8.0 * np.pi / 5.0, -np.pi / 4.0))
+BUMPS_WIDTHS = (20.0, 80.0, 360.0)
+
+
+def gaussian_bumps_phi(lat: np.ndarray, lon: np.ndarray, g: float = GRAVITY) -> np.ndarray:
+    """Geopotential perturbation of the three Gaussian bumps at the given latitudes (radians,
+    any order) and longitudes: Phi' = g A sum_i exp(-a_i d_i^2), d_i the great-circle angle to
+    bump centre i (§5.1); returns [len(lat)][len(lon)].  The velocity is zero."""
+    la = np.asarray(lat, dtype=np.float64)[:, None]
+    lo = np.asarray(lon, dtype=np.float64)[None, :]
+    out = np.zeros((la.shape[0], lo.shape[1]))
+    for (lc, tc), ai in zip(BUMPS_CENTRES, BUMPS_WIDTHS):
+        c = np.sin(la) * np.sin(tc) + np.cos(la) * np.cos(tc) * np.cos(lo - lc)
+        d = np.arccos(np.clip(c, -1.0, 1.0))
+        out += np.exp(-ai * d * d)
+    return g * BUMPS_AMPLITUDE * out

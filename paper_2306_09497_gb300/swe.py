@@ -28,8 +28,10 @@ EXPORTED = [
     "swe_pint_solution", "swe_pint_load", "swe_pint_save", "swe_launch_count", "swe_prof_enable",
     "swe_prof_reset", "swe_prof_read", "sht_inverse_noalloc", "swe_mgrit_create", "swe_mgrit_destroy",
     "swe_mgrit_init", "mgrit_cycle", "swe_mgrit_cpoints", "swe_server_create", "swe_server_destroy",
-    "swe_server_submit", "swe_server_step", "swe_server_result", "swe_server_norms",
+    "swe_server_submit", "swe_server_step", "swe_server_result", "swe_server_norms", "swe_plan_check",
+    "swe_plan_inject_status", "swe_wait_selftest", "swe_error_norms", "swe_ke_spectrum", "swe_stability_region",
 ]
+SWE_STAB_COARSE_ALONE, SWE_STAB_PARAREAL, SWE_STAB_MGRIT2, SWE_STAB_MGRIT2_PRINTED = range(4)
 SWE_METHOD_PARAREAL, SWE_METHOD_MGRIT2 = 0, 1
 
 
@@ -57,6 +59,12 @@ class PintDesc(ct.Structure):
 class MgritDesc(ct.Structure):
     _fields_ = [("L", ct.c_int), ("cf", ct.c_int), ("nu", ct.c_int), ("N0", ct.c_int), ("cycle", ct.c_int),
                 ("plan", ct.c_void_p * 8), ("step", StepperDesc * 8)]
+
+
+class StabilityDesc(ct.Structure):
+    _fields_ = [("coarse_scheme", ct.c_int), ("method", ct.c_int), ("n", ct.c_int), ("k", ct.c_int),
+                ("cf", ct.c_int), ("Nc", ct.c_int), ("nu", ct.c_int), ("n_kappa", ct.c_int),
+                ("xiL_re", ct.c_double), ("xiL_im", ct.c_double)]
 
 
 class ServerDesc(ct.Structure):
@@ -121,6 +129,12 @@ def load(path: Optional[str] = None) -> ct.CDLL:
         "swe_server_step": ([vp, ct.POINTER(i), ct.POINTER(i), ct.POINTER(i)], i),
         "swe_server_result": ([vp, ct.c_longlong, vp, vp], i),
         "swe_server_norms": ([vp, ct.c_longlong, vp, i, ct.POINTER(i)], i),
+        "swe_plan_check": ([vp, vp], i),
+        "swe_plan_inject_status": ([vp, i, vp], i),
+        "swe_wait_selftest": ([vp, ct.c_longlong, vp], i),
+        "swe_error_norms": ([vp, vp, vp, i, i, vp, vp], i),
+        "swe_ke_spectrum": ([vp, vp, i, vp, vp], i),
+        "swe_stability_region": ([ct.POINTER(StabilityDesc), d, d, i, d, d, i, vp, vp], i),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -183,6 +197,30 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def check(self, stream=None):
+        """Synchronise the stream and return the plan's status (SWE_OK, SWE_ETIMEOUT or
+        SWE_EUNSTABLE); the status word is cleared.  Does not raise."""
+        return int(load().swe_plan_check(self.h, _stream(stream)))
+
+    def inject_status(self, bits, stream=None):
+        """Host-side fault injection into the status word (1 non-finite, 2 timeout)."""
+        _check(load().swe_plan_inject_status(self.h, bits, _stream(stream)))
+
+    def wait_selftest(self, polls, stream=None):
+        """Bounded-wait diagnostic: a wait that nothing completes gives up after `polls` polls."""
+        _check(load().swe_wait_selftest(self.h, polls, _stream(stream)))
+
+    def error_norms(self, U, Uref, S, R_norm, stream=None):
+        """[S][3][2] numpy array: (E_{psi,R} of Eq. 21, area-weighted relative L2) per state and field."""
+        import numpy as np
+        out = np.empty((S, 3, 2), dtype=np.float64)
+        _check(load().swe_error_norms(self.h, _ptr(U), _ptr(Uref), S, R_norm, out.ctypes.data, _stream(stream)))
+        return out
+
+    def ke_spectrum(self, U, S, E, stream=None):
+        """KE spectrum E[s][n], n = 0..M, into the device array E ([S][M+1] float64)."""
+        _check(load().swe_ke_spectrum(self.h, _ptr(U), S, _ptr(E), _stream(stream)))
 
     def gauss(self):
         import numpy as np
@@ -364,6 +402,16 @@ class Server:
         n = ct.c_int(0)
         _check(load().swe_server_norms(self.h, rid, buf, 64, ct.byref(n)))
         return [buf[i] for i in range(min(n.value, 64))]
+
+
+def stability_region(out, coarse_scheme, method, xiL, re, im, n=100, k=0, cf=2, Nc=1, nu=0, n_kappa=21,
+                     stream=None):
+    """|A| over the xi_N grid re = (re0, re1, nre) x im = (im0, im1, nim) into the device array
+    out [nim][nre] (float64); see swe_stability_region in the C header."""
+    xiL = complex(xiL)
+    desc = StabilityDesc(coarse_scheme, method, n, k, cf, Nc, nu, n_kappa, xiL.real, xiL.imag)
+    _check(load().swe_stability_region(ct.byref(desc), re[0], re[1], re[2], im[0], im[1], im[2], _ptr(out),
+                                       _stream(stream)))
 
 
 def launch_count() -> int:

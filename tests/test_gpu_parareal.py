@@ -54,7 +54,11 @@ def test_parareal_t31_matches_oracle_and_serial_fine(use_graphs):
         ref = to_packed(s, hist[K][n])
         for f in range(3):
             assert _relL2(got[n, f], ref[f]) < 1e-10
-    # the update norms are finite and positive; slices n <= K are the serial fine solution
+    # Slices n <= K are the serial fine solution (finite termination, §3.1).  The update norm
+    # itself need not fall at every iteration (Parareal's amplification, Eq. 17, can exceed one
+    # for some modes before the finite-termination bound is reached), so only its finiteness
+    # is asserted here; convergence to the serial fine solution is asserted below and in
+    # test_parareal_t31_converges_to_serial_fine.
     assert all(np.isfinite(x) and x > 0 for x in norms)
     Uf = U0
     for n in range(K + 1):
@@ -89,5 +93,41 @@ def test_parareal_finite_termination_gpu():
         assert np.linalg.norm(a - b) <= 1e-13 * np.linalg.norm(b)
         plan.propagate(fine, cur, nxt, 1)
         cur, nxt = nxt, cur
+    pr.close()
+    plan.close()
+
+
+def test_parareal_t31_converges_to_serial_fine():
+    """Config 1 (T31, 8 slices over 12 h): at iteration k the first k slices equal the serial
+    fine solution, and after K = N = 8 iterations every slice equals it (finite termination,
+    §3.1)."""
+    from paper_2306_09497_gb300 import swe
+    M, nlat, nlon, S = 31, 48, 96, 8
+    fine = swe.stepper(swe.SWE_IMEX, 120.0, 45)
+    coarse = swe.stepper(swe.SWE_IMEX, 1080.0, 5)
+    plan = swe.Plan(M, nlat, nlon)
+    xi, noise = inputs.initial_fields(M, 1)
+    U0 = torch.empty(1, 3, plan.nc * 2, dtype=torch.float64, device="cuda")
+    plan.balance(_dev(xi[None]), _dev(noise[None]), U0, 1)
+    ref = torch.empty(S + 1, 3, plan.nc * 2, dtype=torch.float64, device="cuda")
+    ref[0] = U0[0]
+    cur = U0.clone()
+    for n in range(1, S + 1):
+        plan.propagate(fine, cur, cur, 1)
+        ref[n] = cur[0]
+    pr = swe.Parareal(plan, plan, fine, coarse, S)
+    pr.init(U0)
+    sol = torch.empty_like(ref)
+    errs = []
+    for k in range(S + 1):
+        if k > 0:
+            pr.iterate(1)
+        pr.solution(sol)
+        e = plan.error_norms(sol, ref, S + 1, M)           # [S+1][3][2]
+        for n in range(k + 1):
+            assert e[n, :, 1].max() <= 1e-12, (k, n, e[n])
+        errs.append(e[S, 0, 1])
+    assert errs[0] > 1e-6                                  # the coarse guess really differs
+    assert errs[-1] <= 1e-12
     pr.close()
     plan.close()
