@@ -108,6 +108,17 @@ int64_t swe_ncoef(int M);
 swe_status swe_plan_create(const swe_plan_desc* desc, swe_plan_t* out);
 swe_status swe_plan_destroy(swe_plan_t plan);
 
+/* Form of the geopotential tendency in N (Eq. 1).  SWE_NPHI_FLUX (the default): the
+ * analytically identical flux form -div(Phi' V), which conserves the global mean Phi'_00 to
+ * rounding.  SWE_NPHI_ADVECTIVE: Eq. 1 as written, -V.grad(Phi') - Phi' delta, with
+ * grad Phi' synthesised from its spectral derivatives and the products taken on the grid;
+ * it costs six extra inverse scalar transforms and one forward transform per nonlinear
+ * evaluation, with the grid fields in device memory.  Applies to every later nonlinear
+ * evaluation on the plan (swe_nonlinear, the IMEX stepper, propagate_*, PinT); the
+ * SL-SI-SETTLS scheme uses N_R = -Phi' delta only and is unaffected.  Host-side setting. */
+typedef enum { SWE_NPHI_FLUX = 0, SWE_NPHI_ADVECTIVE = 1 } swe_nphi_form;
+swe_status swe_plan_set_nphi_form(swe_plan_t plan, int form);
+
 /* Copies the Gauss-Legendre nodes mu_j (north to south) and weights w_j into
  * HOST arrays of nlat doubles.  Synchronises. */
 swe_status swe_plan_gauss(swe_plan_t plan, double* mu_host, double* w_host);
@@ -224,15 +235,24 @@ swe_status mgrit_cycle(swe_mgrit_t g, int ncycles, double tol, int* k_done, doub
 swe_status swe_mgrit_cpoints(swe_mgrit_t g, double* U_out, void* stream);
 
 /* Continuous-batching forecast server.  A request is a Parareal (§3.1) or two-level
- * MGRIT (§3.2) solve of one initial state; requests queue FIFO and are admitted at the
- * start of a swe_server_step call while fewer than max_active run and the device memory
- * they need fits in hbm_budget_bytes.  Each step advances every active request by one
- * iteration / cycle.  Parareal requests with the same plans and steppers share their
- * launches: all their slices go through one fine propagation, and their serial coarse
- * chains advance together (one batched coarse step per chain position); requests
- * admitted later join at the next step.  Every kernel treats state columns
- * independently, so a result does not depend on the other requests in the batch.
- * State stays in device memory from admission until swe_server_result. */
+ * MGRIT (§3.2) solve of one initial state; requests queue FIFO and are admitted at the start
+ * of a swe_server_step call while fewer than max_active run and the device memory they are
+ * charged (swe_request_bytes: their state, staging for their slices and the plan workspace
+ * their batched propagations need) fits in hbm_budget_bytes.  Each step advances every
+ * active request by one iteration / cycle and synchronises once.  Requests that share a plan
+ * run in one lane (one CUDA stream, in order); lanes run concurrently, so requests of
+ * different truncations with their own plans overlap on the device (give coarse levels plan
+ * objects of their own for that).  Parareal requests with the same plans and steppers
+ * share their launches: all their slices go through one fine propagation, their serial
+ * coarse chains advance together (one batched coarse step per chain position), and the
+ * initial coarse chains of requests admitted together are batched the same way.  State
+ * stays in device memory from admission until swe_server_result.  On FP64 plans a result
+ * equals the request's result alone up to rounding (relative 1e-12); on split-precision
+ * plans the batch width selects the Legendre kernel (narrow FP32 contraction for at most 8
+ * complex columns, tcgen05 GEMM above) and the implicit-solve kernel, so a result in a mix
+ * equals the result alone within the split-precision tolerance (full height 1e-6), not bit
+ * for bit.  A non-finite value or a timed-out wait in any active request fails the step
+ * (SWE_EUNSTABLE / SWE_ETIMEOUT). */
 typedef struct swe_server* swe_server_t;
 typedef enum { SWE_METHOD_PARAREAL = 0, SWE_METHOD_MGRIT2 = 1 } swe_method;
 typedef struct {
@@ -252,6 +272,8 @@ typedef struct {
 } swe_request_desc;
 
 swe_status swe_server_create(const swe_server_desc* desc, swe_server_t* out);
+/* Device memory the server charges to a request while it is held (HOST *bytes). */
+swe_status swe_request_bytes(const swe_request_desc* req, size_t* bytes);
 swe_status swe_server_destroy(swe_server_t s);
 /* Queues a request; *id receives its handle.  Host-side only. */
 swe_status swe_server_submit(swe_server_t s, const swe_request_desc* req, long long* id);

@@ -40,10 +40,17 @@ class Physics:
 
 
 class SWE:
-    """Operators of Eq. 1 on a given Sphere (dense spectral arrays)."""
+    """Operators of Eq. 1 on a given Sphere (dense spectral arrays).
 
-    def __init__(self, sph: Sphere, phys: Physics = Physics()):
+    nphi_form selects the geopotential tendency of N: "flux" evaluates -div(Phi' V) (the
+    default, mass-conserving form), "advective" evaluates Eq. 1 as written,
+    -V.grad(Phi') - Phi' delta, with grad Phi' synthesised from its spectral derivatives.
+    """
+
+    def __init__(self, sph: Sphere, phys: Physics = Physics(), nphi_form: str = "flux"):
+        assert nphi_form in ("flux", "advective")
         self.s, self.p = sph, phys
+        self.nphi_form = nphi_form
         M = sph.M
         m, n = sph.m, sph.n
         e_n = eps(m, n)              # eps_n^m
@@ -202,11 +209,34 @@ class SWE:
         Ug, Vg = s.uv_to_grid(s.inv_lap(xi), s.inv_lap(de))
         Pg = s.sh_to_grid(Phi)
         Xg = s.sh_to_grid(xi)
-        divP, _ = s.div_curl_from_grid(Pg * Ug, Pg * Vg)
         divX, curlX = s.div_curl_from_grid(Xg * Ug, Xg * Vg)
         ke = (Ug * Ug + Vg * Vg) / (2.0 * s.coslat2[:, None])
         KE = s.grid_to_sh(ke)
-        return (-divP, -divX, curlX - s.lap(KE))
+        if self.nphi_form == "flux":
+            divP, _ = s.div_curl_from_grid(Pg * Ug, Pg * Vg)
+            NPhi = -divP
+        else:
+            NPhi = self.nphi_advective(U, Ug, Vg, Pg)
+        return (NPhi, -divX, curlX - s.lap(KE))
+
+    def nphi_advective(self, U, Ug=None, Vg=None, Pg=None):
+        """Geopotential tendency in the advective form of Eq. 1, -V.grad(Phi') - Phi' delta.
+
+        With U = u cos(lat), V = v cos(lat):
+        V.grad(Phi') = [U dPhi'/dlambda + V (1 - mu^2) dPhi'/dmu] / (a (1 - mu^2)),
+        the derivatives synthesised exactly from the spectral coefficients (i m P and the
+        H = (1 - mu^2) dP/dmu table), the products and the forward projection on the grid.
+        """
+        s = self.s
+        Phi, xi, de = U
+        if Ug is None:
+            Ug, Vg = s.uv_to_grid(s.inv_lap(xi), s.inv_lap(de))
+            Pg = s.sh_to_grid(Phi)
+        Plam = s.fourier_to_grid(np.einsum("mnj,mn->jm", s.P, 1j * s.m * Phi))
+        Pmu = s.fourier_to_grid(np.einsum("mnj,mn->jm", s.H, Phi))
+        Dg = s.sh_to_grid(de)
+        adv = (Ug * Plam + Vg * Pmu) / (self.p.a * s.coslat2[:, None])
+        return s.real_m0(s.grid_to_sh(-adv - Pg * Dg))
 
     def nonlinear_R_grid(self, U):
         """N_R of Eq. 1 on the grid: -Phi' delta (geopotential component only)."""

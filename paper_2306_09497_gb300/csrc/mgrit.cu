@@ -594,6 +594,25 @@ extern "C" swe_status mgrit_cycle(swe_mgrit_t g, int ncycles, double tol, int* k
     return status;
 }
 
+// One cycle enqueued behind `user` without synchronising the host: the cycle, the C-point norm
+// reduction and the copies of its six reduction words (red_host, pinned host memory) and of the
+// levels' status words (bits_host[0..L-1]) all follow `user`'s prior work, and `user` waits for
+// them; the host values are valid once `user` is synchronised.  Used by the server, which
+// synchronises once per tick for all its requests.
+swe_status mgrit_cycle_enqueue(swe_mgrit* g, cudaStream_t user, unsigned long long* red_host, int* bits_host) {
+    SWE_CHECK(sync_in(g, user));
+    MGLevel& F0 = g->lv[0];
+    for (auto& L : g->lv) SWE_CHECK(plan_flags_clear(L.plan, g->cs));
+    const int Nc = F0.N / g->d.cf;
+    SWE_CHECK(run_cycle(g));
+    SWE_CHECK_CUDA(cudaMemsetAsync(g->red, 0, sizeof(unsigned long long) * 6, g->cs));
+    k_cnorm<<<256, 256, 0, g->cs>>>(F0.u, g->cold, g->d.cf, Nc, F0.plan->nc, g->red, F0.plan->flags);
+    SWE_CHECK_LAUNCH("k_cnorm");
+    SWE_CHECK_CUDA(cudaMemcpyAsync(red_host, g->red, sizeof(unsigned long long) * 6, cudaMemcpyDeviceToHost, g->cs));
+    for (size_t l = 0; l < g->lv.size(); ++l) SWE_CHECK(plan_flags_fetch(g->lv[l].plan, &bits_host[l], g->cs));
+    return sync_out(g, user);
+}
+
 extern "C" swe_status swe_mgrit_cpoints(swe_mgrit_t g, double* U_out, void* stream) {
     if (!g || !U_out) {
         swe_set_error("swe_mgrit_cpoints: invalid argument");

@@ -145,6 +145,8 @@ __global__ void k_row_coef(int M, double a, double* rc, float* rcf) {
         c[RC_P] = n >= 1 ? (n + 1.0) / n * en : 0.0;
         c[RC_Q] = n >= 1 ? n / (n + 1.0) * en1 : 0.0;
         c[RC_R] = n >= 1 ? (double)m / ((double)n * (n + 1.0)) : 0.0;
+        c[RC_GM] = (n - 1 >= m) ? -(n - 1.0) * en : 0.0;
+        c[RC_GP] = (n + 2.0) * en1;
         for (int k = 0; k < RC_NUM; ++k) rcf[(ex_off(m, M) + (n - m)) * RC_NUM + k] = (float)c[k];
     }
 }
@@ -299,11 +301,21 @@ swe_status plan_workspace(swe_plan* p, size_t bytes, char** out) {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// extra workspace of the advective geopotential tendency (zero in the flux form)
+static size_t nphi_bytes(const swe_plan* p, int S) {
+    if (!p->nphi_adv) return 0;
+    const size_t fe = (p->prec == SWE_FP64) ? sizeof(double2) : sizeof(float2);
+    const size_t re = fe / 2;
+    const size_t four = (size_t)(p->M + 1) * p->nlat, grid = (size_t)p->nlat * p->nlon;
+    return align256(fe * p->ncx * 6 * S) + align256(fe * four * 6 * S) + align256(re * grid * 6 * S) +
+           align256(fe * four * S) + align256(fe * p->ncx * S);
+}
+
 size_t nl_bytes(const swe_plan* p, int S) {
     size_t fe = (p->prec == SWE_FP64) ? sizeof(double2) : sizeof(float2);
     size_t four = (size_t)(p->M + 1) * p->nlat;
     return align256(sizeof(double2) * p->ncx * 4 * S) + align256(fe * four * 4 * S) +
-           align256(fe * four * 5 * S) + align256(sizeof(double2) * p->ncx * 5 * S);
+           align256(fe * four * 5 * S) + align256(sizeof(double2) * p->ncx * 5 * S) + nphi_bytes(p, S);
 }
 
 NLBuffers nl_carve(const swe_plan* p, char* base, int S) {
@@ -318,7 +330,35 @@ NLBuffers nl_carve(const swe_plan* p, char* base, int S) {
     b.Fout = c;
     c += align256(fe * four * 5 * S);
     b.Y = (double2*)c;
+    c += align256(sizeof(double2) * p->ncx * 5 * S);
+    b.X2 = nullptr;
+    b.F2 = b.G2 = b.F3 = nullptr;
+    b.Y2 = nullptr;
+    if (p->nphi_adv) {
+        const size_t re = fe / 2, grid = (size_t)p->nlat * p->nlon;
+        b.X2 = (double2*)c;
+        c += align256(fe * p->ncx * 6 * S);
+        b.F2 = c;
+        c += align256(fe * four * 6 * S);
+        b.G2 = c;
+        c += align256(re * grid * 6 * S);
+        b.F3 = c;
+        c += align256(fe * four * S);
+        b.Y2 = (double2*)c;
+    }
     return b;
+}
+
+extern "C" swe_status swe_plan_set_nphi_form(swe_plan_t p, int form) {
+    if (!p || (form != SWE_NPHI_FLUX && form != SWE_NPHI_ADVECTIVE)) {
+        swe_set_error("swe_plan_set_nphi_form: invalid argument");
+        return SWE_EINVAL;
+    }
+    if (p->nphi_adv != form) {
+        p->nphi_adv = form;
+        p->gen += 1;          // workspace layout changed: captured graphs are stale
+    }
+    return SWE_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -230,7 +230,8 @@ __global__ void k_nl_pre_kernel(StateView U, double2* __restrict__ X, const int*
 __global__ void k_nl_post_kernel(const double2* __restrict__ Y, int mode, double dt, const double2* __restrict__ in0,
                                  const double2* __restrict__ in1, double2* __restrict__ out0,
                                  double2* __restrict__ out1, const int* __restrict__ srow_m, int M, int64_t nc, int S,
-                                 double ia, const double* __restrict__ rc, int* flags) {
+                                 double ia, const double* __restrict__ rc, int* flags,
+                                 const double2* __restrict__ Yphi) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= nc * S) return;
     int s = (int)(t % S);
@@ -250,7 +251,8 @@ __global__ void k_nl_post_kernel(const double2* __restrict__ Y, int mode, double
     const double cp = c[RC_DCP], cm = c[RC_DCM], ma = m * ia;
     // div = i m A/a + n eps_{n+1} B_{n+1}/a - (n+1) eps_n B_{n-1}/a ; curl likewise (A <-> B, sign)
     double2 N[3];
-    N[0] = make_double2(-fma(cp, B2p.x, fma(-cm, B2m.x, -ma * A2.y)), -fma(cp, B2p.y, fma(-cm, B2m.y, ma * A2.x)));
+    N[0] = Yphi ? Yphi[rx * S + s]       // advective form, already a scalar transform
+                : make_double2(-fma(cp, B2p.x, fma(-cm, B2m.x, -ma * A2.y)), -fma(cp, B2p.y, fma(-cm, B2m.y, ma * A2.x)));
     N[1] = make_double2(-fma(cp, B1p.x, fma(-cm, B1m.x, -ma * A1.y)), -fma(cp, B1p.y, fma(-cm, B1m.y, ma * A1.x)));
     const double ke = (double)(n * (n + 1)) * ia * ia;
     N[2] = make_double2(fma(cm, A1m.x, fma(-cp, A1p.x, fma(ke, KE.x, -ma * B1.y))),
@@ -599,7 +601,7 @@ __device__ __forceinline__ void flag_nonfinite_f(int* flags, float2 v) {
 __global__ void k_nl_post_f32(const float2* __restrict__ Y, int mode, float dt, const double2* __restrict__ in0,
                               const double2* __restrict__ in1, double2* __restrict__ out0,
                               double2* __restrict__ out1, const int* __restrict__ srow_m, int M, int64_t nc, int S,
-                              float ia, const float* __restrict__ rcf, int* flags) {
+                              float ia, const float* __restrict__ rcf, int* flags, const float2* __restrict__ Yphi) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= nc * S) return;
     int s = (int)(t % S);
@@ -618,7 +620,8 @@ __global__ void k_nl_post_f32(const float2* __restrict__ Y, int mode, float dt, 
     const float* c = rcf + rx * RC_NUM;
     const float cp = c[RC_DCP], cm = c[RC_DCM], ma = (float)m * ia;
     float2 N[3];
-    N[0] = make_float2(-fmaf(cp, B2p.x, fmaf(-cm, B2m.x, -ma * A2.y)), -fmaf(cp, B2p.y, fmaf(-cm, B2m.y, ma * A2.x)));
+    N[0] = Yphi ? Yphi[rx * S + s]       // advective form, already a scalar transform
+                : make_float2(-fmaf(cp, B2p.x, fmaf(-cm, B2m.x, -ma * A2.y)), -fmaf(cp, B2p.y, fmaf(-cm, B2m.y, ma * A2.x)));
     N[1] = make_float2(-fmaf(cp, B1p.x, fmaf(-cm, B1m.x, -ma * A1.y)), -fmaf(cp, B1p.y, fmaf(-cm, B1m.y, ma * A1.x)));
     const float ke = (float)(n * (n + 1)) * ia * ia;
     N[2] = make_float2(fmaf(cm, A1m.x, fmaf(-cp, A1p.x, fmaf(ke, KE.x, -ma * B1.y))),
@@ -1028,16 +1031,17 @@ swe_status k_nl_pre(const swe_plan* p, const double2* Ua, const double2* Ub, dou
     return SWE_OK;
 }
 swe_status k_nl_post(const swe_plan* p, const double2* Y, int mode, double dt, const double2* in0, const double2* in1,
-                     double2* out0, double2* out1, int S, cudaStream_t st) {
+                     double2* out0, double2* out1, int S, cudaStream_t st, const double2* Yphi) {
     const double ye = (p->prec == SWE_FP64) ? 16.0 : 8.0;   // bytes per operand element
     ProfToken tk_ = prof_begin("nl_post", st, 0.0, S * (ye * 5.0 * p->ncx + 16.0 * 3.0 * p->nc * (in1 ? 4.0 : 3.0)));
     if (p->prec == SWE_FP64) {
         k_nl_post_kernel<<<nblk(p->nc * S), 256, 0, st>>>(Y, mode, dt, in0, in1, out0, out1, p->srow_m, p->M, p->nc, S,
-                                                          1.0 / p->a, p->rc, p->flags);
+                                                          1.0 / p->a, p->rc, p->flags, Yphi);
     } else {
         k_nl_post_f32<<<nblk(p->nc * S), 256, 0, st>>>(reinterpret_cast<const float2*>(Y), mode, (float)dt, in0, in1,
                                                        out0, out1, p->srow_m, p->M,
-                                                       p->nc, S, (float)(1.0 / p->a), p->rcf, p->flags);
+                                                       p->nc, S, (float)(1.0 / p->a), p->rcf, p->flags,
+                                                       reinterpret_cast<const float2*>(Yphi));
     }
     prof_end(tk_, st);
     SWE_CHECK_LAUNCH("k_nl_post");

@@ -40,7 +40,8 @@ swe_status nonlinear_soa(swe_plan* p, const double2* Ua, const double2* Ub, doub
     SWE_CHECK(leg_inverse(p, b.X, b.Fin, 4 * S, st));
     SWE_CHECK(ring_nonlinear(p, b.Fin, b.Fout, S, st));
     SWE_CHECK(leg_forward(p, b.Fout, b.Y, 5 * S, st));
-    SWE_CHECK(k_nl_post(p, b.Y, POST_N, 0.0, nullptr, nullptr, N, nullptr, S, st));
+    if (p->nphi_adv) SWE_CHECK(nphi_adv_eval(p, Ua, Ub, beta, b, S, st));
+    SWE_CHECK(k_nl_post(p, b.Y, POST_N, 0.0, nullptr, nullptr, N, nullptr, S, st, b.Y2));
     return SWE_OK;
 }
 
@@ -57,13 +58,15 @@ static swe_status imex_step(swe_plan* p, double dt, double nu, int q, double2* U
     SWE_CHECK(leg_inverse(p, b.X, b.Fin, 4 * S, st));
     SWE_CHECK(ring_nonlinear(p, b.Fin, b.Fout, S, st));
     SWE_CHECK(leg_forward(p, b.Fout, b.Y, 5 * S, st));
-    SWE_CHECK(k_nl_post(p, b.Y, POST_STAGE1, dt, Us, nullptr, Ub, T, S, st));
+    if (p->nphi_adv) SWE_CHECK(nphi_adv_eval(p, Us, nullptr, 0.0, b, S, st));
+    SWE_CHECK(k_nl_post(p, b.Y, POST_STAGE1, dt, Us, nullptr, Ub, T, S, st, b.Y2));
     // U** = U* + (Ubar + dt N(U* + Ubar)) / 2   -> written into U (no longer needed)
     SWE_CHECK(k_nl_pre(p, T, nullptr, 0.0, b.X, S, st));
     SWE_CHECK(leg_inverse(p, b.X, b.Fin, 4 * S, st));
     SWE_CHECK(ring_nonlinear(p, b.Fin, b.Fout, S, st));
     SWE_CHECK(leg_forward(p, b.Fout, b.Y, 5 * S, st));
-    SWE_CHECK(k_nl_post(p, b.Y, POST_STAGE2, dt, Us, Ub, U, nullptr, S, st));
+    if (p->nphi_adv) SWE_CHECK(nphi_adv_eval(p, T, nullptr, 0.0, b, S, st));
+    SWE_CHECK(k_nl_post(p, b.Y, POST_STAGE2, dt, Us, Ub, U, nullptr, S, st, b.Y2));
     // U^{n+1} = CN(dt/4) U**, then backward-Euler viscosity
     SWE_CHECK(k_implicit(p, alpha, 1, U, T, dt, nu, q, S, st));
     *out = T;
@@ -136,6 +139,12 @@ static int chunk_cols(const swe_plan* p, int S) {
     int c = (int)(budget / per);
     if (c < 1) c = 1;
     return S < c ? S : c;
+}
+
+// plan workspace one propagation of S states claims (one chunk's staging and stepper buffers)
+size_t stepper_bytes_chunked(const swe_plan* p, int S) {
+    const int cols = chunk_cols(p, S);
+    return state_bytes(p, cols) + stepper_bytes(p, cols);
 }
 
 static swe_status propagate_impl(swe_plan* p, const swe_stepper_desc* sd, const double* U_in, double* U_out, int S,

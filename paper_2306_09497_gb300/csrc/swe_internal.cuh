@@ -59,7 +59,9 @@ enum RowCoef {
     RC_P = 5,     // p_n = (n+1)/n eps_n
     RC_Q = 6,     // q_n = n/(n+1) eps_{n+1}
     RC_R = 7,     // r_n = m/(n(n+1))
-    RC_NUM = 8
+    RC_GM = 8,    // -(n-1) eps_n        ((1 - mu^2) d/dmu of a scalar: weight of its n-1 coefficient)
+    RC_GP = 9,    // (n+2) eps_{n+1}     (weight of its n+1 coefficient)
+    RC_NUM = 10
 };
 
 // FP64 <-> FP32 conversions on the integer pipe.  GB300 executes the hardware conversion
@@ -142,6 +144,8 @@ struct swe_plan {
     void* thx = nullptr;
     // launch configuration of the fused nonlinear ring kernel (autotuned on first large call)
     int ring_cfg = -1, ring_G = 1;
+    // geopotential tendency of N: 0 flux form -div(Phi' V), 1 advective form -V.grad Phi' - Phi' delta
+    int nphi_adv = 0;
     // bumped whenever a plan-owned device buffer is allocated, grown or freed after creation
     // (workspace, implicit-solve factors, SL geometry): a CUDA graph that captured pointers
     // into the plan is valid only while the generation it was captured at is current
@@ -179,6 +183,12 @@ struct NLBuffers {
     void* Fin;      // [M+1][nlat][4S] Fourier coefficients (double2 or float2)
     void* Fout;     // [M+1][nlat][5S]
     double2* Y;     // [ncx][5S]    forward-transform results (A1, B1, A2, B2, KE)
+    // advective geopotential tendency only (plan nphi_adv), else null:
+    double2* X2;    // [ncx][6S]    operands U, V, Phi', delta, dPhi'/dlambda, (1 - mu^2) dPhi'/dmu
+    void* F2;       // [M+1][nlat][6S] Fourier coefficients of those
+    void* G2;       // [6S][nlat][nlon] grid fields (double or float); slot 0 later holds N_Phi
+    void* F3;       // [M+1][nlat][S]  Fourier coefficients of N_Phi
+    double2* Y2;    // [ncx][S]     N_Phi coefficients (rows n <= M used)
 };
 size_t nl_bytes(const swe_plan* p, int S);
 NLBuffers nl_carve(const swe_plan* p, char* base, int S);
@@ -215,7 +225,12 @@ enum { POST_N = 0, POST_STAGE1 = 1, POST_STAGE2 = 2 };
 //   POST_STAGE1: out0 <- dt N (=Ubar), out1 <- in0 + dt N  (in0 = U*)
 //   POST_STAGE2: out0 <- in0 + (in1 + dt N) / 2            (in0 = U*, in1 = Ubar)
 swe_status k_nl_post(const swe_plan* p, const double2* Y, int mode, double dt, const double2* in0,
-                     const double2* in1, double2* out0, double2* out1, int S, cudaStream_t st);
+                     const double2* in1, double2* out0, double2* out1, int S, cudaStream_t st,
+                     const double2* Yphi = nullptr);
+// advective-form geopotential tendency of U_a + beta U_b into b.Y2 (nphi_adv.cu); k_nl_post then
+// takes N_Phi from b.Y2 instead of the flux divergence
+swe_status nphi_adv_eval(const swe_plan* p, const double2* Ua, const double2* Ub, double beta, const NLBuffers& b,
+                         int S, cudaStream_t st);
 
 // implicit solve (SoA). If with_rhs, R = (I + alpha L) U is formed first (Crank-Nicolson).
 // Viscosity factor [1 + dt nu (n(n+1)/a^2)^{q/2}]^{-1} applied to the result if nu > 0.
@@ -236,6 +251,8 @@ swe_status sl_step(swe_plan* p, double dt, double nu, int q, const double2* Upre
 // stepper (stepper.cu), SoA state with S columns; U updated in place
 swe_status stepper_run(swe_plan* p, const swe_stepper_desc* sd, double2* U, int S, cudaStream_t st);
 size_t stepper_bytes(const swe_plan* p, int S);
+// plan workspace one propagation of S states claims (batches are chunked to bound it)
+size_t stepper_bytes_chunked(const swe_plan* p, int S);
 // S states at in + s*in_stride (AoS, strides in states) advanced by sd; written to out + s*out_stride,
 // plus add + s*add_stride when add != nullptr.  in and out may alias with equal strides.
 swe_status propagate_strided(swe_plan* p, const swe_stepper_desc* sd, const double2* in, int64_t in_stride,
@@ -243,6 +260,10 @@ swe_status propagate_strided(swe_plan* p, const swe_stepper_desc* sd, const doub
                              cudaStream_t st);
 swe_status nonlinear_soa(swe_plan* p, const double2* Ua, const double2* Ub, double beta,
                          double2* N, int S, char* ws, cudaStream_t st);
+
+// one MGRIT cycle enqueued behind `user` without a host synchronisation (mgrit.cu); red_host: 6
+// pinned words (max |du|, max |u| per field, double bits), bits_host: one status word per level
+swe_status mgrit_cycle_enqueue(swe_mgrit* g, cudaStream_t user, unsigned long long* red_host, int* bits_host);
 
 // Parareal correction of one slice boundary (pint.cu)
 swe_status parareal_correct_launch(const double2* G, const double2* F, double2* Gold, double2* Unext, int64_t nc,

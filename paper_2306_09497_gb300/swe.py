@@ -30,7 +30,9 @@ EXPORTED = [
     "swe_mgrit_init", "mgrit_cycle", "swe_mgrit_cpoints", "swe_server_create", "swe_server_destroy",
     "swe_server_submit", "swe_server_step", "swe_server_result", "swe_server_norms", "swe_plan_check",
     "swe_plan_inject_status", "swe_wait_selftest", "swe_error_norms", "swe_ke_spectrum", "swe_stability_region",
+    "swe_request_bytes", "swe_plan_set_nphi_form",
 ]
+SWE_NPHI_FLUX, SWE_NPHI_ADVECTIVE = 0, 1
 SWE_STAB_COARSE_ALONE, SWE_STAB_PARAREAL, SWE_STAB_MGRIT2, SWE_STAB_MGRIT2_PRINTED = range(4)
 SWE_METHOD_PARAREAL, SWE_METHOD_MGRIT2 = 0, 1
 
@@ -135,6 +137,8 @@ def load(path: Optional[str] = None) -> ct.CDLL:
         "swe_error_norms": ([vp, vp, vp, i, i, vp, vp], i),
         "swe_ke_spectrum": ([vp, vp, i, vp, vp], i),
         "swe_stability_region": ([ct.POINTER(StabilityDesc), d, d, i, d, d, i, vp, vp], i),
+        "swe_request_bytes": ([ct.POINTER(RequestDesc), ct.POINTER(ct.c_size_t)], i),
+        "swe_plan_set_nphi_form": ([vp, i], i),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -197,6 +201,10 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def set_nphi_form(self, form):
+        """SWE_NPHI_FLUX (default) or SWE_NPHI_ADVECTIVE geopotential tendency (see the C header)."""
+        _check(load().swe_plan_set_nphi_form(self.h, form))
 
     def check(self, stream=None):
         """Synchronise the stream and return the plan's status (SWE_OK, SWE_ETIMEOUT or
@@ -381,6 +389,15 @@ class Server:
         _check(load().swe_server_submit(self.h, ct.byref(d), ct.byref(rid)))
         self._keep[rid.value] = (S, fine_plan.nc)
         return rid.value
+
+    @staticmethod
+    def request_bytes(fine_plan: Plan, coarse_plan: Plan, method: int, fine: StepperDesc, coarse: StepperDesc,
+                      S: int, iters: int = 1, U0_host=None, cf: int = 1, nu_relax: int = 0) -> int:
+        """Device memory the server charges to such a request (swe_request_bytes)."""
+        d = RequestDesc(fine_plan.h.value, coarse_plan.h.value, method, fine, coarse, S, cf, nu_relax, iters, None)
+        n = ct.c_size_t(0)
+        _check(load().swe_request_bytes(ct.byref(d), ct.byref(n)))
+        return n.value
 
     def step(self):
         a, q, dn = ct.c_int(0), ct.c_int(0), ct.c_int(0)

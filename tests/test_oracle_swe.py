@@ -240,3 +240,57 @@ def test_zonal_flow_has_no_mass_or_vorticity_flux_divergence(t31):
     assert scale > 0.0
     assert np.max(np.abs(N[0])) <= 1e-12 * np.max(np.abs(phi)) * np.max(np.abs(xi)) * s.M
     assert np.max(np.abs(N[1])) <= 1e-12 * scale
+
+
+# ---------------------------------------------------------------------------------------
+# advective form of the geopotential tendency (Eq. 1 as written): -V.grad(Phi') - Phi' delta
+def test_advective_nphi_rigid_rotation_is_exact():
+    """Solid-body rotation u = u0 cos(lat), v = 0: V.grad(Phi') = (u0/a) dPhi'/dlambda exactly,
+    delta = 0, so N_Phi = -i m (u0/a) Phi'_mn for any band-limited Phi'."""
+    s = Sphere(31, 48, 96)
+    sw = SWE(s, nphi_form="advective")
+    u0 = 30.0
+    xi = np.zeros((32, 32), dtype=complex)
+    xi[0, 1] = 2.0 * u0 / sw.p.a * np.sqrt(2.0 / 3.0)
+    Phi = s.unpack(inputs.random_state(31, 1, seed=17)[0, 0])
+    N = sw.nphi_advective((Phi, xi, np.zeros_like(xi)))
+    ref = -1j * s.m * (u0 / sw.p.a) * Phi
+    assert np.max(np.abs(N - s.real_m0(ref))) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_advective_nphi_equals_flux_form_on_an_oversampled_grid():
+    """-V.grad(Phi') - Phi' delta = -div(Phi' V) analytically; with both integrands resolved
+    (an oversampled Gaussian grid) the two discrete forms agree to quadrature accuracy.  A
+    sign, a factor a or a swapped wind component in either form breaks the agreement."""
+    M = 10
+    s = Sphere(M, 64, 128)
+    U = tuple(s.unpack(x) for x in inputs.random_state(M, 1, seed=23, scale=(1e3, 1e-5, 4e-6))[0])
+    Na = SWE(s, nphi_form="advective").nonlinear(U)[0]
+    Nf = SWE(s, nphi_form="flux").nonlinear(U)[0]
+    assert np.max(np.abs(Na - Nf)) < 1e-9 * np.max(np.abs(Nf))
+
+
+def test_advective_and_flux_forms_agree_on_the_three_halves_grid():
+    """On a grid that satisfies the 3/2 rule every integrand of either form is a polynomial in
+    mu (the (1 - mu^2) denominators cancel against the factors of U, V and P_n^m), so both are
+    exact projections of the same expression and agree to rounding; mass is conserved."""
+    M = 31
+    s = Sphere(M, 48, 96)
+    U = tuple(s.unpack(x) for x in inputs.random_state(M, 1, seed=29, scale=(1e3, 1e-5, 4e-6))[0])
+    Na = SWE(s, nphi_form="advective").nonlinear(U)[0]
+    Nf = SWE(s, nphi_form="flux").nonlinear(U)[0]
+    assert np.max(np.abs(Na - Nf)) < 1e-12 * np.max(np.abs(Nf))
+    assert abs(Nf[0, 0]) < 1e-12 * np.max(np.abs(Nf))         # no mass tendency
+    assert abs(Na[0, 0]) < 1e-12 * np.max(np.abs(Nf))
+
+
+def test_advective_and_flux_forms_differ_below_the_three_halves_rule():
+    """With too few latitudes (T31 on 36 instead of 48) the products alias, differently in the
+    two forms: the advective form is a computation of its own."""
+    M = 31
+    s = Sphere(M, 36, 96)
+    U = tuple(s.unpack(x) for x in inputs.random_state(M, 1, seed=29, scale=(1e3, 1e-5, 4e-6))[0])
+    Na = SWE(s, nphi_form="advective").nonlinear(U)[0]
+    Nf = SWE(s, nphi_form="flux").nonlinear(U)[0]
+    d = np.max(np.abs(Na - Nf)) / np.max(np.abs(Nf))
+    assert 1e-5 < d < 1e-1
