@@ -354,12 +354,14 @@ __global__ void __launch_bounds__(NT, MINB) k_ring_nl_g(const typename CT<T>::V*
 // lane t takes the butterflies j = t + T b.  Between passes the values go through a
 // padded per-ring shared-memory buffer (index i + i/16 against bank conflicts), with
 // a warp barrier only, since a ring never leaves its warp.
-//   inverse radices 12, then T = 32: 4 4 2 | 16: 4 4 | 8: 4 2 ; the first pass takes the
-//     c2r-prepared spectrum straight from the staged modes, the last keeps its outputs
-//     in registers (lane t, register b R + r: grid pair n = t + T (b + r 12/R));
-//   forward radices in the reverse order, so its first pass reads exactly that register
-//     layout, and its last (radix 12, span T) leaves X_{t + T r} in register r, whose
-//     r2c partner X_{H-k} is register 11 - r of lane T - t (one shuffle per r).
+//   inverse radices T = 32: 4 4 2 12 | 16: 4 4 12 | 8: 4 2 12 (every span Ns a power of
+//     two); the first pass takes the c2r-prepared spectrum straight from the staged modes,
+//     the last (radix 12, span T) keeps its outputs in registers (lane t, register q: grid
+//     pair n = t + T q);
+//   forward radices T = 32: 2 4 4 12 | 16: 4 4 12 | 8: 2 4 12; its first pass reads the
+//     same grid pairs after a compile-time register permutation, and its last (radix 12,
+//     span T) leaves X_{t + T r} in register r, whose r2c partner X_{H-k} is register
+//     11 - r of lane T - t (one shuffle per r).
 // The grid products of the nonlinear terms are taken in registers.  Twiddles of each
 // pass live in a shared table ordered by (j mod Ns, r).  Each block holds G = 128 / T
 // rings (G consecutive slices of one latitude), so every (mode, field) access of the
@@ -452,11 +454,14 @@ __device__ __forceinline__ void spass(float2 (&a)[EL], float2* buf, const float2
     }
 }
 
-// twiddle-table layout per T: offsets of the passes' tables (entries (Ns)(R-1))
+// twiddle-table layout per T: offsets of the passes' tables (entries (Ns)(R-1)).  The inverse
+// runs the radices 4 4 2 12 (T = 32), 4 4 12 (16), 4 2 12 (8), so that every span Ns is a
+// power of two (j mod Ns is a mask); the radix-12 pass, last in the inverse and in the forward,
+// shares one table (the inverse takes the conjugates).
 template <int T> struct RingTw;
-template <> struct RingTw<32> { static constexpr int i1 = 0, i2 = 36, i3 = 180, f1 = 372, f2 = 378, f3 = 402, n = 754; };
-template <> struct RingTw<16> { static constexpr int i1 = 0, i2 = 36, f1 = 180, f2 = 192, n = 368; };
-template <> struct RingTw<8> { static constexpr int i1 = 0, i2 = 36, f1 = 84, f2 = 90, n = 178; };
+template <> struct RingTw<32> { static constexpr int i1 = 0, i2 = 12, i3 = 28, f1 = 380, f2 = 386, f3 = 28, n = 410; };
+template <> struct RingTw<16> { static constexpr int i1 = 0, i2 = 12, f1 = 0, f2 = 12, n = 188; };
+template <> struct RingTw<8> { static constexpr int i1 = 0, i2 = 4, f1 = 92, f2 = 4, n = 98; };
 
 // entries e^{-2 pi i r k / (Ns R)}, k < Ns, r = 1..R-1, from the 2H-point table twg
 __device__ __forceinline__ void fill_tw(float2* dst, int R, int Ns, int H, const float2* twg) {
@@ -470,23 +475,33 @@ template <int T> __device__ __forceinline__ void fill_ring_tw(float2* tws, const
     constexpr int H = EL * T;
     using L = RingTw<T>;
     if constexpr (T == 32) {
-        fill_tw(tws + L::i1, 4, 12, H, twg);
-        fill_tw(tws + L::i2, 4, 48, H, twg);
-        fill_tw(tws + L::i3, 2, 192, H, twg);
+        fill_tw(tws + L::i1, 4, 4, H, twg);
+        fill_tw(tws + L::i2, 2, 16, H, twg);
+        fill_tw(tws + L::i3, 12, 32, H, twg);     // also f3
         fill_tw(tws + L::f1, 4, 2, H, twg);
         fill_tw(tws + L::f2, 4, 8, H, twg);
-        fill_tw(tws + L::f3, 12, 32, H, twg);
     } else if constexpr (T == 16) {
-        fill_tw(tws + L::i1, 4, 12, H, twg);
-        fill_tw(tws + L::i2, 4, 48, H, twg);
-        fill_tw(tws + L::f1, 4, 4, H, twg);
-        fill_tw(tws + L::f2, 12, 16, H, twg);
+        fill_tw(tws + L::i1, 4, 4, H, twg);       // also f1
+        fill_tw(tws + L::i2, 12, 16, H, twg);     // also f2
     } else {
-        fill_tw(tws + L::i1, 4, 12, H, twg);
-        fill_tw(tws + L::i2, 2, 48, H, twg);
+        fill_tw(tws + L::i1, 2, 4, H, twg);
+        fill_tw(tws + L::i2, 12, 8, H, twg);      // also f2
         fill_tw(tws + L::f1, 4, 2, H, twg);
-        fill_tw(tws + L::f2, 12, 8, H, twg);
     }
+}
+
+// Register order of the grid pairs a lane holds: the inverse leaves grid pair n = t + T q in
+// register q; the forward's first pass (radix 2 for T = 32 and 8, radix 4 for T = 16, span 1)
+// wants register b R + r to hold x[t + T b + r H / R], i.e. inverse register b + (12 / R) r.
+template <int T> __device__ __forceinline__ void grid_to_forward_order(float2 (&a)[EL]) {
+    constexpr int R = (T == 16) ? 4 : 2;
+    float2 w[EL];
+#pragma unroll
+    for (int q = 0; q < EL; ++q) w[q] = a[q];
+#pragma unroll
+    for (int b = 0; b < EL / R; ++b)
+#pragma unroll
+        for (int r = 0; r < R; ++r) a[b * R + r] = w[b + (EL / R) * r];
 }
 
 // inverse transform of one field: modes X[0..M] (staged) -> grid pairs in registers
@@ -495,34 +510,39 @@ __device__ __forceinline__ void ring_inverse_regs(const float2* X, int M, const 
                                                   float2* buf, int t, float2 (&a)[EL]) {
     constexpr int H = EL * T;
     using L = RingTw<T>;
+    // c2r-prepared spectrum Z_k in the first pass's order: register b 4 + r holds
+    // x[t + T b + r H/4], i.e. k = t + T (b + 3 r)
 #pragma unroll
-    for (int r = 0; r < EL; ++r) {
-        const int k = t + T * r;
-        float2 xa = (k <= M) ? X[k] : f2(0.f, 0.f);
-        if (k == 0) xa.y = 0.f;                             // the m = 0 mode is real
-        const float2 xb = (k > 0 && H - k <= M) ? X[H - k] : f2(0.f, 0.f);
-        const float2 e = f2(twN[k].x, -twN[k].y);          // e^{+i theta_k}, theta_k = 2 pi k / (2H)
-        const float2 s1 = cadd(xa, cconj(xb)), d1 = csub(xa, cconj(xb));
-        a[r] = cadd(s1, cmul_si<1>(cmul(e, d1)));
-    }
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int k = t + T * (b + 3 * r);
+            float2 xa = (k <= M) ? X[k] : f2(0.f, 0.f);
+            if (k == 0) xa.y = 0.f;                         // the m = 0 mode is real
+            const float2 xb = (k > 0 && H - k <= M) ? X[H - k] : f2(0.f, 0.f);
+            const float2 e = f2(twN[k].x, -twN[k].y);      // e^{+i theta_k}, theta_k = 2 pi k / (2H)
+            const float2 s1 = cadd(xa, cconj(xb)), d1 = csub(xa, cconj(xb));
+            a[b * 4 + r] = cadd(s1, cmul_si<1>(cmul(e, d1)));
+        }
     __syncwarp();                                          // buf free (previous transform done)
-    spass<T, 12, 1, +1, false, true>(a, buf, nullptr, t);
+    spass<T, 4, 1, +1, false, true>(a, buf, nullptr, t);
     __syncwarp();
     if constexpr (T == 32) {
-        spass<T, 4, 12, +1, true, true>(a, buf, tws + L::i1, t);
+        spass<T, 4, 4, +1, true, true>(a, buf, tws + L::i1, t);
         __syncwarp();
-        spass<T, 4, 48, +1, true, true>(a, buf, tws + L::i2, t);
+        spass<T, 2, 16, +1, true, true>(a, buf, tws + L::i2, t);
         __syncwarp();
-        spass<T, 2, 192, +1, true, false>(a, buf, tws + L::i3, t);
+        spass<T, 12, 32, +1, true, false>(a, buf, tws + L::i3, t);
     } else if constexpr (T == 16) {
-        spass<T, 4, 12, +1, true, true>(a, buf, tws + L::i1, t);
+        spass<T, 4, 4, +1, true, true>(a, buf, tws + L::i1, t);
         __syncwarp();
-        spass<T, 4, 48, +1, true, false>(a, buf, tws + L::i2, t);
+        spass<T, 12, 16, +1, true, false>(a, buf, tws + L::i2, t);
     } else {
-        spass<T, 4, 12, +1, true, true>(a, buf, tws + L::i1, t);
+        spass<T, 2, 4, +1, true, true>(a, buf, tws + L::i1, t);
         __syncwarp();
-        spass<T, 2, 48, +1, true, false>(a, buf, tws + L::i2, t);
+        spass<T, 12, 8, +1, true, false>(a, buf, tws + L::i2, t);
     }
+    // register q now holds grid pair n = t + T q
 }
 
 // forward transform of one field from the grid pairs in registers -> modes X[0..M] (scaled)
@@ -530,6 +550,7 @@ template <int T>
 __device__ __forceinline__ void ring_forward_regs(float2 (&a)[EL], int M, const float2* twN, const float2* tws,
                                                   float2* buf, int t, float scale, float2* X) {
     using L = RingTw<T>;
+    grid_to_forward_order<T>(a);                           // a arrives in grid order (n = t + T q)
     __syncwarp();
     if constexpr (T == 32) {
         spass<T, 2, 1, -1, false, true>(a, buf, nullptr, t);
@@ -703,11 +724,8 @@ __global__ void __launch_bounds__(128) k_ring_inv_lg(const float2* __restrict__ 
     ring_inverse_regs<T>(reg + g * RS, M, twN, tws, fbuf + g * HB, t, a);
     if (c0 + g < C) {
         float2* row = reinterpret_cast<float2*>(grid + ((int64_t)(c0 + g) * nlat + j) * (2 * H));
-        constexpr int RL = (T == 16) ? 4 : 2;               // radix of the last inverse pass
 #pragma unroll
-        for (int b = 0; b < EL / RL; ++b)
-#pragma unroll
-            for (int r = 0; r < RL; ++r) row[t + T * (b + r * (EL / RL))] = a[b * RL + r];
+        for (int q = 0; q < EL; ++q) row[t + T * q] = a[q];  // register q: grid pair t + T q
     }
 }
 
@@ -727,13 +745,10 @@ __global__ void __launch_bounds__(128) k_ring_fwd_lg(const float* __restrict__ g
     const int t = threadIdx.x & (T - 1), g = threadIdx.x / T;
     float2 a[EL];
     {
-        constexpr int RL = (T == 16) ? 4 : 2;               // radix of the first forward pass
         const bool ok = c0 + g < C;
         const float2* row = reinterpret_cast<const float2*>(grid + ((int64_t)(ok ? c0 + g : 0) * nlat + j) * (2 * H));
 #pragma unroll
-        for (int b = 0; b < EL / RL; ++b)
-#pragma unroll
-            for (int r = 0; r < RL; ++r) a[b * RL + r] = ok ? row[t + T * (b + r * (EL / RL))] : f2(0.f, 0.f);
+        for (int q = 0; q < EL; ++q) a[q] = ok ? row[t + T * q] : f2(0.f, 0.f);   // grid order
     }
     for (int k = threadIdx.x; k < 2 * H; k += blockDim.x) twN[k] = twg[k];
     fill_ring_tw<T>(tws, twg);
