@@ -424,15 +424,45 @@ __device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
 // One Stockham pass over a ring of H = 12 T values.  Register b R + r holds input
 // x[j_b + r H/R] (LOAD: read from buf first) and receives output y[(j_b - k) R + k + r Ns]
 // (STORE: written to buf instead).
-template <int T, int R, int Ns, int S, bool LOAD, bool STORE>
+// Position of element i of a ring buffer.  SW < 0: one padding element per 16 (i + i/16).
+// SW >= 0 (T = 32 passes): i stays in its 16-element row (128 bytes, all 32 banks) and its
+// position in the row is XORed with a mask of the row index, chosen per pass so that the
+// pass's strided stores hit 16 different bank pairs in every half-warp; the next pass reads
+// whole rows, which any in-row permutation leaves conflict-free.
+template <int SW> __device__ __forceinline__ int bidx(int i) {
+    if constexpr (SW < 0) {
+        return padi(i);
+    } else {
+        const int q = i >> 4;
+        int x = 0;
+        if constexpr (SW == 1) x = q & 1;                  // forward (2, Ns 1)
+        else if constexpr (SW == 2) x = q & 3;             // inverse (4, Ns 1)
+        else if constexpr (SW == 3) x = (q & 7) << 1;      // forward (4, Ns 2)
+        else if constexpr (SW == 4) x = (q & 3) << 2;      // inverse (4, Ns 4)
+        else if constexpr (SW == 5) x = ((q >> 1) & 1) << 3;   // forward (4, Ns 8)
+        return i ^ x;
+    }
+}
+
+// SWL: layout the previous pass stored with; SWS: layout this pass stores with
+template <int T, int R, int Ns, int S, bool LOAD, bool STORE, int SWL = -1, int SWS = -1>
 __device__ __forceinline__ void spass(float2 (&a)[EL], float2* buf, const float2* twp, int t) {
     constexpr int H = EL * T, NB = EL / R;
     if constexpr (LOAD) {
 #pragma unroll
         for (int b = 0; b < NB; ++b)
 #pragma unroll
-            for (int r = 0; r < R; ++r) a[b * R + r] = buf[padi(t + T * b + r * (H / R))];
+            for (int r = 0; r < R; ++r) a[b * R + r] = buf[bidx<SWL>(t + T * b + r * (H / R))];
         if constexpr (STORE) __syncwarp();
+    }
+    // when Ns divides T (every lane-group pass), k = j mod Ns = t mod Ns for all of the lane's
+    // butterflies: its R - 1 twiddles are loaded once
+    constexpr bool kLane = (Ns > 1) && (T % Ns == 0);
+    float2 twl[R > 1 ? R - 1 : 1];
+    if constexpr (kLane) {
+        const int k = t & (Ns - 1);
+#pragma unroll
+        for (int r = 1; r < R; ++r) twl[r - 1] = twd<S>(twp[k * (R - 1) + r - 1]);
     }
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
@@ -441,14 +471,17 @@ __device__ __forceinline__ void spass(float2 (&a)[EL], float2* buf, const float2
         float2 v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = a[b * R + r];
-        if constexpr (Ns > 1) {
+        if constexpr (kLane) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twl[r - 1]);
+        } else if constexpr (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twd<S>(twp[k * (R - 1) + r - 1]));
         }
         bfly<R, S>(v);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            if constexpr (STORE) buf[padi((j - k) * R + k + r * Ns)] = v[r];
+            if constexpr (STORE) buf[bidx<SWS>((j - k) * R + k + r * Ns)] = v[r];
             else a[b * R + r] = v[r];
         }
     }
@@ -525,15 +558,19 @@ __device__ __forceinline__ void ring_inverse_regs(const float2* X, int M, const 
             a[b * 4 + r] = cadd(s1, cmul_si<1>(cmul(e, d1)));
         }
     __syncwarp();                                          // buf free (previous transform done)
+    if constexpr (T == 32) {
+        spass<T, 4, 1, +1, false, true, -1, 2>(a, buf, nullptr, t);
+        __syncwarp();
+        spass<T, 4, 4, +1, true, true, 2, 4>(a, buf, tws + L::i1, t);
+        __syncwarp();
+        spass<T, 2, 16, +1, true, true, 4, 0>(a, buf, tws + L::i2, t);
+        __syncwarp();
+        spass<T, 12, 32, +1, true, false, 0, -1>(a, buf, tws + L::i3, t);
+        return;
+    }
     spass<T, 4, 1, +1, false, true>(a, buf, nullptr, t);
     __syncwarp();
-    if constexpr (T == 32) {
-        spass<T, 4, 4, +1, true, true>(a, buf, tws + L::i1, t);
-        __syncwarp();
-        spass<T, 2, 16, +1, true, true>(a, buf, tws + L::i2, t);
-        __syncwarp();
-        spass<T, 12, 32, +1, true, false>(a, buf, tws + L::i3, t);
-    } else if constexpr (T == 16) {
+    if constexpr (T == 16) {
         spass<T, 4, 4, +1, true, true>(a, buf, tws + L::i1, t);
         __syncwarp();
         spass<T, 12, 16, +1, true, false>(a, buf, tws + L::i2, t);
@@ -553,13 +590,13 @@ __device__ __forceinline__ void ring_forward_regs(float2 (&a)[EL], int M, const 
     grid_to_forward_order<T>(a);                           // a arrives in grid order (n = t + T q)
     __syncwarp();
     if constexpr (T == 32) {
-        spass<T, 2, 1, -1, false, true>(a, buf, nullptr, t);
+        spass<T, 2, 1, -1, false, true, -1, 1>(a, buf, nullptr, t);
         __syncwarp();
-        spass<T, 4, 2, -1, true, true>(a, buf, tws + L::f1, t);
+        spass<T, 4, 2, -1, true, true, 1, 3>(a, buf, tws + L::f1, t);
         __syncwarp();
-        spass<T, 4, 8, -1, true, true>(a, buf, tws + L::f2, t);
+        spass<T, 4, 8, -1, true, true, 3, 5>(a, buf, tws + L::f2, t);
         __syncwarp();
-        spass<T, 12, 32, -1, true, false>(a, buf, tws + L::f3, t);
+        spass<T, 12, 32, -1, true, false, 5, -1>(a, buf, tws + L::f3, t);
     } else if constexpr (T == 16) {
         spass<T, 4, 1, -1, false, true>(a, buf, nullptr, t);
         __syncwarp();
@@ -594,6 +631,12 @@ __device__ __forceinline__ void ring_forward_regs(float2 (&a)[EL], int M, const 
 // stride of the per-ring staging regions: n float2 rounded up to 1 mod 16, so that the rings
 // of a block (up to 16) fall on different shared-memory banks at the same offset
 __host__ __device__ constexpr int ring_stride(int n) { return n + (17 - n % 16) % 16; }
+// T = 32 (one ring per warp, 4 rings per block): the transforms never mix rings within a
+// warp, but the staging and output loops do (lane q: ring q mod 4, mode q / 4); a stride of
+// 4 mod 16 puts the 16 (ring, mode) pairs of a half-warp on 16 different bank pairs
+template <int T> __host__ __device__ constexpr int ring_stride_t(int n) {
+    return T == 32 ? n + (20 - n % 16) % 16 : ring_stride(n);
+}
 
 __device__ __forceinline__ void cp_async8(void* dst, const void* src, bool pred) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
@@ -611,7 +654,7 @@ __global__ void __launch_bounds__(128, 3) k_ring_nl_lg(const float2* __restrict_
     float2* tws = twN + 2 * H;                              // pass tables
     float2* fbuf = tws + RingTw<T>::n;                      // [G][HB]
     float2* reg = fbuf + G * HB;                            // [G][5][M+1], ring stride RS
-    const int Mp = M + 1, RS = ring_stride(5 * Mp);
+    const int Mp = M + 1, RS = ring_stride_t<T>(5 * Mp);
     const int s0 = blockIdx.x * G;
     const int j = blockIdx.y;
     const int64_t C4 = 4 * (int64_t)S, C5 = 5 * (int64_t)S;
@@ -706,7 +749,7 @@ __global__ void __launch_bounds__(128) k_ring_inv_lg(const float2* __restrict__ 
     float2* tws = twN + 2 * H;
     float2* fbuf = tws + RingTw<T>::n;                      // [G][HB]
     float2* reg = fbuf + G * HB;                            // [G][M+1], ring stride RS
-    const int Mp = M + 1, RS = ring_stride(Mp);
+    const int Mp = M + 1, RS = ring_stride_t<T>(Mp);
     const int c0 = blockIdx.x * G;
     const int j = blockIdx.y;
     for (int q = threadIdx.x; q < Mp * G; q += blockDim.x) {
@@ -739,7 +782,7 @@ __global__ void __launch_bounds__(128) k_ring_fwd_lg(const float* __restrict__ g
     float2* tws = twN + 2 * H;
     float2* fbuf = tws + RingTw<T>::n;
     float2* reg = fbuf + G * HB;                            // [G][M+1], ring stride RS
-    const int Mp = M + 1, RS = ring_stride(Mp);
+    const int Mp = M + 1, RS = ring_stride_t<T>(Mp);
     const int c0 = blockIdx.x * G;
     const int j = blockIdx.y;
     const int t = threadIdx.x & (T - 1), g = threadIdx.x / T;
@@ -765,7 +808,7 @@ __global__ void __launch_bounds__(128) k_ring_fwd_lg(const float* __restrict__ g
 template <int T>
 static swe_status ring_plain_lg(const swe_plan* p, const void* in, void* out, int C, bool inverse, cudaStream_t st) {
     constexpr int H = EL * T, G = 128 / T, HB = H + H / 16 + 1;
-    const size_t sm = (2 * (size_t)H + RingTw<T>::n + (size_t)G * HB + (size_t)G * ring_stride(p->M + 1)) * sizeof(float2);
+    const size_t sm = (2 * (size_t)H + RingTw<T>::n + (size_t)G * HB + (size_t)G * ring_stride_t<T>(p->M + 1)) * sizeof(float2);
     dim3 g((C + G - 1) / G, p->nlat);
     if (inverse) {
         SWE_CHECK_CUDA(cudaFuncSetAttribute(k_ring_inv_lg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -995,7 +1038,7 @@ template <int T>
 static swe_status ring_lg_launch(const swe_plan* p, const void* Fin, void* Fout, int S, cudaStream_t st) {
     constexpr int H = EL * T, G = 128 / T, HB = H + H / 16 + 1;
     const size_t sm =
-        (2 * (size_t)H + RingTw<T>::n + (size_t)G * HB + (size_t)G * ring_stride(5 * (p->M + 1))) * sizeof(float2);
+        (2 * (size_t)H + RingTw<T>::n + (size_t)G * HB + (size_t)G * ring_stride_t<T>(5 * (p->M + 1))) * sizeof(float2);
     SWE_CHECK_CUDA(cudaFuncSetAttribute(k_ring_nl_lg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     dim3 g((S + G - 1) / G, p->nlat);
     k_ring_nl_lg<T><<<g, 128, sm, st>>>((const float2*)Fin, (float2*)Fout, p->M, p->nlat, S, p->twf, p->mu, p->w);
