@@ -991,6 +991,179 @@ def run_bumps(args):
     return 0
 
 
+# Parareal configurations of the other BASELINE workloads: (truncation, grid, slices, horizon,
+# fine steps per slice, coarse plan, coarse steps per slice, coarse hyperviscosity candidates;
+# the first is the configured one, the next is taken if the iteration goes non-finite)
+PARA_CONFIGS = {
+    # T127, 64 slices over 2 days, fine 60 s, coarse IMEX 900 s with 4th-order hyperviscosity
+    # 1e14 m^4/s as configured; 1e15 m^4/s (the smallest 4th-order value of the paper's §5.2
+    # viscosity study) if the configured value is unstable at this step
+    "config2": dict(workload="t127_parareal_s64", M=127, grid=(192, 384), S=64, days=2, nf=45, Mc=127,
+                    cgrid=(192, 384), nc=3, q=4, nus=(1.0e14, 1.0e15), bump=False, iters=4, fp64_iters=4,
+                    fp64_serial=True, seed=2),
+    # T511, 256 slices over 3 days, fine ~29.78 s (34 per slice), coarse on T255 with 12 steps
+    # per slice and hyperviscosity scaled from the T255 workload's coarse level, plus a 120 m bump
+    "config4": dict(workload="t511_parareal_s256", M=511, grid=(768, 1536), S=256, days=3, nf=34, Mc=255,
+                    cgrid=(384, 768), nc=12, q=4, nus=(1.0e16 * (127.0 / 255.0) ** 4,), bump=True, iters=4,
+                    fp64_iters=1, fp64_serial=False, seed=4),
+}
+
+
+def _para_initial_state(cfg, dev):
+    """Balanced k^-3 flow + height noise (+ the 120 m bump) of the configuration, on an FP64 plan."""
+    import numpy as np
+    import torch
+
+    from paper_2306_09497_gb300 import inputs, swe
+
+    Mq, (nl, nn) = cfg["M"], cfg["grid"]
+    p64 = swe.Plan(Mq, nl, nn)
+    xi, noise = inputs.initial_fields(Mq, cfg["seed"])
+    if cfg["bump"]:
+        mu, _ = p64.gauss()
+        grid = torch.from_numpy(inputs.single_bump_phi(np.arcsin(mu), 2.0 * np.pi * np.arange(nn) / nn)[None]
+                                .copy()).to(dev)
+        bump = torch.empty((1, p64.nc * 2), dtype=torch.float64, device=dev)
+        p64.sht_forward(grid, bump, 1)
+        noise = noise + bump.cpu().numpy().view(np.complex128)[0]
+    U0 = torch.empty(1, 3, p64.nc * 2, dtype=torch.float64, device=dev)
+    p64.balance(torch.from_numpy(xi.view(np.float64).copy()).to(dev),
+                torch.from_numpy(np.ascontiguousarray(noise).view(np.float64).copy()).to(dev), U0, 1)
+    p64.close()
+    return U0
+
+
+def _para_run(cfg, prec_name, nu, U0, local):
+    """One precision of a Parareal configuration: serial fine solution (unless left out),
+    initial coarse guess, K iterations timed one by one with CUDA events."""
+    import numpy as np
+    import torch
+
+    from paper_2306_09497_gb300 import swe
+
+    Mq, (nl, nn), Sq = cfg["M"], cfg["grid"], cfg["S"]
+    slice_s = cfg["days"] * 86400.0 / Sq
+    fine = swe.stepper(swe.SWE_IMEX, slice_s / cfg["nf"], cfg["nf"])
+    coarse = swe.stepper(swe.SWE_IMEX, slice_s / cfg["nc"], cfg["nc"], cfg["q"], nu)
+    prec = swe.SWE_FP64 if prec_name == "fp64" else swe.SWE_SPLIT_BF16X3
+    plan = swe.Plan(Mq, nl, nn, prec=prec)
+    cplan = swe.Plan(cfg["Mc"], *cfg["cgrid"], prec=prec) if cfg["Mc"] != Mq else plan
+    it = None
+    try:
+        ref, t_serial = None, None
+        if prec_name == "mixed" or cfg["fp64_serial"]:
+            ref = U0.clone()
+            t0 = time.perf_counter()
+            plan.propagate(swe.stepper(swe.SWE_IMEX, slice_s / cfg["nf"], cfg["nf"] * Sq), ref, ref, 1)
+            torch.cuda.synchronize()
+            t_serial = time.perf_counter() - t0
+        it = swe.Parareal(plan, cplan, fine, coarse, Sq, use_graphs=True)
+        it.init(U0)
+        sol = torch.empty((Sq + 1, 3, plan.nc * 2), dtype=torch.float64, device=U0.device)
+        K = cfg["iters"] if prec_name == "mixed" else cfg["fp64_iters"]
+        stream = torch.cuda.current_stream()
+        hist, ms, last = [], [], []
+
+        def record():
+            it.solution(sol)
+            last.append(sol[Sq:Sq + 1].clone())
+            if ref is not None:
+                e = plan.error_norms(last[-1], ref, 1, R_NORM)
+                hist.append({"E_phi_R32": float(e[0, 0, 0]), "L2_phi": float(e[0, 0, 1]),
+                             "L2_xi": float(e[0, 1, 1]), "L2_delta": float(e[0, 2, 1])})
+
+        record()
+        clocks = ClockSampler(local)
+        clocks.start()
+        for _ in range(K):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            it.iterate(1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            record()
+        clk = clocks.stop()
+        # the first iteration also captures the iteration graph; the rest replay it
+        steady = ms[1:] if len(ms) > 1 else ms
+        res = {"value": Sq * cfg["nf"] / (np.mean(steady) / 1000.0), "unit": "slice-steps/s", "coarse_nu": nu,
+               "ms_per_iteration": ms, "serial_fine_seconds": t_serial, "error_vs_serial_fine": hist,
+               "clocks": clk}
+        return res, last, ref, plan
+    except Exception:
+        plan.close()
+        raise
+    finally:
+        if it is not None:
+            it.close()
+        if cplan is not plan:
+            cplan.close()
+
+
+def run_parareal_config(args):
+    """--workload config2 | config4: Parareal at the configuration's size, split precision and
+    FP64 plain on the same GPU; slice-steps/s, E_{Phi,32} and the area-weighted L2 error of the
+    last slice boundary against each precision's serial fine solution after every iteration, and
+    the per-field error of the split-precision iterates against the FP64 ones.  At T511 the FP64
+    serial fine solution (8704 steps of one state) is left out: it would take minutes."""
+    import numpy as np
+    import torch
+
+    from paper_2306_09497_gb300 import swe
+
+    cfg = PARA_CONFIGS[args.workload]
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    U0 = _para_initial_state(cfg, dev)
+    unstable = []
+    mixed = None
+    for nu in cfg["nus"]:
+        try:
+            mixed = _para_run(cfg, "mixed", nu, U0, local)
+            break
+        except swe.SWEError as e:
+            if e.status != swe.SWE_EUNSTABLE:
+                raise
+            unstable.append({"coarse_nu": nu, "precision": "mixed", "status": str(e)})
+    if mixed is None:
+        raise RuntimeError("every coarse hyperviscosity candidate went non-finite: %s" % unstable)
+    nu = mixed[0]["coarse_nu"]
+    fp64 = _para_run(cfg, "fp64", nu, U0, local)
+    (rm_, lm, rm, pm), (r6_, l6, r6, p6) = mixed, fp64
+    # split precision against FP64, per field, at the last slice boundary of each iteration
+    cmp = []
+    for k in range(min(len(lm), len(l6))):
+        e = pm.error_norms(lm[k], l6[k], 1, R_NORM)
+        cmp.append({"iteration": k, "L2_phi": float(e[0, 0, 1]), "L2_xi": float(e[0, 1, 1]),
+                    "L2_delta": float(e[0, 2, 1]), "E_phi_R32": float(e[0, 0, 0])})
+    serial_cmp = None
+    if r6 is not None:
+        e = pm.error_norms(rm, r6, 1, R_NORM)
+        serial_cmp = {"L2_phi": float(e[0, 0, 1]), "L2_xi": float(e[0, 1, 1]), "L2_delta": float(e[0, 2, 1]),
+                      "E_phi_R32": float(e[0, 0, 0])}
+    pm.close()
+    p6.close()
+    Mq, (nl, nn), Sq = cfg["M"], cfg["grid"], cfg["S"]
+    slice_s = cfg["days"] * 86400.0 / Sq
+    line = {"metric": "SWE slice-steps/s (Parareal, %s)" % cfg["workload"], "value": rm_["value"],
+            "unit": "slice-steps/s", "n_gpus": world, "steps": cfg["iters"] - 1, "warmup": 1,
+            "ms_per_step": float(np.mean(rm_["ms_per_iteration"][1:])), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "mixed: bf16 split x6 tensor GEMM, f32 FFT/grid, f64 state", "data": "synthetic",
+            "config": {"workload": cfg["workload"], "M": Mq, "nlat": nl, "nlon": nn, "slices": Sq, "days": cfg["days"],
+                       "fine": "IMEX %d x %.2f s per slice" % (cfg["nf"], slice_s / cfg["nf"]),
+                       "coarse": "IMEX T%d %d x %.2f s per slice, q=%d nu=%.3g" % (
+                           cfg["Mc"], cfg["nc"], slice_s / cfg["nc"], cfg["q"], nu),
+                       "bump_120m": cfg["bump"]},
+            "unstable_coarse_settings": unstable,
+            "mixed": rm_, "fp64_plain": r6_, "mixed_over_fp64": rm_["value"] / r6_["value"],
+            "mixed_vs_fp64_per_iteration": cmp, "mixed_vs_fp64_serial_fine": serial_cmp}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -998,7 +1171,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["fp64", "mixed"])
-    ap.add_argument("--workload", default="mgrit", choices=["mgrit", "parareal", "serve", "ncu-case", "bumps"])
+    ap.add_argument("--workload", default="mgrit", choices=["mgrit", "parareal", "serve", "ncu-case", "bumps", "config2",
+                                                              "config4"])
     ap.add_argument("--bumps-iters", type=int, default=10, help="MGRIT iterations per bumps configuration")
     ap.add_argument("--S", type=int, default=32, help="states of the ncu case")
     ap.add_argument("--case-steps", type=int, default=1, help="IMEX steps of the ncu case")
@@ -1020,6 +1194,8 @@ def main():
         return ncu_case(args)
     if args.workload == "bumps":
         return run_bumps(args)
+    if args.workload in PARA_CONFIGS:
+        return run_parareal_config(args)
     return run_ours(args)
 
 

@@ -149,3 +149,16 @@ def gaussian_bumps_phi(lat: np.ndarray, lon: np.ndarray, g: float = GRAVITY) -> 
         d = np.arccos(np.clip(c, -1.0, 1.0))
         out += np.exp(-ai * d * d)
     return g * BUMPS_AMPLITUDE * out
+
+
+def single_bump_phi(lat: np.ndarray, lon: np.ndarray, height: float = 120.0, width: float = 80.0,
+                    centre=(np.pi / 5.0, np.pi / 3.0), g: float = GRAVITY) -> np.ndarray:
+    """A localised Gaussian height bump, g * height * exp(-width d^2), d the great-circle angle to
+    the centre (longitude, latitude), at the given latitudes and longitudes (radians); the form of
+    the §5.1 bumps, with a 120 m default height.  Returns [len(lat)][len(lon)]."""
+    la = np.asarray(lat, dtype=np.float64)[:, None]
+    lo = np.asarray(lon, dtype=np.float64)[None, :]
+    lc, tc = centre
+    c = np.sin(la) * np.sin(tc) + np.cos(la) * np.cos(tc) * np.cos(lo - lc)
+    d = np.arccos(np.clip(c, -1.0, 1.0))
+    return g * height * np.exp(-width * d * d)
