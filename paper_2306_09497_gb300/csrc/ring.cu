@@ -444,6 +444,31 @@ template <int SW> __device__ __forceinline__ int bidx(int i) {
     }
 }
 
+// Barrier of the T lanes that own one ring: a warp barrier for T <= 32; for T = 64 (two warps
+// per ring, two rings per 128-thread block) the named barrier 1 + ring index over 64 threads.
+template <int T> __device__ __forceinline__ void ring_sync() {
+    if constexpr (T <= 32) {
+        __syncwarp();
+    } else if (threadIdx.x < 64) {               // warp-uniform: ring 0 is warps 0-1
+        asm volatile("bar.sync 1, 64;" ::: "memory");
+    } else {
+        asm volatile("bar.sync 2, 64;" ::: "memory");
+    }
+}
+
+// Period of a layout: bidx<SW>(i + P) = bidx<SW>(i) + P (+ P / 16 for the padded layout).
+template <int SW> __host__ __device__ constexpr int bperiod() {
+    return SW < 0 ? 16 : (SW == 1 ? 32 : (SW == 3 ? 128 : 64));
+}
+// Position of element L + C, with L the lane's part and C >= 0 a constant of the unrolled
+// loop: only bidx<SW>(L + C mod P) depends on the lane, and accesses whose C agree mod P
+// share it; the rest is an immediate offset of the shared-memory access.
+template <int SW> __device__ __forceinline__ int bidx_at(int L, int C) {
+    constexpr int P = bperiod<SW>();
+    const int c = C % P, hi = C - c;
+    return bidx<SW>(L + c) + (SW < 0 ? hi + hi / 16 : hi);
+}
+
 // SWL: layout the previous pass stored with; SWS: layout this pass stores with
 template <int T, int R, int Ns, int S, bool LOAD, bool STORE, int SWL = -1, int SWS = -1>
 __device__ __forceinline__ void spass(float2 (&a)[EL], float2* buf, const float2* twp, int t) {
@@ -452,22 +477,25 @@ __device__ __forceinline__ void spass(float2 (&a)[EL], float2* buf, const float2
 #pragma unroll
         for (int b = 0; b < NB; ++b)
 #pragma unroll
-            for (int r = 0; r < R; ++r) a[b * R + r] = buf[bidx<SWL>(t + T * b + r * (H / R))];
-        if constexpr (STORE) __syncwarp();
+            for (int r = 0; r < R; ++r) a[b * R + r] = buf[bidx_at<SWL>(t, T * b + r * (H / R))];
+        if constexpr (STORE) ring_sync<T>();
     }
     // when Ns divides T (every lane-group pass), k = j mod Ns = t mod Ns for all of the lane's
     // butterflies: its R - 1 twiddles are loaded once
     constexpr bool kLane = (Ns > 1) && (T % Ns == 0);
     float2 twl[R > 1 ? R - 1 : 1];
+    const int kl = t & (Ns - 1);                 // j mod Ns of every butterfly when kLane
     if constexpr (kLane) {
-        const int k = t & (Ns - 1);
 #pragma unroll
-        for (int r = 1; r < R; ++r) twl[r - 1] = twd<S>(twp[k * (R - 1) + r - 1]);
+        for (int r = 1; r < R; ++r) twl[r - 1] = twd<S>(twp[kl * (R - 1) + r - 1]);
     }
+    // store position (j - k) R + k + r Ns of butterfly j = t + T b: lane part (t - k) R + k,
+    // constant part T b R + r Ns (when k = j mod Ns is the lane's own kl)
+    const int Ls = (t - kl) * R + kl;
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
         const int j = t + T * b;
-        const int k = (Ns == 1) ? 0 : j % Ns;
+        const int k = (Ns == 1) ? 0 : (kLane ? kl : j % Ns);
         float2 v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = a[b * R + r];
@@ -481,8 +509,12 @@ __device__ __forceinline__ void spass(float2 (&a)[EL], float2* buf, const float2
         bfly<R, S>(v);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            if constexpr (STORE) buf[bidx<SWS>((j - k) * R + k + r * Ns)] = v[r];
-            else a[b * R + r] = v[r];
+            if constexpr (STORE) {
+                if constexpr (Ns == 1 || kLane) buf[bidx_at<SWS>(Ls, T * b * R + r * Ns)] = v[r];
+                else buf[bidx<SWS>((j - k) * R + k + r * Ns)] = v[r];
+            } else {
+                a[b * R + r] = v[r];
+            }
         }
     }
 }
@@ -495,6 +527,7 @@ template <int T> struct RingTw;
 template <> struct RingTw<32> { static constexpr int i1 = 0, i2 = 12, i3 = 28, f1 = 380, f2 = 386, f3 = 28, n = 410; };
 template <> struct RingTw<16> { static constexpr int i1 = 0, i2 = 12, f1 = 0, f2 = 12, n = 188; };
 template <> struct RingTw<8> { static constexpr int i1 = 0, i2 = 4, f1 = 92, f2 = 4, n = 98; };
+template <> struct RingTw<64> { static constexpr int i1 = 0, i2 = 12, i3 = 60, f1 = 0, f2 = 12, f3 = 60, n = 764; };
 
 // entries e^{-2 pi i r k / (Ns R)}, k < Ns, r = 1..R-1, from the 2H-point table twg
 __device__ __forceinline__ void fill_tw(float2* dst, int R, int Ns, int H, const float2* twg) {
@@ -513,6 +546,10 @@ template <int T> __device__ __forceinline__ void fill_ring_tw(float2* tws, const
         fill_tw(tws + L::i3, 12, 32, H, twg);     // also f3
         fill_tw(tws + L::f1, 4, 2, H, twg);
         fill_tw(tws + L::f2, 4, 8, H, twg);
+    } else if constexpr (T == 64) {
+        fill_tw(tws + L::i1, 4, 4, H, twg);       // also f1
+        fill_tw(tws + L::i2, 4, 16, H, twg);      // also f2
+        fill_tw(tws + L::i3, 12, 64, H, twg);     // also f3
     } else if constexpr (T == 16) {
         fill_tw(tws + L::i1, 4, 4, H, twg);       // also f1
         fill_tw(tws + L::i2, 12, 16, H, twg);     // also f2
@@ -527,7 +564,7 @@ template <int T> __device__ __forceinline__ void fill_ring_tw(float2* tws, const
 // register q; the forward's first pass (radix 2 for T = 32 and 8, radix 4 for T = 16, span 1)
 // wants register b R + r to hold x[t + T b + r H / R], i.e. inverse register b + (12 / R) r.
 template <int T> __device__ __forceinline__ void grid_to_forward_order(float2 (&a)[EL]) {
-    constexpr int R = (T == 16) ? 4 : 2;
+    constexpr int R = (T == 16 || T == 64) ? 4 : 2;
     float2 w[EL];
 #pragma unroll
     for (int q = 0; q < EL; ++q) w[q] = a[q];
@@ -537,8 +574,29 @@ template <int T> __device__ __forceinline__ void grid_to_forward_order(float2 (&
         for (int r = 0; r < R; ++r) a[b * R + r] = w[b + (EL / R) * r];
 }
 
+// MP: M + 1 fixed at compile time (0: the runtime M).  With MP a multiple of T, whether mode
+// k = t + T c exists is decided per c at compile time, for every lane at once.
+template <int T, int MP>
+__device__ __forceinline__ bool mode_in(int k, int c, int M) {
+    if constexpr (MP > 0) {
+        if (T * (c + 1) <= MP) return true;
+        if (T * c >= MP) return false;
+    }
+    return k <= M;
+}
+// whether H - k <= M for k = t + T c, k > 0 (the conjugate partner of mode k exists)
+template <int T, int MP>
+__device__ __forceinline__ bool partner_in(int k, int c, int M) {
+    constexpr int H = EL * T;
+    if constexpr (MP > 0) {
+        if (T * c >= H - MP + 1) return true;           // every k of this c
+        if (T * c + T - 1 < H - MP + 1) return false;   // none
+    }
+    return k > 0 && H - k <= M;
+}
+
 // inverse transform of one field: modes X[0..M] (staged) -> grid pairs in registers
-template <int T>
+template <int T, int MP = 0>
 __device__ __forceinline__ void ring_inverse_regs(const float2* X, int M, const float2* twN, const float2* tws,
                                                   float2* buf, int t, float2 (&a)[EL]) {
     constexpr int H = EL * T;
@@ -549,77 +607,107 @@ __device__ __forceinline__ void ring_inverse_regs(const float2* X, int M, const 
     for (int b = 0; b < 3; ++b)
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            const int k = t + T * (b + 3 * r);
-            float2 xa = (k <= M) ? X[k] : f2(0.f, 0.f);
-            if (k == 0) xa.y = 0.f;                         // the m = 0 mode is real
-            const float2 xb = (k > 0 && H - k <= M) ? X[H - k] : f2(0.f, 0.f);
+            const int c = b + 3 * r;
+            const int k = t + T * c;
+            float2 xa = mode_in<T, MP>(k, c, M) ? X[k] : f2(0.f, 0.f);
+            if (c == 0 && t == 0) xa.y = 0.f;               // the m = 0 mode is real
+            const float2 xb = partner_in<T, MP>(k, c, M) ? X[H - k] : f2(0.f, 0.f);
             const float2 e = f2(twN[k].x, -twN[k].y);      // e^{+i theta_k}, theta_k = 2 pi k / (2H)
             const float2 s1 = cadd(xa, cconj(xb)), d1 = csub(xa, cconj(xb));
             a[b * 4 + r] = cadd(s1, cmul_si<1>(cmul(e, d1)));
         }
-    __syncwarp();                                          // buf free (previous transform done)
+    ring_sync<T>();                                          // buf free (previous transform done)
     if constexpr (T == 32) {
         spass<T, 4, 1, +1, false, true, -1, 2>(a, buf, nullptr, t);
-        __syncwarp();
+        ring_sync<T>();
         spass<T, 4, 4, +1, true, true, 2, 4>(a, buf, tws + L::i1, t);
-        __syncwarp();
+        ring_sync<T>();
         spass<T, 2, 16, +1, true, true, 4, 0>(a, buf, tws + L::i2, t);
-        __syncwarp();
+        ring_sync<T>();
         spass<T, 12, 32, +1, true, false, 0, -1>(a, buf, tws + L::i3, t);
         return;
     }
     spass<T, 4, 1, +1, false, true>(a, buf, nullptr, t);
-    __syncwarp();
-    if constexpr (T == 16) {
+    ring_sync<T>();
+    if constexpr (T == 64) {
         spass<T, 4, 4, +1, true, true>(a, buf, tws + L::i1, t);
-        __syncwarp();
+        ring_sync<T>();
+        spass<T, 4, 16, +1, true, true>(a, buf, tws + L::i2, t);
+        ring_sync<T>();
+        spass<T, 12, 64, +1, true, false>(a, buf, tws + L::i3, t);
+    } else if constexpr (T == 16) {
+        spass<T, 4, 4, +1, true, true>(a, buf, tws + L::i1, t);
+        ring_sync<T>();
         spass<T, 12, 16, +1, true, false>(a, buf, tws + L::i2, t);
     } else {
         spass<T, 2, 4, +1, true, true>(a, buf, tws + L::i1, t);
-        __syncwarp();
+        ring_sync<T>();
         spass<T, 12, 8, +1, true, false>(a, buf, tws + L::i2, t);
     }
     // register q now holds grid pair n = t + T q
 }
 
 // forward transform of one field from the grid pairs in registers -> modes X[0..M] (scaled)
-template <int T>
+template <int T, int MP = 0>
 __device__ __forceinline__ void ring_forward_regs(float2 (&a)[EL], int M, const float2* twN, const float2* tws,
                                                   float2* buf, int t, float scale, float2* X) {
     using L = RingTw<T>;
     grid_to_forward_order<T>(a);                           // a arrives in grid order (n = t + T q)
-    __syncwarp();
+    ring_sync<T>();
     if constexpr (T == 32) {
         spass<T, 2, 1, -1, false, true, -1, 1>(a, buf, nullptr, t);
-        __syncwarp();
+        ring_sync<T>();
         spass<T, 4, 2, -1, true, true, 1, 3>(a, buf, tws + L::f1, t);
-        __syncwarp();
+        ring_sync<T>();
         spass<T, 4, 8, -1, true, true, 3, 5>(a, buf, tws + L::f2, t);
-        __syncwarp();
+        ring_sync<T>();
         spass<T, 12, 32, -1, true, false, 5, -1>(a, buf, tws + L::f3, t);
+    } else if constexpr (T == 64) {
+        spass<T, 4, 1, -1, false, true>(a, buf, nullptr, t);
+        ring_sync<T>();
+        spass<T, 4, 4, -1, true, true>(a, buf, tws + L::f1, t);
+        ring_sync<T>();
+        spass<T, 4, 16, -1, true, true>(a, buf, tws + L::f2, t);
+        ring_sync<T>();
+        spass<T, 12, 64, -1, true, false>(a, buf, tws + L::f3, t);
     } else if constexpr (T == 16) {
         spass<T, 4, 1, -1, false, true>(a, buf, nullptr, t);
-        __syncwarp();
+        ring_sync<T>();
         spass<T, 4, 4, -1, true, true>(a, buf, tws + L::f1, t);
-        __syncwarp();
+        ring_sync<T>();
         spass<T, 12, 16, -1, true, false>(a, buf, tws + L::f2, t);
     } else {
         spass<T, 2, 1, -1, false, true>(a, buf, nullptr, t);
-        __syncwarp();
+        ring_sync<T>();
         spass<T, 4, 2, -1, true, true>(a, buf, tws + L::f1, t);
-        __syncwarp();
+        ring_sync<T>();
         spass<T, 12, 8, -1, true, false>(a, buf, tws + L::f2, t);
     }
     const int partner = (T - t) & (T - 1);
+    if constexpr (T > 32) {
+        // the partner lane is in the other warp of the ring: exchange through the ring buffer
+        // (after the last pass's loads from it)
+        ring_sync<T>();
+#pragma unroll
+        for (int r = 0; r < EL; ++r) buf[padi(t + T * r)] = a[r];
+        ring_sync<T>();
+    }
 #pragma unroll
     for (int r = 0; r < EL; ++r) {
+        if constexpr (MP > 0) {
+            if (T * r >= MP) continue;                      // no lane keeps a mode of this r
+        }
         // Z_{H-k}: lane T - t, register 11 - r (t >= 1); lane 0: its own register (12 - r) mod 12
         float2 zp;
-        zp.x = __shfl_sync(0xffffffffu, a[EL - 1 - r].x, partner, T);
-        zp.y = __shfl_sync(0xffffffffu, a[EL - 1 - r].y, partner, T);
-        if (t == 0) zp = a[(EL - r) % EL];
+        if constexpr (T > 32) {
+            zp = buf[padi(t == 0 ? T * ((EL - r) % EL) : partner + T * (EL - 1 - r))];
+        } else {
+            zp.x = __shfl_sync(0xffffffffu, a[EL - 1 - r].x, partner, T);
+            zp.y = __shfl_sync(0xffffffffu, a[EL - 1 - r].y, partner, T);
+            if (t == 0) zp = a[(EL - r) % EL];
+        }
         const int k = t + T * r;
-        if (k <= M) {
+        if (mode_in<T, MP>(k, r, M)) {
             const float2 zk = a[r], zn = cconj(zp);
             const float2 s1 = cadd(zk, zn), d1 = csub(zk, zn);
             const float2 tt = cmul_si<-1>(cmul(twN[k], d1));
@@ -644,7 +732,7 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src, bool pred)
                  : "memory");
 }
 
-template <int T>
+template <int T, int MP>
 __global__ void __launch_bounds__(128, 3) k_ring_nl_lg(const float2* __restrict__ Fin, float2* __restrict__ Fout, int M,
                                                     int nlat, int S, const float2* __restrict__ twg,
                                                     const double* __restrict__ mu, const double* __restrict__ w) {
@@ -654,6 +742,7 @@ __global__ void __launch_bounds__(128, 3) k_ring_nl_lg(const float2* __restrict_
     float2* tws = twN + 2 * H;                              // pass tables
     float2* fbuf = tws + RingTw<T>::n;                      // [G][HB]
     float2* reg = fbuf + G * HB;                            // [G][5][M+1], ring stride RS
+    if constexpr (MP > 0) M = MP - 1;
     const int Mp = M + 1, RS = ring_stride_t<T>(5 * Mp);
     const int s0 = blockIdx.x * G;
     const int j = blockIdx.y;
@@ -691,7 +780,7 @@ __global__ void __launch_bounds__(128, 3) k_ring_nl_lg(const float2* __restrict_
 #pragma unroll 1
     for (int i = 0; i < 4; ++i) {
         const int in_slot = i == 0 ? 2 : (i == 1 ? 3 : (i == 2 ? 1 : 0));
-        ring_inverse_regs<T>(R + in_slot * Mp, M, twN, tws, buf, t, a);
+        ring_inverse_regs<T, MP>(R + in_slot * Mp, M, twN, tws, buf, t, a);
         if (i < 2) {
 #pragma unroll
             for (int e = 0; e < EL; ++e) {
@@ -700,7 +789,7 @@ __global__ void __launch_bounds__(128, 3) k_ring_nl_lg(const float2* __restrict_
             }
             continue;
         }
-        __syncwarp();                                        // slots 2-3 no longer read
+        ring_sync<T>();                                      // slots 2-3 no longer read
 #pragma unroll
         for (int e = 0; e < EL; ++e) {
             park[e * T + t] = f2(a[e].x * v[e].x * ic2, a[e].y * v[e].y * ic2);
@@ -719,7 +808,7 @@ __global__ void __launch_bounds__(128, 3) k_ring_nl_lg(const float2* __restrict_
                               0.5f * (u[e].y * u[e].y + v[e].y * v[e].y) * ic2);
             }
             const int out_slot = (i == 2) ? (o == 0 ? 1 : 4) : (o == 0 ? 0 : (o == 1 ? 3 : 2));
-            ring_forward_regs<T>(a, M, twN, tws, buf, t, scale, R + out_slot * Mp);
+            ring_forward_regs<T, MP>(a, M, twN, tws, buf, t, scale, R + out_slot * Mp);
         }
     }
     __syncthreads();
@@ -740,7 +829,7 @@ __global__ void __launch_bounds__(128, 3) k_ring_nl_lg(const float2* __restrict_
 //            grid pairs stored straight from registers (lane t holds n = t + T i: coalesced)
 //   forward: grid -> Fourier; grid pairs loaded straight into the forward's register layout,
 //            modes staged in shared memory for a coalesced write (G columns per mode)
-template <int T>
+template <int T, int MP>
 __global__ void __launch_bounds__(128) k_ring_inv_lg(const float2* __restrict__ F, float* __restrict__ grid, int M,
                                                      int nlat, int C, const float2* __restrict__ twg) {
     constexpr int H = EL * T, G = 128 / T, HB = H + H / 16 + 1;
@@ -749,6 +838,7 @@ __global__ void __launch_bounds__(128) k_ring_inv_lg(const float2* __restrict__ 
     float2* tws = twN + 2 * H;
     float2* fbuf = tws + RingTw<T>::n;                      // [G][HB]
     float2* reg = fbuf + G * HB;                            // [G][M+1], ring stride RS
+    if constexpr (MP > 0) M = MP - 1;
     const int Mp = M + 1, RS = ring_stride_t<T>(Mp);
     const int c0 = blockIdx.x * G;
     const int j = blockIdx.y;
@@ -764,7 +854,7 @@ __global__ void __launch_bounds__(128) k_ring_inv_lg(const float2* __restrict__ 
     __syncthreads();
     const int t = threadIdx.x & (T - 1), g = threadIdx.x / T;
     float2 a[EL];
-    ring_inverse_regs<T>(reg + g * RS, M, twN, tws, fbuf + g * HB, t, a);
+    ring_inverse_regs<T, MP>(reg + g * RS, M, twN, tws, fbuf + g * HB, t, a);
     if (c0 + g < C) {
         float2* row = reinterpret_cast<float2*>(grid + ((int64_t)(c0 + g) * nlat + j) * (2 * H));
 #pragma unroll
@@ -772,7 +862,7 @@ __global__ void __launch_bounds__(128) k_ring_inv_lg(const float2* __restrict__ 
     }
 }
 
-template <int T>
+template <int T, int MP>
 __global__ void __launch_bounds__(128) k_ring_fwd_lg(const float* __restrict__ grid, float2* __restrict__ F, int M,
                                                      int nlat, int C, const float2* __restrict__ twg,
                                                      const double* __restrict__ w) {
@@ -782,6 +872,7 @@ __global__ void __launch_bounds__(128) k_ring_fwd_lg(const float* __restrict__ g
     float2* tws = twN + 2 * H;
     float2* fbuf = tws + RingTw<T>::n;
     float2* reg = fbuf + G * HB;                            // [G][M+1], ring stride RS
+    if constexpr (MP > 0) M = MP - 1;
     const int Mp = M + 1, RS = ring_stride_t<T>(Mp);
     const int c0 = blockIdx.x * G;
     const int j = blockIdx.y;
@@ -797,7 +888,7 @@ __global__ void __launch_bounds__(128) k_ring_fwd_lg(const float* __restrict__ g
     fill_ring_tw<T>(tws, twg);
     __syncthreads();
     const float scale = (float)(w[j] / (double)(2 * H));
-    ring_forward_regs<T>(a, M, twN, tws, fbuf + g * HB, t, scale, reg + g * RS);
+    ring_forward_regs<T, MP>(a, M, twN, tws, fbuf + g * HB, t, scale, reg + g * RS);
     __syncthreads();
     for (int q = threadIdx.x; q < Mp * G; q += blockDim.x) {
         const int gg = q % G, m = q / G;
@@ -805,21 +896,28 @@ __global__ void __launch_bounds__(128) k_ring_fwd_lg(const float* __restrict__ g
     }
 }
 
-template <int T>
-static swe_status ring_plain_lg(const swe_plan* p, const void* in, void* out, int C, bool inverse, cudaStream_t st) {
+template <int T, int MP>
+static swe_status ring_plain_lg_mp(const swe_plan* p, const void* in, void* out, int C, bool inverse, cudaStream_t st) {
     constexpr int H = EL * T, G = 128 / T, HB = H + H / 16 + 1;
     const size_t sm = (2 * (size_t)H + RingTw<T>::n + (size_t)G * HB + (size_t)G * ring_stride_t<T>(p->M + 1)) * sizeof(float2);
     dim3 g((C + G - 1) / G, p->nlat);
     if (inverse) {
-        SWE_CHECK_CUDA(cudaFuncSetAttribute(k_ring_inv_lg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_ring_inv_lg<T><<<g, 128, sm, st>>>((const float2*)in, (float*)out, p->M, p->nlat, C, p->twf);
+        SWE_CHECK_CUDA(cudaFuncSetAttribute(k_ring_inv_lg<T, MP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_ring_inv_lg<T, MP><<<g, 128, sm, st>>>((const float2*)in, (float*)out, p->M, p->nlat, C, p->twf);
         SWE_CHECK_LAUNCH("k_ring_inv_lg");
     } else {
-        SWE_CHECK_CUDA(cudaFuncSetAttribute(k_ring_fwd_lg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_ring_fwd_lg<T><<<g, 128, sm, st>>>((const float*)in, (float2*)out, p->M, p->nlat, C, p->twf, p->w);
+        SWE_CHECK_CUDA(cudaFuncSetAttribute(k_ring_fwd_lg<T, MP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_ring_fwd_lg<T, MP><<<g, 128, sm, st>>>((const float*)in, (float2*)out, p->M, p->nlat, C, p->twf, p->w);
         SWE_CHECK_LAUNCH("k_ring_fwd_lg");
     }
     return SWE_OK;
+}
+
+// the 3/2-rule truncation of the grid (M + 1 = 2 H / 3 = 8 T) is compiled with M fixed
+template <int T>
+static swe_status ring_plain_lg(const swe_plan* p, const void* in, void* out, int C, bool inverse, cudaStream_t st) {
+    if (p->M + 1 == 8 * T) return ring_plain_lg_mp<T, 8 * T>(p, in, out, C, inverse, st);
+    return ring_plain_lg_mp<T, 0>(p, in, out, C, inverse, st);
 }
 
 // the lane-group kernels serve FP32 plans with nlon / 2 = 12 T whose two mode slots cover a ring
@@ -827,7 +925,7 @@ static int ring_lg_T(const swe_plan* p) {
     if (p->prec == SWE_FP64) return 0;
     const int H = p->nlon / 2;
     if (2 * (p->M + 1) < H) return 0;
-    return H == 96 ? 8 : (H == 192 ? 16 : (H == 384 ? 32 : 0));
+    return H == 96 ? 8 : (H == 192 ? 16 : (H == 384 ? 32 : (H == 768 ? 64 : 0)));
 }
 
 constexpr int RING_G = 4;   // columns per block in the plain transforms
@@ -925,7 +1023,8 @@ swe_status ring_inverse(const swe_plan* p, const void* F, void* grid, int C, cud
         ProfToken tk = prof_begin("ring_inv", st, 0.0, 4.0 * (double)C * p->nlat * (2.0 * (p->M + 1) + p->nlon));
         const swe_status r = lgT == 8    ? ring_plain_lg<8>(p, F, grid, C, true, st)
                              : lgT == 16 ? ring_plain_lg<16>(p, F, grid, C, true, st)
-                                         : ring_plain_lg<32>(p, F, grid, C, true, st);
+                             : lgT == 32 ? ring_plain_lg<32>(p, F, grid, C, true, st)
+                                         : ring_plain_lg<64>(p, F, grid, C, true, st);
         prof_end(tk, st);
         return r;
     }
@@ -952,7 +1051,8 @@ swe_status ring_forward(const swe_plan* p, const void* grid, void* F, int C, cud
         ProfToken tk = prof_begin("ring_fwd", st, 0.0, 4.0 * (double)C * p->nlat * (2.0 * (p->M + 1) + p->nlon));
         const swe_status r = lgT == 8    ? ring_plain_lg<8>(p, grid, F, C, false, st)
                              : lgT == 16 ? ring_plain_lg<16>(p, grid, F, C, false, st)
-                                         : ring_plain_lg<32>(p, grid, F, C, false, st);
+                             : lgT == 32 ? ring_plain_lg<32>(p, grid, F, C, false, st)
+                                         : ring_plain_lg<64>(p, grid, F, C, false, st);
         prof_end(tk, st);
         return r;
     }
@@ -1034,16 +1134,22 @@ swe_status ring_run(const swe_plan* p, int id, int G, const void* Fin, void* Fou
 }  // namespace
 
 // lane-group FP32 kernel for H = 12 T, T in {8, 16, 32}
-template <int T>
-static swe_status ring_lg_launch(const swe_plan* p, const void* Fin, void* Fout, int S, cudaStream_t st) {
+template <int T, int MP>
+static swe_status ring_lg_launch_mp(const swe_plan* p, const void* Fin, void* Fout, int S, cudaStream_t st) {
     constexpr int H = EL * T, G = 128 / T, HB = H + H / 16 + 1;
     const size_t sm =
         (2 * (size_t)H + RingTw<T>::n + (size_t)G * HB + (size_t)G * ring_stride_t<T>(5 * (p->M + 1))) * sizeof(float2);
-    SWE_CHECK_CUDA(cudaFuncSetAttribute(k_ring_nl_lg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    SWE_CHECK_CUDA(cudaFuncSetAttribute(k_ring_nl_lg<T, MP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     dim3 g((S + G - 1) / G, p->nlat);
-    k_ring_nl_lg<T><<<g, 128, sm, st>>>((const float2*)Fin, (float2*)Fout, p->M, p->nlat, S, p->twf, p->mu, p->w);
+    k_ring_nl_lg<T, MP><<<g, 128, sm, st>>>((const float2*)Fin, (float2*)Fout, p->M, p->nlat, S, p->twf, p->mu, p->w);
     SWE_CHECK_LAUNCH("k_ring_nl_lg");
     return SWE_OK;
+}
+
+template <int T>
+static swe_status ring_lg_launch(const swe_plan* p, const void* Fin, void* Fout, int S, cudaStream_t st) {
+    if (p->M + 1 == 8 * T) return ring_lg_launch_mp<T, 8 * T>(p, Fin, Fout, S, st);
+    return ring_lg_launch_mp<T, 0>(p, Fin, Fout, S, st);
 }
 
 swe_status ring_nonlinear(const swe_plan* pc, const void* Fin, void* Fout, int S, cudaStream_t st) {
@@ -1055,9 +1161,10 @@ swe_status ring_nonlinear(const swe_plan* pc, const void* Fin, void* Fout, int S
         const double by = 8.0 * 9.0 * (p->M + 1.0) * p->nlat * S;
         const double fl = ((9.0 * 2.5 * log2((double)p->nlon)) + 30.0) * p->nlon * (double)p->nlat * S;
         ProfToken tk = prof_begin("ring_nl_f32", st, fl, by);
-        swe_status r = H == 96 ? ring_lg_launch<8>(p, Fin, Fout, S, st)
-                               : (H == 192 ? ring_lg_launch<16>(p, Fin, Fout, S, st)
-                                           : ring_lg_launch<32>(p, Fin, Fout, S, st));
+        swe_status r = H == 96    ? ring_lg_launch<8>(p, Fin, Fout, S, st)
+                       : H == 192 ? ring_lg_launch<16>(p, Fin, Fout, S, st)
+                       : H == 384 ? ring_lg_launch<32>(p, Fin, Fout, S, st)
+                                  : ring_lg_launch<64>(p, Fin, Fout, S, st);
         prof_end(tk, st);
         return r;
     }
