@@ -74,7 +74,7 @@ METRIC = "SWE slice-steps/s at T255"
 # DRAM bytes / algorithmic bytes of a kernel, from one ncu capture of that kernel (dram__bytes
 # read + write over the algorithmic bytes of the same launch); valid only while the kernel is
 # unchanged since that capture
-NCU_TRAFFIC_RATIO = {"ring_nl_f32": (0.807, "ncu capture of k_ring_nl_lg, T255, 32 states, scaled per ring")}
+NCU_TRAFFIC_RATIO = {"ring_nl_f32": (0.804, "ncu capture of k_ring_nl_lg<32, 256>, T255, 32 states, scaled per ring")}
 FP64_PEAK_TFLOPS = 1.25           # nominal dense FP64 rate of GB300
 R_NORM = 32                       # spectral resolution of the error norm (Eq. 21), as in the paper's figures
 
@@ -540,6 +540,7 @@ def measure(args, prec_name, rank, world, local, with_e2e=True):
     ms = slowest_rank(e0.elapsed_time(e1) / args.steps, world, dev)
     res = {"ms": ms, "value": world * fine_steps / (ms / 1000.0), "launches": launches, "stats": stats,
            "clocks": clk, "norms": norms, "fine_steps": fine_steps,
+           "tuning": {"level0": plan.tuning(), "coarse": cplan.tuning()},
            "problem_steps_per_s": world * (S * NF if args.workload == "parareal" else N0_MG) / (ms / 1000.0)}
     if with_e2e:
         # end to end through the public API with host buffers: the iteration's state
@@ -769,6 +770,7 @@ def run_ours(args):
         "roofline": roofline(r["stats"]),
         "clocks": r["clocks"],
         "convergence_norms": r["norms"],
+        "tuning": r["tuning"],
         "fine_steps_per_iteration": r["fine_steps"],
         "problem_steps_per_s": r["problem_steps_per_s"],
     }
@@ -997,12 +999,12 @@ def run_bumps(args):
 PARA_CONFIGS = {
     # T127, 64 slices over 2 days, fine 60 s, coarse IMEX 900 s with 4th-order hyperviscosity
     # 1e14 m^4/s as configured, then the 4th-order values of the paper's §5.2 viscosity study
-    # (1e15, 1e16 m^4/s) while the iteration goes non-finite: at 900 s the explicit Heun
+    # (1e15, 1e16, 1e17 m^4/s) while the iteration goes non-finite: at 900 s the explicit Heun
     # advection of the coarse step has |lambda dt| ~ 1.4 at n = 127 for 80 m/s winds, a growth
     # of ~1.4 per step that only the larger coefficients damp
     "config2": dict(workload="t127_parareal_s64", M=127, grid=(192, 384), S=64, days=2, nf=45, Mc=127,
-                    cgrid=(192, 384), nc=3, q=4, nus=(1.0e14, 1.0e15, 1.0e16), bump=False, iters=4, fp64_iters=4,
-                    fp64_serial=True, seed=2),
+                    cgrid=(192, 384), nc=3, q=4, nus=(1.0e14, 1.0e15, 1.0e16, 1.0e17), bump=False, iters=4,
+                    fp64_iters=4, fp64_serial=True, seed=2),
     # T511, 256 slices over 3 days, fine ~29.78 s (34 per slice), coarse on T255 with 12 steps
     # per slice and hyperviscosity scaled from the T255 workload's coarse level, plus a 120 m bump
     "config4": dict(workload="t511_parareal_s256", M=511, grid=(768, 1536), S=256, days=3, nf=34, Mc=255,
@@ -1077,10 +1079,15 @@ def _para_run(cfg, prec_name, nu, U0, local):
         record()
         clocks = ClockSampler(local)
         clocks.start()
-        for _ in range(K):
+        for k in range(K):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            it.iterate(1)
+            try:
+                it.iterate(1)
+            except swe.SWEError as exc:
+                exc.iteration, exc.history = k + 1, list(hist)
+                clocks.stop()
+                raise
             e1.record(stream)
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
@@ -1092,10 +1099,16 @@ def _para_run(cfg, prec_name, nu, U0, local):
                "ms_per_iteration": ms, "serial_fine_seconds": t_serial, "error_vs_serial_fine": hist,
                "clocks": clk}
         if prec_name == "mixed":
+            res["tuning"] = {"fine": plan.tuning(), "coarse": cplan.tuning()}
             # kernel shares of one more (uncaptured, per-launch timed) iteration, after the timed ones
             swe.prof_reset()
             swe.prof_enable(True)
-            it.iterate(1)
+            try:
+                it.iterate(1)
+            except swe.SWEError as exc:      # an attempt must also survive this iteration
+                swe.prof_enable(False)
+                exc.iteration, exc.history = K + 1, list(hist)
+                raise
             torch.cuda.synchronize()
             swe.prof_enable(False)
             stats = swe.prof_stats()
@@ -1139,7 +1152,9 @@ def run_parareal_config(args):
         except swe.SWEError as e:
             if e.status != swe.SWE_EUNSTABLE:
                 raise
-            unstable.append({"coarse_nu": nu, "precision": "mixed", "status": str(e)})
+            unstable.append({"coarse_nu": nu, "precision": "mixed", "status": str(e),
+                             "non_finite_at_iteration": getattr(e, "iteration", None),
+                             "error_vs_serial_fine_before": getattr(e, "history", None)})
     if mixed is None:
         raise RuntimeError("every coarse hyperviscosity candidate went non-finite: %s" % unstable)
     nu = mixed[0]["coarse_nu"]

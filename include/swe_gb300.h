@@ -119,6 +119,24 @@ swe_status swe_plan_destroy(swe_plan_t plan);
 typedef enum { SWE_NPHI_FLUX = 0, SWE_NPHI_ADVECTIVE = 1 } swe_nphi_form;
 swe_status swe_plan_set_nphi_form(swe_plan_t plan, int form);
 
+/* Kernel variant of the split-precision tensor-core Legendre contractions (§2.2) of a plan:
+ *   SWE_LEGENDRE_AUTO (default): per direction and column count, the first call outside CUDA
+ *     stream capture runs both variants twice on its own operands, times them with CUDA events
+ *     on the call's stream (it synchronises that stream once) and keeps the faster; a call
+ *     under capture before that takes the persistent kernel;
+ *   SWE_LEGENDRE_PERSISTENT: one CTA per SM walks all (column tile, m, N tile) work items,
+ *     with two TMEM accumulator sets so that one item's epilogue overlaps the next's MMAs;
+ *   SWE_LEGENDRE_PER_TILE: one CTA per work item.
+ * Both variants issue the same MMAs in the same order per item: their results are identical.
+ * Host-side setting; SWE_EINVAL for another value. */
+typedef enum { SWE_LEGENDRE_AUTO = 0, SWE_LEGENDRE_PERSISTENT = 1, SWE_LEGENDRE_PER_TILE = 2 } swe_legendre_mode;
+swe_status swe_plan_set_legendre_mode(swe_plan_t plan, int mode);
+
+/* Launch configurations the plan has chosen so far (fused ring kernel, Legendre variant per
+ * direction and column count with the measured times), as a NUL-terminated text in the HOST
+ * buffer buf of len bytes (truncated to fit).  SWE_EINVAL for a null plan or buffer. */
+swe_status swe_plan_tuning(swe_plan_t plan, char* buf, size_t len);
+
 /* Copies the Gauss-Legendre nodes mu_j (north to south) and weights w_j into
  * HOST arrays of nlat doubles.  Synchronises. */
 swe_status swe_plan_gauss(swe_plan_t plan, double* mu_host, double* w_host);

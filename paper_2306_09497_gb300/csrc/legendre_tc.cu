@@ -32,6 +32,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <string>
 #include <vector>
 
 #include "swe_internal.cuh"
@@ -52,7 +53,6 @@ constexpr int NR_FWD = 4;        // raw data-operand prefetch depth, forward (FP
 constexpr int NT_MAX = 224;      // largest N tile (two parity accumulators + a 32-column read fit in 512)
 constexpr int NB_MAX = 4;        // table-tile ring depth (set per plan from the shared-memory budget)
 
-__constant__ int c_terms[NTERMS][2] = {{0, 0}, {0, 1}, {1, 0}, {0, 2}, {2, 0}, {1, 1}};
 
 // ----------------------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -251,16 +251,20 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 // 2 parities x 6 partial products of one chunk into the two accumulators
+// (the descriptors' start-address field is the shared-memory address / 16, 14 bits: the
+// planes' descriptors are the stage's plus the plane offset / 16, which never carries out)
 __device__ __forceinline__ void issue_mmas(const unsigned char* sA, uint32_t a_plane, const unsigned char* sB,
                                            uint32_t b_plane, uint32_t tmem, int acc_stride, uint32_t idesc,
                                            bool first) {
+    constexpr int ta[NTERMS] = {0, 0, 1, 0, 2, 1}, tb[NTERMS] = {0, 1, 0, 2, 0, 1};
+    const uint64_t da = smem_desc(sA, 128, 256), db = smem_desc(sB, 128, 256);
 #pragma unroll
     for (int par = 0; par < 2; ++par) {
+#pragma unroll
         for (int t = 0; t < NTERMS; ++t) {
-            const unsigned char* a = sA + par * NPLANE * a_plane + c_terms[t][0] * a_plane;
-            const unsigned char* b = sB + par * NPLANE * b_plane + c_terms[t][1] * b_plane;
-            mma_bf16(tmem + par * acc_stride, smem_desc(a, 128, 256), smem_desc(b, 128, 256), idesc,
-                     (!first || t > 0) ? 1u : 0u);
+            const uint64_t a = da + (uint64_t)(((uint32_t)(par * NPLANE + ta[t]) * a_plane) >> 4);
+            const uint64_t b = db + (uint64_t)(((uint32_t)(par * NPLANE + tb[t]) * b_plane) >> 4);
+            mma_bf16(tmem + par * acc_stride, a, b, idesc, (!first || t > 0) ? 1u : 0u);
         }
     }
 }
@@ -390,14 +394,16 @@ __device__ __forceinline__ void ws_control(WS* ws, unsigned char* sA0, uint32_t 
 
 // converter side of chunk q, after its planes are stored: make them visible to the
 // tensor core and signal (one lane per warp)
-__device__ __forceinline__ void ws_planes_ready(WS* ws, int q, int lane) {
+template <typename W>
+__device__ __forceinline__ void ws_planes_ready(W* ws, int q, int lane) {
     fence_proxy_async();
     __syncwarp();
     if (lane == 0) mbar_arrive(&ws->a_full[q & 1]);
 }
 
 // converter warp: wait (lane 0) for a barrier phase, broadcast the outcome
-__device__ __forceinline__ bool ws_warp_wait(WS* ws, uint64_t* bar, uint32_t parity, int lane) {
+template <typename W>
+__device__ __forceinline__ bool ws_warp_wait(W* ws, uint64_t* bar, uint32_t parity, int lane) {
     bool ok = true;
     if (lane == 0) ok = ws_wait(bar, parity, &ws->abort);
     return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
@@ -405,7 +411,8 @@ __device__ __forceinline__ bool ws_warp_wait(WS* ws, uint64_t* bar, uint32_t par
 
 // converter warp: every lane waits for a TMA-filled raw stage (each lane then sees the
 // tile's bytes); the warp gives up together if any lane does
-__device__ __forceinline__ bool ws_raw_wait(WS* ws, uint64_t* bar, uint32_t parity) {
+template <typename W>
+__device__ __forceinline__ bool ws_raw_wait(W* ws, uint64_t* bar, uint32_t parity) {
     const bool ok = ws_wait(bar, parity, &ws->abort);
     return __all_sync(0xffffffffu, ok) != 0;
 }
@@ -690,6 +697,400 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_fwd_tc(const float* __restrict__
     tmem_release(tmem, tid);
 }
 
+// ----------------------------------------------------------------------------- persistent kernels
+// One CTA per SM walks a list of work items (column tile, wavenumber m, N tile) round-robin
+// (CTA b takes items b, b + G, b + 2G, ...; the items are ordered by decreasing K so that the
+// longest come first).  The K chunks of all its items form one continuous pipeline:
+//   converter warps 0-15: as in the per-tile kernels, chunk after chunk across items;
+//   control warp 16, one lane: raw TMA tiles NR chunks ahead and table tiles NB - 2 chunks
+//     ahead across item boundaries; the MMAs of item i go to accumulator set i mod 2 (TMEM
+//     columns 256 (i mod 2) ..), after "acc_empty" of that set shows the epilogue of item
+//     i - 2 done; after the item's last chunk it commits to "acc_full" of the set;
+//   epilogue warps 17-20 (TMEM lane quarter = warp mod 4): wait "acc_full" of item i, read
+//     the accumulators, write the result, fence, arrive on "acc_empty".
+// So the epilogue of one item and the set-up of the next overlap the MMAs of the next, and the
+// CTA's prologue (barriers, TMEM allocation, first copies) is paid once per SM.  Every wait is
+// bounded as in the per-tile kernels.
+constexpr int NEPI = 4;                       // epilogue warps
+constexpr int NTHP = NCV + 32 + 32 * NEPI;    // 672 threads
+// Accumulator sets: two of 256 TMEM columns when both parities of an item fit in 256 (N tile
+// <= 128), else one set of all 512 (then item i + 1's MMAs wait for item i's epilogue, while
+// its copies and conversions still run ahead).  Item i uses set i mod nsets.
+
+struct WSP {
+    uint64_t a_full[2], a_empty[2], b_full[NB_MAX], b_empty[NB_MAX];
+    uint64_t acc_full[2], acc_empty[2];
+    uint64_t r_full[NR_MAX];
+    int abort;
+    uint32_t tmem_slot;
+};
+
+__device__ __forceinline__ uint32_t wsp_setup(WSP* ws, int tid) {
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&ws->a_full[i], NCV / 32);
+            mbar_init(&ws->a_empty[i], 1);
+            mbar_init(&ws->acc_full[i], 1);
+            mbar_init(&ws->acc_empty[i], NEPI);
+        }
+        for (int i = 0; i < NB_MAX; ++i) {
+            mbar_init(&ws->b_full[i], 1);
+            mbar_init(&ws->b_empty[i], 1);
+        }
+        for (int i = 0; i < NR_MAX; ++i) mbar_init(&ws->r_full[i], 1);
+        ws->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if ((tid >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ws->tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    return ws->tmem_slot;
+}
+
+// Work item of a persistent launch: pair list entry (m | z << 16) and column tile x.
+struct PItem {
+    int m, z, x, nq;
+};
+
+// Per-direction parameters the control lane needs for item `it`.
+struct PInv {
+    const unsigned char* B;
+    const long long* off;
+    const int* nqm;
+    const int* pairs;
+    int nx, M, nt, ntl;
+    __device__ __forceinline__ PItem item(int it) const {
+        const int pr = pairs[it / nx];
+        PItem r{pr & 0xFFFF, pr >> 16, it % nx, 0};
+        r.nq = nqm[r.m];
+        return r;
+    }
+    __device__ __forceinline__ uint32_t nt_of(const PItem&) const { return (uint32_t)nt; }
+    __device__ __forceinline__ int acc_of(const PItem&) const { return nt; }
+    // table tile of chunk q: tiles ordered (q, z, par, plane), ntl tiles per chunk
+    __device__ __forceinline__ const unsigned char* btile(const PItem& w, int q, uint32_t& bytes) const {
+        const uint32_t bs = 2 * NPLANE * (uint32_t)nt * KC * 2;
+        bytes = bs;
+        return B + off[w.m] + ((int64_t)q * ntl + w.z) * bs;
+    }
+    __device__ __forceinline__ void raw(const CUtensorMap* map, unsigned char* dst, const PItem& w, int q,
+                                        uint64_t* bar) const {
+        tma_load_2d(dst, map, w.x * BM, (int)ex_off(w.m, M) + 32 * q, bar);
+    }
+};
+struct PFwd {
+    const unsigned char* B;
+    const long long* off;
+    const int* nzm;
+    const int* ntm;
+    const int* pairs;
+    int nx, M, nlat, nq;
+    __device__ __forceinline__ PItem item(int it) const {
+        const int pr = pairs[it / nx];
+        return PItem{pr & 0xFFFF, pr >> 16, it % nx, nq};
+    }
+    __device__ __forceinline__ uint32_t nt_of(const PItem& w) const { return (uint32_t)ntm[w.m]; }
+    __device__ __forceinline__ int acc_of(const PItem& w) const { return (ntm[w.m] + 31) & ~31; }
+    __device__ __forceinline__ const unsigned char* btile(const PItem& w, int q, uint32_t& bytes) const {
+        const uint32_t bs = 2 * NPLANE * (uint32_t)ntm[w.m] * KC * 2;
+        bytes = bs;
+        return B + off[w.m] + ((int64_t)q * nzm[w.m] + w.z) * bs;
+    }
+    __device__ __forceinline__ void raw(const CUtensorMap* map, unsigned char* dst, const PItem& w, int q,
+                                        uint64_t* bar) const {
+        tma_load_2d(dst, map, w.x * BM, w.m * nlat + 16 * q, bar);
+        tma_load_2d(dst + KC * BM * 4, map, w.x * BM, w.m * nlat + nlat - 16 * (q + 1), bar);
+    }
+};
+
+// Walks the (item, chunk) sequence of this CTA: items blockIdx.x + i gridDim.x, chunks 0..nq-1.
+template <typename D>
+struct PCursor {
+    const D* d;
+    int nitems, i = 0, q = 0, g = 0;
+    PItem w{};
+    bool done = false;
+    __device__ __forceinline__ void start(const D* dd, int n) {
+        d = dd;
+        nitems = n;
+        load();
+    }
+    // (every item has at least one chunk: the host builds no other)
+    __device__ __forceinline__ void load() {
+        const int it = (int)blockIdx.x + i * (int)gridDim.x;
+        if (it >= nitems) {
+            done = true;
+            return;
+        }
+        w = d->item(it);
+    }
+    __device__ __forceinline__ void next() {
+        ++g;
+        if (++q >= w.nq) {
+            q = 0;
+            ++i;
+            load();
+        }
+    }
+};
+
+// control lane of a persistent launch
+template <typename D>
+__device__ __forceinline__ void wsp_control(WSP* ws, const D& d, int nitems, const CUtensorMap* map,
+                                            unsigned char* sA0, uint32_t a_stage, uint32_t a_plane, unsigned char* sB0,
+                                            uint32_t b_stride, int NB, unsigned char* raw, uint32_t raw_stage, int NR,
+                                            uint32_t tmem, int nsets) {
+    volatile int* ab = &ws->abort;
+    PCursor<D> rc, bc, mc;               // raw tiles, table tiles, MMAs
+    rc.start(&d, nitems);
+    bc.start(&d, nitems);
+    mc.start(&d, nitems);
+    auto issue_raw = [&]() {
+        uint64_t* bar = &ws->r_full[rc.g % NR];
+        mbar_expect_tx(bar, raw_stage);
+        d.raw(map, raw + (size_t)(rc.g % NR) * raw_stage, rc.w, rc.q, bar);
+        rc.next();
+    };
+    for (int c = 0; c < NR && !rc.done; ++c) issue_raw();
+    const int D_AHEAD = NB - 2;
+    bool ok = true;
+    auto issue_b = [&]() {
+        if (bc.g >= NB) {
+            ok = ws_wait(&ws->b_empty[bc.g % NB], ((bc.g / NB) - 1) & 1, ab);
+            if (!ok) return;
+        }
+        uint32_t bytes;
+        const unsigned char* src = d.btile(bc.w, bc.q, bytes);
+        mbar_expect_tx(&ws->b_full[bc.g % NB], bytes);
+        bulk_g2s(sB0 + (size_t)(bc.g % NB) * b_stride, src, bytes, &ws->b_full[bc.g % NB]);
+        bc.next();
+    };
+    while (ok && !bc.done && bc.g < D_AHEAD) issue_b();
+    int last_mma = -1, item_i = -1;
+    uint32_t idesc = 0, acc_base = 0;
+    int acc_stride = 0;
+    while (ok && !mc.done) {
+        if (mc.q == 0) {                                  // first chunk of local item mc.i
+            item_i = mc.i;
+            const int s = item_i % nsets;
+            if (item_i >= nsets) {
+                ok = ws_wait(&ws->acc_empty[s], ((item_i / nsets) - 1) & 1, ab);
+                if (!ok) break;
+            }
+            idesc = make_idesc((int)d.nt_of(mc.w));
+            acc_stride = d.acc_of(mc.w);
+            acc_base = tmem + (uint32_t)s * (TMEM_COLS / nsets);
+        }
+        const int g = mc.g;
+        while (ok && !bc.done && bc.g < g + D_AHEAD + 1) issue_b();
+        if (!ok) break;
+        ok = ws_wait(&ws->a_full[g & 1], (g >> 1) & 1, ab);
+        if (!ok) break;
+        if (!rc.done) issue_raw();                        // raw stage of chunk g is free again
+        ok = ws_wait(&ws->b_full[g % NB], (g / NB) & 1, ab);
+        if (!ok) break;
+        tc_fence_after();
+        issue_mmas(sA0 + (g & 1) * a_stage, a_plane, sB0 + (size_t)(g % NB) * b_stride,
+                   d.nt_of(mc.w) * KC * 2, acc_base, acc_stride, idesc, mc.q == 0);
+        mma_commit(&ws->a_empty[g & 1]);
+        mma_commit(&ws->b_empty[g % NB]);
+        last_mma = g;
+        const bool last_of_item = (mc.q + 1 >= mc.w.nq);
+        mc.next();
+        if (last_of_item) mma_commit(&ws->acc_full[item_i % nsets]);
+    }
+    if (ok) return;
+    *ab = 1;
+    // bounded drain of this CTA's own work in flight: the last MMAs, the table tiles and raw
+    // tiles issued but not consumed
+    volatile int zero = 0;
+    if (last_mma >= 0) ws_wait(&ws->a_empty[last_mma & 1], (last_mma >> 1) & 1, &zero);
+    for (int c = last_mma + 1; c < bc.g; ++c) ws_wait(&ws->b_full[c % NB], (c / NB) & 1, &zero);
+    for (int c = last_mma + 1; c < rc.g; ++c) ws_wait(&ws->r_full[c % NR], (c / NR) & 1, &zero);
+}
+
+// epilogue warp: wait for item i's accumulators (lane 0, broadcast)
+__device__ __forceinline__ bool wsp_acc_wait(WSP* ws, int i, int nsets, int lane) {
+    bool ok = true;
+    if (lane == 0) ok = ws_wait(&ws->acc_full[i % nsets], (i / nsets) & 1, &ws->abort);
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    tc_fence_after();
+    return ok;
+}
+__device__ __forceinline__ void wsp_acc_release(WSP* ws, int i, int nsets, int lane) {
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&ws->acc_empty[i % nsets]);
+}
+
+__global__ void __launch_bounds__(NTHP, 1) k_leg_inv_tcp(float* __restrict__ F, PInv d, int nitems, int ncol,
+                                                        int nlat, int nlat2, int NB, int nsets, int* err,
+                                                        const __grid_constant__ CUtensorMap tmX) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int nt = d.nt;
+    const uint32_t a_plane = BM * KC * 2;
+    const uint32_t b_plane = (uint32_t)nt * KC * 2;
+    const uint32_t a_stage = 2 * NPLANE * a_plane;
+    const uint32_t b_stage = 2 * NPLANE * b_plane;
+    const uint32_t raw_stage = 2 * KC * BM * 4;
+    unsigned char* const sA0 = smem;
+    unsigned char* sB0 = smem + 2 * a_stage;
+    float* raw = reinterpret_cast<float*>(sB0 + (size_t)NB * b_stage);   // [NR][32 rows][BM]
+    WSP* ws = reinterpret_cast<WSP*>(raw + NR_INV * 2 * KC * BM);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t tmem = wsp_setup(ws, tid);
+    if (warp == NCV / 32) {
+        if (lane == 0)
+            wsp_control(ws, d, nitems, &tmX, sA0, a_stage, a_plane, sB0, b_stage, NB,
+                        reinterpret_cast<unsigned char*>(raw), raw_stage, NR_INV, tmem, nsets);
+    } else if (warp < NCV / 32) {
+        const int col = tid & (BM - 1), sub = (tid >> 7) & 3;
+        PCursor<PInv> cc;
+        cc.start(&d, nitems);
+        while (!cc.done) {
+            const int g = cc.g, q = cc.q;
+            const int Kx = d.M + 2 - cc.w.m;
+            if (!ws_raw_wait(ws, &ws->r_full[g % NR_INV], (g / NR_INV) & 1)) break;
+            if (g >= 2 && !ws_warp_wait(ws, &ws->a_empty[g & 1], ((g - 2) >> 1) & 1, lane)) break;
+            const float* r = raw + (g % NR_INV) * (2 * KC * BM);
+#pragma unroll
+            for (int par = 0; par < 2; ++par) {
+                float v[KQ];
+#pragma unroll
+                for (int i = 0; i < KQ; ++i) {
+                    const int kk = KQ * sub + i;
+                    const float x = r[(par + 2 * kk) * BM + col];
+                    v[i] = par + 2 * (KC * q + kk) < Kx ? x : 0.f;
+                }
+                store_quad_planes(sA0 + (g & 1) * a_stage + par * NPLANE * a_plane, a_plane, col, KQ * sub, v);
+            }
+            ws_planes_ready(ws, g, lane);
+            cc.next();
+        }
+    } else {
+        // epilogue warps: TMEM lanes (= data columns) 32 (warp mod 4) .. + 31
+        const int quarter = warp & 3;
+        const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+        for (int i = 0;; ++i) {
+            const int it = (int)blockIdx.x + i * (int)gridDim.x;
+            if (it >= nitems) break;
+            const PItem w = d.item(it);
+            if (!wsp_acc_wait(ws, i, nsets, lane)) break;
+            const uint32_t base = tmem + (uint32_t)(i % nsets) * (TMEM_COLS / nsets) + lane_base;
+            const int c = w.x * BM + quarter * 32 + lane;
+            const bool cin = c < ncol;
+            const int jt0 = w.z * nt;
+            float* Fm = F + (int64_t)w.m * nlat * ncol + c;
+            for (int j0 = 0; j0 < nt; j0 += 32) {
+                float e[32], o[32];
+                tmem_ld32(base + (uint32_t)j0, e);
+                tmem_ld32(base + (uint32_t)(nt + j0), o);
+                if (cin) {
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) {
+                        const int j = jt0 + j0 + k;
+                        if (j < nlat2) {
+                            Fm[(int64_t)j * ncol] = e[k] + o[k];
+                            Fm[(int64_t)(nlat - 1 - j) * ncol] = e[k] - o[k];
+                        }
+                    }
+                }
+            }
+            wsp_acc_release(ws, i, nsets, lane);
+        }
+    }
+    __syncthreads();
+    if (ws->abort && tid == 0) atomicOr(err, PLAN_FLAG_TIMEOUT);
+    tmem_release(tmem, tid);
+}
+
+__global__ void __launch_bounds__(NTHP, 1) k_leg_fwd_tcp(float* __restrict__ Y, PFwd d, int nitems, int ncol,
+                                                        int nlat2, int b_stage_max, int NB, int nsets, int* err,
+                                                        const __grid_constant__ CUtensorMap tmF) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const uint32_t a_plane = BM * KC * 2;
+    const uint32_t a_stage = 2 * NPLANE * a_plane;
+    const uint32_t raw_stage = 2 * KC * BM * 4;
+    unsigned char* const sA0 = smem;
+    unsigned char* sB0 = smem + 2 * a_stage;               // NB stages of b_stage_max bytes
+    float* raw = reinterpret_cast<float*>(sB0 + (size_t)NB * b_stage_max);   // [NR][2 KC][BM]
+    WSP* ws = reinterpret_cast<WSP*>(raw + NR_FWD * 2 * KC * BM);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t tmem = wsp_setup(ws, tid);
+    if (warp == NCV / 32) {
+        if (lane == 0)
+            wsp_control(ws, d, nitems, &tmF, sA0, a_stage, a_plane, sB0, (uint32_t)b_stage_max, NB,
+                        reinterpret_cast<unsigned char*>(raw), raw_stage, NR_FWD, tmem, nsets);
+    } else if (warp < NCV / 32) {
+        const int col = tid & (BM - 1), sub = (tid >> 7) & 3;
+        PCursor<PFwd> cc;
+        cc.start(&d, nitems);
+        while (!cc.done) {
+            const int g = cc.g, q = cc.q;
+            if (!ws_raw_wait(ws, &ws->r_full[g % NR_FWD], (g / NR_FWD) & 1)) break;
+            if (g >= 2 && !ws_warp_wait(ws, &ws->a_empty[g & 1], ((g - 2) >> 1) & 1, lane)) break;
+            const float* r = raw + (g % NR_FWD) * (2 * KC * BM);
+            float vs[KQ], va[KQ];
+#pragma unroll
+            for (int i = 0; i < KQ; ++i) {
+                const int jj = KQ * sub + i;
+                // rows j >= nlat/2 of the last chunk are the other hemisphere's: dropped
+                const bool in = KC * q + jj < nlat2;
+                const float fn = in ? r[jj * BM + col] : 0.f;
+                const float fs = in ? r[(2 * KC - 1 - jj) * BM + col] : 0.f;
+                vs[i] = fn + fs;
+                va[i] = fn - fs;
+            }
+            store_quad_planes(sA0 + (g & 1) * a_stage, a_plane, col, KQ * sub, vs);
+            store_quad_planes(sA0 + (g & 1) * a_stage + NPLANE * a_plane, a_plane, col, KQ * sub, va);
+            ws_planes_ready(ws, g, lane);
+            cc.next();
+        }
+    } else {
+        const int quarter = warp & 3;
+        const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+        for (int i = 0;; ++i) {
+            const int it = (int)blockIdx.x + i * (int)gridDim.x;
+            if (it >= nitems) break;
+            const PItem w = d.item(it);
+            if (!wsp_acc_wait(ws, i, nsets, lane)) break;
+            const int nt = (int)d.nt_of(w), acc = d.acc_of(w);
+            const uint32_t base = tmem + (uint32_t)(i % nsets) * (TMEM_COLS / nsets) + lane_base;
+            const int c = w.x * BM + quarter * 32 + lane;
+            const bool cin = c < ncol;
+            const int kt0 = w.z * nt;
+            const int Kx = d.M + 2 - w.m;
+            float* Ym = Y + ex_off(w.m, d.M) * (int64_t)ncol + c;
+            for (int k0 = 0; k0 < nt; k0 += 32) {
+                float d0[32], d1[32];
+                tmem_ld32(base + (uint32_t)k0, d0);
+                tmem_ld32(base + (uint32_t)(acc + k0), d1);
+                if (cin) {
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) {
+                        const int kk = kt0 + k0 + k;
+                        const int r0 = 2 * kk, r1 = 2 * kk + 1;   // extended-row offsets of parities 0 / 1
+                        if (k0 + k < nt) {
+                            if (r0 < Kx) Ym[(int64_t)r0 * ncol] = d0[k];
+                            if (r1 < Kx) Ym[(int64_t)r1 * ncol] = d1[k];
+                        }
+                    }
+                }
+            }
+            wsp_acc_release(ws, i, nsets, lane);
+        }
+    }
+    __syncthreads();
+    if (ws->abort && tid == 0) atomicOr(err, PLAN_FLAG_TIMEOUT);
+    tmem_release(tmem, tid);
+}
+
 // ----------------------------------------------------------------------------- table builders
 // Inverse table: element (j, kk) of tile (m, q, tile z, par, plane) = P_{m+par+2(16q+kk)}(mu_{16... j})
 __global__ void k_build_inv_table(const double* __restrict__ P, unsigned char* __restrict__ T,
@@ -762,6 +1163,18 @@ __global__ void k_build_fwd_table(const double* __restrict__ P, unsigned char* _
 // ----------------------------------------------------------------------------- host side
 struct SplitTables {
     int nt_inv, ntiles_inv, nt_fwd, nz_fwd;   // nt_fwd, nz_fwd: largest over m
+    int* inv_pairs = nullptr;                 // persistent work lists: m | z << 16, m ascending
+    int* fwd_pairs = nullptr;
+    int n_inv_pairs = 0, n_fwd_pairs = 0;
+    size_t smem_inv_p = 0, smem_fwd_p = 0;    // persistent kernels
+    int nb_inv_p = 2, nb_fwd_p = 2;
+    // autotuned choice per direction and real column count: 1 persistent, 2 per tile, with the
+    // two measured times (ms; 0 when not measured)
+    struct Tune {
+        int ncol, choice;
+        float ms_persist, ms_tile;
+    };
+    std::vector<Tune> tune[2];                // [0] inverse, [1] forward
     unsigned char* inv = nullptr;
     unsigned char* fwd = nullptr;
     long long* inv_off = nullptr;
@@ -789,13 +1202,22 @@ static int tc_nb(int nt, size_t raw_stage, int nr) {
         if (tc_smem(nt, raw_stage, nr, nb) <= SMEM_LIMIT) return nb;
     return 0;
 }
+static size_t tcp_smem(int nt, size_t raw_stage, int nr, int nb) {
+    return tc_smem(nt, raw_stage, nr, nb) - sizeof(WS) + sizeof(WSP);
+}
+static int tcp_nb(int nt, size_t raw_stage, int nr) {
+    for (int nb = NB_MAX; nb >= 2; --nb)
+        if (tcp_smem(nt, raw_stage, nr, nb) <= SMEM_LIMIT) return nb;
+    return 0;
+}
 
 swe_status split_tables_build(swe_plan* p) {
     if (p->Pbf) return SWE_OK;
     SplitTables* t = new SplitTables();
     const int M = p->M;
-    // inverse: N tiles over the northern latitudes, at most 192 (equal tiles), so that the
-    // table stages and a three-deep FP64 prefetch ring fit in shared memory
+    // inverse: N tiles over the northern latitudes, at most 192 (equal tiles, multiples of 32
+    // for the epilogue's 32-column reads), so that the table stages and the raw prefetch ring
+    // fit in shared memory
     int ntiles = (p->nlat2 + 191) / 192;
     t->ntiles_inv = ntiles;
     t->nt_inv = round16((p->nlat2 + ntiles - 1) / ntiles);
@@ -835,6 +1257,20 @@ swe_status split_tables_build(swe_plan* p) {
     if (e == cudaSuccess) e = cudaMemcpy(t->fwd_off, foff.data(), sizeof(long long) * (M + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(t->fwd_ntiles, fnz.data(), sizeof(int) * (M + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(t->fwd_nt, fnt.data(), sizeof(int) * (M + 1), cudaMemcpyHostToDevice);
+    // work lists of the persistent kernels, m ascending (the inverse's longest K first)
+    std::vector<int> ipairs, fpairs;
+    for (int m = 0; m <= M; ++m) {
+        for (int z = 0; z < ntiles; ++z) ipairs.push_back(m | (z << 16));
+        for (int z = 0; z < fnz[m]; ++z) fpairs.push_back(m | (z << 16));
+    }
+    t->n_inv_pairs = (int)ipairs.size();
+    t->n_fwd_pairs = (int)fpairs.size();
+    if (e == cudaSuccess) e = cudaMalloc((void**)&t->inv_pairs, sizeof(int) * ipairs.size());
+    if (e == cudaSuccess) e = cudaMalloc((void**)&t->fwd_pairs, sizeof(int) * fpairs.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(t->inv_pairs, ipairs.data(), sizeof(int) * ipairs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(t->fwd_pairs, fpairs.data(), sizeof(int) * fpairs.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(t->inv);
         cudaFree(t->fwd);
@@ -843,6 +1279,8 @@ swe_status split_tables_build(swe_plan* p) {
         cudaFree(t->fwd_off);
         cudaFree(t->fwd_ntiles);
         cudaFree(t->fwd_nt);
+        cudaFree(t->inv_pairs);
+        cudaFree(t->fwd_pairs);
         delete t;
         return swe_cuda_status(e, "split tables");
     }
@@ -872,6 +1310,12 @@ swe_status split_tables_build(swe_plan* p) {
         e = cudaFuncSetAttribute(k_leg_fwd_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_fwd);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_leg_fwd_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_fwd);
+    t->nb_inv_p = tcp_nb(t->nt_inv, 2 * KC * BM * sizeof(float), NR_INV);
+    t->nb_fwd_p = tcp_nb(t->nt_fwd, 2 * KC * BM * sizeof(float), NR_FWD);
+    t->smem_inv_p = t->nb_inv_p ? tcp_smem(t->nt_inv, 2 * KC * BM * sizeof(float), NR_INV, t->nb_inv_p) : 0;
+    t->smem_fwd_p = t->nb_fwd_p ? tcp_smem(t->nt_fwd, 2 * KC * BM * sizeof(float), NR_FWD, t->nb_fwd_p) : 0;
+    if (t->smem_inv_p && t->smem_inv_p < one_per_sm) t->smem_inv_p = one_per_sm;
+    if (t->smem_fwd_p && t->smem_fwd_p < one_per_sm) t->smem_fwd_p = one_per_sm;
     p->Pbf = t;
     if (e != cudaSuccess) return swe_cuda_status(e, "split table kernels");
     return SWE_OK;
@@ -887,6 +1331,8 @@ void split_tables_free(swe_plan* p) {
     cudaFree(t->fwd_off);
     cudaFree(t->fwd_ntiles);
     cudaFree(t->fwd_nt);
+    cudaFree(t->inv_pairs);
+    cudaFree(t->fwd_pairs);
     delete t;
     p->Pbf = nullptr;
 }
@@ -927,8 +1373,61 @@ static bool encode_rows(CUtensorMap* map, const float* base, int ncol, long long
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+static int sm_count() {
+    static int n = [] {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            v = 0;
+        return v > 0 ? v : 1;
+    }();
+    return n;
+}
+
+// Kernel variant for one direction and real column count.  Mode 1 / 2 force the persistent /
+// per-tile kernel.  Mode 0: the first call with this column count outside stream capture runs
+// both variants twice on the call's own operands (the kernels only read the input and write
+// the output), times the second run of each with CUDA events on the call's stream and keeps
+// the faster; a call under capture before that takes the persistent kernel untimed.
+template <typename A, typename B>
+static swe_status legendre_choice(const swe_plan* p, SplitTables* t, int dir, int ncol, cudaStream_t st, A& persistent,
+                                  B& per_tile, int* choice) {
+    if (p->legendre_mode == 1 || p->legendre_mode == 2) {
+        *choice = p->legendre_mode;
+        return SWE_OK;
+    }
+    for (const auto& e : t->tune[dir])
+        if (e.ncol == ncol) {
+            *choice = e.choice;
+            return SWE_OK;
+        }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    SWE_CHECK_CUDA(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) {
+        *choice = 1;
+        return SWE_OK;
+    }
+    cudaEvent_t e0, e1;
+    SWE_CHECK_CUDA(cudaEventCreate(&e0));
+    SWE_CHECK_CUDA(cudaEventCreate(&e1));
+    float ms[2] = {0.f, 0.f};
+    swe_status r = SWE_OK;
+    for (int v = 0; v < 2 && r == SWE_OK; ++v)
+        for (int rep = 0; rep < 2 && r == SWE_OK; ++rep) {
+            cudaEventRecord(e0, st);
+            r = v == 0 ? persistent() : per_tile();
+            cudaEventRecord(e1, st);
+            if (r == SWE_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms[v], e0, e1);
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    SWE_CHECK(r);
+    *choice = ms[0] <= ms[1] ? 1 : 2;
+    t->tune[dir].push_back(SplitTables::Tune{ncol, *choice, ms[0], ms[1]});
+    return SWE_OK;
+}
+
 swe_status leg_inverse_split(const swe_plan* p, const float2* X, float2* F, int C, cudaStream_t st) {
-    const SplitTables* t = (const SplitTables*)p->Pbf;
+    SplitTables* t = (SplitTables*)p->Pbf;
     if (!t) {
         swe_set_error("split-precision tables missing");
         return SWE_EINVAL;
@@ -939,6 +1438,36 @@ swe_status leg_inverse_split(const swe_plan* p, const float2* X, float2* F, int 
     const double by = 8.0 * C * p->ncx + 8.0 * C * (p->M + 1.0) * p->nlat;
     alignas(64) CUtensorMap tm{};
     const bool tma = p->nlat2 >= KC && encode_rows(&tm, (const float*)X, sh.ncol, p->ncx, 2 * KC);
+    const int nx = (sh.ncol + BM - 1) / BM;
+    auto persistent = [&]() -> swe_status {
+        // one CTA per SM over (column tile, m, N tile) items
+        const int nitems = nx * t->n_inv_pairs;
+        const int grid_p = nitems < sm_count() ? nitems : sm_count();
+        PInv d{t->inv, t->inv_off, t->inv_nq, t->inv_pairs, nx, p->M, t->nt_inv, t->ntiles_inv};
+        SWE_CHECK_CUDA(cudaFuncSetAttribute(k_leg_inv_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)t->smem_inv_p));
+        const int nsets = 2 * t->nt_inv <= (int)TMEM_COLS / 2 ? 2 : 1;
+        k_leg_inv_tcp<<<grid_p, NTHP, t->smem_inv_p, st>>>((float*)F, d, nitems, sh.ncol, p->nlat, p->nlat2,
+                                                            t->nb_inv_p, nsets, p->flags, tm);
+        SWE_CHECK_LAUNCH("k_leg_inv_tcp");
+        return SWE_OK;
+    };
+    auto per_tile = [&]() -> swe_status {
+        SWE_CHECK_CUDA(cudaFuncSetAttribute(k_leg_inv_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)t->smem_inv));
+        k_leg_inv_tc<true><<<grid, NTH, t->smem_inv, st>>>((const float*)X, (float*)F, t->inv, t->inv_off, t->inv_nq,
+                                                            sh, t->nb_inv, p->flags, tm);
+        SWE_CHECK_LAUNCH("k_leg_inv_tc");
+        return SWE_OK;
+    };
+    if (tma && t->smem_inv_p) {
+        int choice = 0;
+        SWE_CHECK(legendre_choice(p, t, 0, sh.ncol, st, persistent, per_tile, &choice));
+        ProfToken tk = prof_begin("leg_inv_tc", st, fl, by);
+        const swe_status r = choice == 1 ? persistent() : per_tile();
+        prof_end(tk, st);
+        return r;
+    }
     auto kern = tma ? k_leg_inv_tc<true> : k_leg_inv_tc<false>;
     // the dynamic shared-memory limit is a per-function attribute shared by all plans: set it per launch
     SWE_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_inv));
@@ -951,7 +1480,7 @@ swe_status leg_inverse_split(const swe_plan* p, const float2* X, float2* F, int 
 }
 
 swe_status leg_forward_split(const swe_plan* p, const float2* F, float2* Y, int C, cudaStream_t st) {
-    const SplitTables* t = (const SplitTables*)p->Pbf;
+    SplitTables* t = (SplitTables*)p->Pbf;
     if (!t) {
         swe_set_error("split-precision tables missing");
         return SWE_EINVAL;
@@ -963,6 +1492,36 @@ swe_status leg_forward_split(const swe_plan* p, const float2* F, float2* Y, int 
     alignas(64) CUtensorMap tm{};
     const bool tma =
         p->nlat2 >= KC && encode_rows(&tm, (const float*)F, sh.ncol, (long long)(p->M + 1) * p->nlat, KC);
+    const int nx = (sh.ncol + BM - 1) / BM;
+    auto persistent = [&]() -> swe_status {
+        const int nitems = nx * t->n_fwd_pairs;
+        const int grid_p = nitems < sm_count() ? nitems : sm_count();
+        PFwd d{t->fwd, t->fwd_off, t->fwd_ntiles, t->fwd_nt, t->fwd_pairs, nx, p->M, p->nlat, (p->nlat2 + KC - 1) / KC};
+        const int b_stage_max = 2 * NPLANE * t->nt_fwd * KC * 2;
+        SWE_CHECK_CUDA(cudaFuncSetAttribute(k_leg_fwd_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)t->smem_fwd_p));
+        const int nsets = 2 * ((t->nt_fwd + 31) & ~31) <= (int)TMEM_COLS / 2 ? 2 : 1;
+        k_leg_fwd_tcp<<<grid_p, NTHP, t->smem_fwd_p, st>>>((float*)Y, d, nitems, sh.ncol, p->nlat2, b_stage_max,
+                                                            t->nb_fwd_p, nsets, p->flags, tm);
+        SWE_CHECK_LAUNCH("k_leg_fwd_tcp");
+        return SWE_OK;
+    };
+    auto per_tile = [&]() -> swe_status {
+        SWE_CHECK_CUDA(cudaFuncSetAttribute(k_leg_fwd_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)t->smem_fwd));
+        k_leg_fwd_tc<true><<<grid, NTH, t->smem_fwd, st>>>((const float*)F, (float*)Y, t->fwd, t->fwd_off,
+                                                            t->fwd_ntiles, t->fwd_nt, sh, t->nb_fwd, p->flags, tm);
+        SWE_CHECK_LAUNCH("k_leg_fwd_tc");
+        return SWE_OK;
+    };
+    if (tma && t->smem_fwd_p) {
+        int choice = 0;
+        SWE_CHECK(legendre_choice(p, t, 1, sh.ncol, st, persistent, per_tile, &choice));
+        ProfToken tk = prof_begin("leg_fwd_tc", st, fl, by);
+        const swe_status r = choice == 1 ? persistent() : per_tile();
+        prof_end(tk, st);
+        return r;
+    }
     auto kern = tma ? k_leg_fwd_tc<true> : k_leg_fwd_tc<false>;
     SWE_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem_fwd));
     ProfToken tk = prof_begin("leg_fwd_tc", st, fl, by);
@@ -992,5 +1551,41 @@ swe_status wait_selftest_launch(const swe_plan* p, long long polls, cudaStream_t
     const unsigned long long n = polls < 1 ? 1ull : (polls > (long long)WAIT_LIMIT ? WAIT_LIMIT : (unsigned long long)polls);
     k_wait_selftest<<<1, 32, 0, st>>>(p->flags, n);
     SWE_CHECK_LAUNCH("k_wait_selftest");
+    return SWE_OK;
+}
+
+// ----------------------------------------------------------------------------- C ABI: tuning
+extern "C" swe_status swe_plan_set_legendre_mode(swe_plan_t p, int mode) {
+    if (!p || mode < SWE_LEGENDRE_AUTO || mode > SWE_LEGENDRE_PER_TILE) {
+        swe_set_error("swe_plan_set_legendre_mode: invalid argument");
+        return SWE_EINVAL;
+    }
+    p->legendre_mode = mode;
+    return SWE_OK;
+}
+
+extern "C" swe_status swe_plan_tuning(swe_plan_t p, char* buf, size_t len) {
+    if (!p || !buf || len == 0) {
+        swe_set_error("swe_plan_tuning: invalid argument");
+        return SWE_EINVAL;
+    }
+    std::string out;
+    char tmp[160];
+    snprintf(tmp, sizeof tmp, "ring_nl: cfg %d G %d", p->ring_cfg, p->ring_G);
+    out += tmp;
+    const SplitTables* t = (const SplitTables*)p->Pbf;
+    if (t) {
+        snprintf(tmp, sizeof tmp, "; legendre mode %d, tiles inv nt %d x %d, fwd nt <= %d", p->legendre_mode, t->nt_inv,
+                 t->ntiles_inv, t->nt_fwd);
+        out += tmp;
+        for (int dir = 0; dir < 2; ++dir)
+            for (const auto& e : t->tune[dir]) {
+                snprintf(tmp, sizeof tmp, "; %s ncol %d: %s (persistent %.3f ms, per tile %.3f ms)",
+                         dir == 0 ? "inverse" : "forward", e.ncol, e.choice == 1 ? "persistent" : "per tile",
+                         e.ms_persist, e.ms_tile);
+                out += tmp;
+            }
+    }
+    snprintf(buf, len, "%s", out.c_str());
     return SWE_OK;
 }

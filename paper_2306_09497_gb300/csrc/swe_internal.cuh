@@ -146,6 +146,9 @@ struct swe_plan {
     int ring_cfg = -1, ring_G = 1;
     // geopotential tendency of N: 0 flux form -div(Phi' V), 1 advective form -V.grad Phi' - Phi' delta
     int nphi_adv = 0;
+    // split-precision Legendre contractions (swe_legendre_mode): 0 pick per column count by
+    // measured time, 1 persistent tcgen05 kernels, 2 one CTA per tile
+    int legendre_mode = 0;
     // bumped whenever a plan-owned device buffer is allocated, grown or freed after creation
     // (workspace, implicit-solve factors, SL geometry): a CUDA graph that captured pointers
     // into the plan is valid only while the generation it was captured at is current

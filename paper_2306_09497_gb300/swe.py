@@ -30,9 +30,10 @@ EXPORTED = [
     "swe_mgrit_init", "mgrit_cycle", "swe_mgrit_cpoints", "swe_server_create", "swe_server_destroy",
     "swe_server_submit", "swe_server_step", "swe_server_result", "swe_server_norms", "swe_plan_check",
     "swe_plan_inject_status", "swe_wait_selftest", "swe_error_norms", "swe_ke_spectrum", "swe_stability_region",
-    "swe_request_bytes", "swe_plan_set_nphi_form",
+    "swe_request_bytes", "swe_plan_set_nphi_form", "swe_plan_set_legendre_mode", "swe_plan_tuning",
 ]
 SWE_NPHI_FLUX, SWE_NPHI_ADVECTIVE = 0, 1
+SWE_LEGENDRE_AUTO, SWE_LEGENDRE_PERSISTENT, SWE_LEGENDRE_PER_TILE = 0, 1, 2
 SWE_STAB_COARSE_ALONE, SWE_STAB_PARAREAL, SWE_STAB_MGRIT2, SWE_STAB_MGRIT2_PRINTED = range(4)
 SWE_METHOD_PARAREAL, SWE_METHOD_MGRIT2 = 0, 1
 
@@ -139,6 +140,8 @@ def load(path: Optional[str] = None) -> ct.CDLL:
         "swe_stability_region": ([ct.POINTER(StabilityDesc), d, d, i, d, d, i, vp, vp], i),
         "swe_request_bytes": ([ct.POINTER(RequestDesc), ct.POINTER(ct.c_size_t)], i),
         "swe_plan_set_nphi_form": ([vp, i], i),
+        "swe_plan_set_legendre_mode": ([vp, i], i),
+        "swe_plan_tuning": ([vp, ct.c_char_p, ct.c_size_t], i),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -205,6 +208,16 @@ class Plan:
     def set_nphi_form(self, form):
         """SWE_NPHI_FLUX (default) or SWE_NPHI_ADVECTIVE geopotential tendency (see the C header)."""
         _check(load().swe_plan_set_nphi_form(self.h, form))
+
+    def set_legendre_mode(self, mode):
+        """SWE_LEGENDRE_AUTO (default), _PERSISTENT or _PER_TILE tensor-core Legendre kernels."""
+        _check(load().swe_plan_set_legendre_mode(self.h, mode))
+
+    def tuning(self) -> str:
+        """Launch configurations chosen so far (ring kernel, Legendre variants with their times)."""
+        buf = ct.create_string_buffer(4096)
+        _check(load().swe_plan_tuning(self.h, buf, len(buf)))
+        return buf.value.decode()
 
     def check(self, stream=None):
         """Synchronise the stream and return the plan's status (SWE_OK, SWE_ETIMEOUT or
