@@ -74,7 +74,7 @@ METRIC = "SWE slice-steps/s at T255"
 # DRAM bytes / algorithmic bytes of a kernel, from one ncu capture of that kernel (dram__bytes
 # read + write over the algorithmic bytes of the same launch); valid only while the kernel is
 # unchanged since that capture
-NCU_TRAFFIC_RATIO = {"ring_nl_f32": (0.804, "ncu capture of k_ring_nl_lg<32, 256>, T255, 32 states, scaled per ring")}
+NCU_TRAFFIC_RATIO = {"ring_nl_f32": (0.806, "ncu capture of k_ring_nl_lg<32, 256>, T255, 32 states, scaled per ring")}
 FP64_PEAK_TFLOPS = 1.25           # nominal dense FP64 rate of GB300
 R_NORM = 32                       # spectral resolution of the error norm (Eq. 21), as in the paper's figures
 
@@ -378,12 +378,14 @@ SERVE_COARSE = {63: 31, 127: 63, 255: 127, 341: 170}
 SERVE_ITERS = {"parareal": 4, "mgrit": 3}
 
 
-def serve_measure(prec_name, local, n_req=16, loads=(0.8,), seed=1000):
+def serve_measure(prec_name, local, n_req=16, loads=(0.8,), seed=1000, sat_requests=0, rate=0.0):
     """Continuous-batching server under Poisson arrivals.  A saturated pass (every request
     queued at t = 0) measures the throughput; the same requests then arrive as a Poisson
     process at each load times that rate.  Latency = arrival to result available.  Every
     truncation has its own fine and coarse plan objects, so the server runs the truncations
-    in separate lanes (streams) that overlap on the device."""
+    in separate lanes (streams) that overlap on the device.  sat_requests > 0 measures the
+    saturated rate on the first sat_requests requests of the mix only; rate > 0 takes that rate
+    as given (from an earlier saturated pass of the same mix) and skips the pass."""
     import math
 
     import numpy as np
@@ -463,9 +465,19 @@ def serve_measure(prec_name, local, n_req=16, loads=(0.8,), seed=1000):
         server.close()
         return lat, wall
 
-    lat0, wall0 = run([0.0] * len(subs))                    # saturated
-    rate = len(subs) / wall0
     work = sum(w for _, w in subs)
+    sat = {}
+    if rate <= 0.0:
+        ns = sat_requests if 0 < sat_requests < len(subs) else len(subs)
+        full = subs
+        subs = full[:ns]
+        lat0, wall0 = run([0.0] * ns)                       # saturated
+        subs = full
+        rate = ns / wall0
+        sat = {"saturated_requests": ns, "saturated_wall_s": wall0,
+               "saturated_fine_slice_steps_per_s": sum(w for _, w in full[:ns]) / wall0}
+    else:
+        sat = {"saturated_rate_given": rate}
     levels = []
     l0 = swe.launch_count()
     clocks = ClockSampler(local)
@@ -489,7 +501,7 @@ def serve_measure(prec_name, local, n_req=16, loads=(0.8,), seed=1000):
             "mix": "T63/T127/T255/T341 (coarse at M/2, plans per truncation), S in {16,32,64,128}, 1-5 days; "
                    "Parareal (K=4, 12-step-equivalent coarse IMEX) or two-level MGRIT (cf 4, SL coarse, 3 cycles), "
                    "about 50/50",
-            "saturated_req_per_s": rate, "saturated_fine_slice_steps_per_s": work / wall0,
+            "saturated_req_per_s": rate, **sat,
             "p50_latency_s": main["p50_latency_s"], "p99_latency_s": main["p99_latency_s"],
             "throughput_req_per_s": main["throughput_req_per_s"], "load_levels": levels,
             "precision": prec_name, "gpu_launches": launches, "clocks": clk}
@@ -827,8 +839,11 @@ def run_serve(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     loads = tuple(float(x) for x in args.serve_loads.split(","))
-    mixed = serve_measure("mixed", local, n_req=args.serve_requests, loads=loads)
-    line = {"metric": "serving p99 latency (Poisson arrivals at 0.8 x saturated rate)", "value": mixed["p99_latency_s"],
+    mixed = serve_measure("mixed", local, n_req=args.serve_requests, loads=loads, sat_requests=args.serve_sat_requests,
+                          rate=args.serve_rate)
+    main_load = min(loads, key=lambda x: abs(x - 0.8))
+    line = {"metric": "serving p99 latency (Poisson arrivals at %g x saturated rate)" % main_load,
+            "value": mixed["p99_latency_s"],
             "unit": "s", "n_gpus": world, "steps": mixed["requests"], "warmup": 0,
             "ms_per_step": 1000.0 / mixed["throughput_req_per_s"], "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "mixed", "data": "synthetic",
@@ -1208,6 +1223,10 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true", help="skip the error pass against the serial fine solution")
     ap.add_argument("--serve-requests", type=int, default=24, help="requests per load level in the serving sample")
     ap.add_argument("--serve-loads", default="0.8", help="offered loads (fractions of the saturated rate)")
+    ap.add_argument("--serve-sat-requests", type=int, default=0,
+                    help="requests of the saturated pass (0: all of the sample)")
+    ap.add_argument("--serve-rate", type=float, default=0.0,
+                    help="saturated rate in requests/s from an earlier pass of the same mix (skips the pass)")
     ap.add_argument("--no-extras", action="store_true", help="skip the SHT and serving measurements")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain comparison run")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

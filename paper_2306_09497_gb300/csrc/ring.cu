@@ -444,15 +444,22 @@ template <int SW> __device__ __forceinline__ int bidx(int i) {
     }
 }
 
-// Barrier of the T lanes that own one ring: a warp barrier for T <= 32; for T = 64 (two warps
-// per ring, two rings per 128-thread block) the named barrier 1 + ring index over 64 threads.
+// Barrier of the T lanes that own one ring (lane group): a warp barrier for T <= 32; for T = 64
+// (two warps per group, groups of 64 consecutive threads, at most 7 per block) the named
+// barrier 1 + group index over 64 threads (the index is warp-uniform; the ids are immediates).
 template <int T> __device__ __forceinline__ void ring_sync() {
     if constexpr (T <= 32) {
         __syncwarp();
-    } else if (threadIdx.x < 64) {               // warp-uniform: ring 0 is warps 0-1
-        asm volatile("bar.sync 1, 64;" ::: "memory");
     } else {
-        asm volatile("bar.sync 2, 64;" ::: "memory");
+        switch (threadIdx.x >> 6) {
+            case 0: asm volatile("bar.sync 1, 64;" ::: "memory"); break;
+            case 1: asm volatile("bar.sync 2, 64;" ::: "memory"); break;
+            case 2: asm volatile("bar.sync 3, 64;" ::: "memory"); break;
+            case 3: asm volatile("bar.sync 4, 64;" ::: "memory"); break;
+            case 4: asm volatile("bar.sync 5, 64;" ::: "memory"); break;
+            case 5: asm volatile("bar.sync 6, 64;" ::: "memory"); break;
+            default: asm volatile("bar.sync 7, 64;" ::: "memory"); break;
+        }
     }
 }
 
@@ -574,6 +581,21 @@ template <int T> __device__ __forceinline__ void grid_to_forward_order(float2 (&
         for (int r = 0; r < R; ++r) a[b * R + r] = w[b + (EL / R) * r];
 }
 
+// Twiddle e^{-2 pi i k / (2H)} of mode k = t + T c, H = 12 T: e^{-i pi t / H} (the lane's own
+// entry of the table) times e^{-i pi c / 12} (cos and sin of multiples of 15 degrees, exact
+// values of the unit circle rounded to FP32): one shared-memory load per transform instead
+// of one per mode.
+__device__ __forceinline__ float2 tw_mode(float2 wt, int c) {
+    // cos(15 c degrees), c = 0..11; sin(15 c degrees) = cos(15 |6 - c| degrees)
+    constexpr float C15[12] = {1.0f, 0.96592582628906829f, 0.86602540378443865f, 0.70710678118654752f, 0.5f,
+                               0.25881904510252076f, 0.0f, -0.25881904510252076f, -0.5f, -0.70710678118654752f,
+                               -0.86602540378443865f, -0.96592582628906829f};
+    if (c == 0) return wt;
+    if (c == 6) return f2(wt.y, -wt.x);                  // times -i
+    const float cr = C15[c], si = -C15[c < 6 ? 6 - c : c - 6];   // e^{-i pi c / 12} = cos - i sin
+    return f2(wt.x * cr - wt.y * si, wt.x * si + wt.y * cr);
+}
+
 // MP: M + 1 fixed at compile time (0: the runtime M).  With MP a multiple of T, whether mode
 // k = t + T c exists is decided per c at compile time, for every lane at once.
 template <int T, int MP>
@@ -603,6 +625,7 @@ __device__ __forceinline__ void ring_inverse_regs(const float2* X, int M, const 
     using L = RingTw<T>;
     // c2r-prepared spectrum Z_k in the first pass's order: register b 4 + r holds
     // x[t + T b + r H/4], i.e. k = t + T (b + 3 r)
+    const float2 wt = twN[t];
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
@@ -612,7 +635,8 @@ __device__ __forceinline__ void ring_inverse_regs(const float2* X, int M, const 
             float2 xa = mode_in<T, MP>(k, c, M) ? X[k] : f2(0.f, 0.f);
             if (c == 0 && t == 0) xa.y = 0.f;               // the m = 0 mode is real
             const float2 xb = partner_in<T, MP>(k, c, M) ? X[H - k] : f2(0.f, 0.f);
-            const float2 e = f2(twN[k].x, -twN[k].y);      // e^{+i theta_k}, theta_k = 2 pi k / (2H)
+            const float2 wk = tw_mode(wt, c);
+            const float2 e = f2(wk.x, -wk.y);               // e^{+i theta_k}, theta_k = 2 pi k / (2H)
             const float2 s1 = cadd(xa, cconj(xb)), d1 = csub(xa, cconj(xb));
             a[b * 4 + r] = cadd(s1, cmul_si<1>(cmul(e, d1)));
         }
@@ -684,6 +708,7 @@ __device__ __forceinline__ void ring_forward_regs(float2 (&a)[EL], int M, const 
         spass<T, 12, 8, -1, true, false>(a, buf, tws + L::f2, t);
     }
     const int partner = (T - t) & (T - 1);
+    const float2 wt = twN[t];
     if constexpr (T > 32) {
         // the partner lane is in the other warp of the ring: exchange through the ring buffer
         // (after the last pass's loads from it)
@@ -710,7 +735,7 @@ __device__ __forceinline__ void ring_forward_regs(float2 (&a)[EL], int M, const 
         if (mode_in<T, MP>(k, r, M)) {
             const float2 zk = a[r], zn = cconj(zp);
             const float2 s1 = cadd(zk, zn), d1 = csub(zk, zn);
-            const float2 tt = cmul_si<-1>(cmul(twN[k], d1));
+            const float2 tt = cmul_si<-1>(cmul(tw_mode(wt, r), d1));
             X[k] = f2(0.5f * (s1.x + tt.x) * scale, 0.5f * (s1.y + tt.y) * scale);
         }
     }
@@ -820,6 +845,74 @@ __global__ void __launch_bounds__(128, 3) k_ring_nl_lg(const float2* __restrict_
             if (s0 + gg < S)
                 Fout[((int64_t)m * nlat + j) * C5 + (int64_t)f * S + s0 + gg] = reg[gg * RS + slot * Mp + m];
         }
+    }
+}
+
+// Latency form of the fused nonlinear ring kernel for few slices (the serial coarse chains run
+// one state): one ring (slice, latitude) per block and five lane groups of T lanes, T in
+// {32, 64}.  Groups 0-3 take the four inverse transforms (Phi', xi, U, V) at once and leave
+// the grid pairs in shared memory; after one block barrier group f forms product f (xi U,
+// xi V, Phi' U, Phi' V, KE, each over cos^2) from them and runs its forward transform.  The
+// dependent chain is one inverse and one forward transform instead of nine.
+constexpr int NLW_GROUPS = 5;
+
+template <int T, int MP>
+__global__ void __launch_bounds__(NLW_GROUPS * T) k_ring_nl_w(const float2* __restrict__ Fin, float2* __restrict__ Fout,
+                                                             int M, int nlat, int S, const float2* __restrict__ twg,
+                                                             const double* __restrict__ mu,
+                                                             const double* __restrict__ w) {
+    constexpr int H = EL * T, HB = H + H / 16 + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* twN = reinterpret_cast<float2*>(smem_raw);     // 2H entries e^{-2 pi i k / (2H)}
+    float2* tws = twN + 2 * H;                              // pass tables
+    float2* fbuf = tws + RingTw<T>::n;                      // [5][HB] exchange buffers
+    float2* gp = fbuf + NLW_GROUPS * HB;                    // [4][H] grid pairs: Phi', xi, U, V
+    float2* spin = gp + 4 * H;                              // [4][M+1] input modes
+    if constexpr (MP > 0) M = MP - 1;
+    const int Mp = M + 1;
+    float2* spout = spin + 4 * Mp;                          // [5][M+1] output modes
+    const int s = blockIdx.x, j = blockIdx.y;
+    const int64_t C4 = 4 * (int64_t)S, C5 = 5 * (int64_t)S;
+    for (int q = threadIdx.x; q < 4 * Mp; q += blockDim.x) {
+        const int f = q / Mp, m = q - f * Mp;
+        cp_async8(&spin[q], &Fin[((int64_t)m * nlat + j) * C4 + (int64_t)f * S + s], true);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (int k = threadIdx.x; k < 2 * H; k += blockDim.x) twN[k] = twg[k];
+    fill_ring_tw<T>(tws, twg);
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    const int t = threadIdx.x & (T - 1), g = threadIdx.x / T;
+    float2* buf = fbuf + g * HB;
+    float2 a[EL];
+    if (g < 4) {
+        // input slots: 0 Phi', 1 xi, 2 U, 3 V (grid pair n = t + T q in register q)
+        ring_inverse_regs<T, MP>(spin + g * Mp, M, twN, tws, buf, t, a);
+#pragma unroll
+        for (int q = 0; q < EL; ++q) gp[g * H + t + T * q] = a[q];
+    }
+    __syncthreads();
+    const double muj = mu[j];
+    const float ic2 = (float)(1.0 / ((1.0 - muj) * (1.0 + muj)));
+    const float scale = (float)(w[j] / (double)(2 * H));
+    // product g: 0 xi U, 1 xi V, 2 Phi' U, 3 Phi' V, 4 KE = (U^2 + V^2) / 2, each / cos^2
+#pragma unroll
+    for (int q = 0; q < EL; ++q) {
+        const int n = t + T * q;
+        const float2 u = gp[2 * H + n], v = gp[3 * H + n];
+        if (g == 4) {
+            a[q] = f2(0.5f * (u.x * u.x + v.x * v.x) * ic2, 0.5f * (u.y * u.y + v.y * v.y) * ic2);
+        } else {
+            const float2 p = gp[(g < 2 ? 1 : 0) * H + n];
+            const float2 o = (g & 1) ? v : u;
+            a[q] = f2(p.x * o.x * ic2, p.y * o.y * ic2);
+        }
+    }
+    ring_forward_regs<T, MP>(a, M, twN, tws, buf, t, scale, spout + g * Mp);
+    __syncthreads();
+    for (int q = threadIdx.x; q < 5 * Mp; q += blockDim.x) {
+        const int f = q / Mp, m = q - f * Mp;
+        Fout[((int64_t)m * nlat + j) * C5 + (int64_t)f * S + s] = spout[q];
     }
 }
 
@@ -1146,8 +1239,30 @@ static swe_status ring_lg_launch_mp(const swe_plan* p, const void* Fin, void* Fo
     return SWE_OK;
 }
 
+template <int T, int MP>
+static swe_status ring_w_launch_mp(const swe_plan* p, const void* Fin, void* Fout, int S, cudaStream_t st) {
+    constexpr int H = EL * T, HB = H + H / 16 + 1;
+    const size_t sm = (2 * (size_t)H + RingTw<T>::n + (size_t)NLW_GROUPS * HB + 4 * (size_t)H +
+                       9 * (size_t)(p->M + 1)) * sizeof(float2);
+    SWE_CHECK_CUDA(cudaFuncSetAttribute(k_ring_nl_w<T, MP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    dim3 g(S, p->nlat);
+    k_ring_nl_w<T, MP><<<g, NLW_GROUPS * T, sm, st>>>((const float2*)Fin, (float2*)Fout, p->M, p->nlat, S, p->twf,
+                                                       p->mu, p->w);
+    SWE_CHECK_LAUNCH("k_ring_nl_w");
+    return SWE_OK;
+}
+
+// batches of at most this many slices take the one-ring-per-block latency form (T >= 32)
+constexpr int RING_W_MAX_S = 4;
+
 template <int T>
 static swe_status ring_lg_launch(const swe_plan* p, const void* Fin, void* Fout, int S, cudaStream_t st) {
+    if constexpr (T >= 32) {
+        if (S <= RING_W_MAX_S) {
+            if (p->M + 1 == 8 * T) return ring_w_launch_mp<T, 8 * T>(p, Fin, Fout, S, st);
+            return ring_w_launch_mp<T, 0>(p, Fin, Fout, S, st);
+        }
+    }
     if (p->M + 1 == 8 * T) return ring_lg_launch_mp<T, 8 * T>(p, Fin, Fout, S, st);
     return ring_lg_launch_mp<T, 0>(p, Fin, Fout, S, st);
 }

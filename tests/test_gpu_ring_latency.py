@@ -1,0 +1,66 @@
+"""Latency form of the fused nonlinear ring kernel (one ring per block, five lane groups; taken
+for batches of at most 4 slices on the nlon = 768 and 1536 grids, i.e. the serial coarse chains
+of the T255 / T511 workloads) against the oracle's nonlinear terms (Eq. 1) and against the
+many-slice lane-group kernel on the same states.
+
+Bounds: those of the split nonlinear evaluation (Phi' 5e-5, xi 1e-5, delta 4e-6 M; FP32 grid
+values through products, then a divergence or curl one to two orders below the fluxes it
+differences), both against the oracle and against the lane-group kernel: the two kernels
+round the same FP32 sums differently (other fused multiply-adds), and on this GPU their
+Phi' tendencies differ by 4e-6 (T255) and 6.5e-6 (T511), the cancellation in the divergence
+amplifying the FP32 rounding of the products.
+"""
+import numpy as np
+import pytest
+
+from oracle.sphere import Sphere
+from oracle.swe import SWE, to_dense, to_packed
+from paper_2306_09497_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.float64).copy()).cuda()
+
+
+def _err(a, b, w):
+    return np.sqrt(np.sum(w * np.abs(a - b) ** 2) / np.sum(w * np.abs(b) ** 2))
+
+
+@pytest.mark.parametrize("M,nlat,nlon", [(255, 384, 768), (511, 768, 1536)], ids=["T255", "T511"])
+def test_latency_ring_kernel(M, nlat, nlon):
+    from paper_2306_09497_gb300 import swe
+    plan = swe.Plan(M, nlat, nlon, prec=swe.SWE_SPLIT_BF16X3)
+    s = Sphere(M, nlat, nlon)
+    sw = SWE(s)
+    S = 8
+    U0 = []
+    for b in range(S):
+        xi, noise = inputs.initial_fields(M, 70 + b)
+        xd = s.unpack(xi)
+        de = 0.1 * s.unpack(inputs.initial_fields(M, 90 + b)[0])
+        U0.append(to_packed(s, (sw.balanced_geopotential(xd) + s.unpack(noise), xd, de)))
+    U0 = np.stack(U0)
+    m, _ = inputs.mn_arrays(M)
+    w = np.where(m == 0, 1.0, 2.0)
+    wide = {}
+    for n in (1, 3, S):                    # 1 and 3: latency form; 8: lane-group kernel
+        out = torch.empty((n, 3, plan.nc * 2), dtype=torch.float64, device="cuda")
+        plan.nonlinear(_dev(U0[:n]), out, n)
+        assert plan.check() == swe.SWE_OK
+        wide[n] = out.cpu().numpy().view(np.complex128).reshape(n, 3, -1)
+    plan.close()
+    # 3 slices (12 complex columns) take the same tcgen05 Legendre kernels as 8: only the ring
+    # kernel differs.  1 slice (4 columns) also takes the narrow FP32 SIMT contraction.
+    bound = (5e-5, 1e-5, 4e-6 * M)
+    for b in range(3):
+        for f in range(3):
+            e = _err(wide[3][b, f], wide[S][b, f], w)
+            assert e < bound[f], (b, f, e)
+    ref = to_packed(s, sw.nonlinear(to_dense(s, U0[0])))
+    for n in (1, 3):
+        for f in range(3):
+            e = _err(wide[n][0, f], ref[f], w)
+            assert e < bound[f], (n, f, e)
