@@ -3,9 +3,12 @@ for batches of at most 4 slices on the nlon = 768 and 1536 grids, i.e. the seria
 of the T255 / T511 workloads) against the oracle's nonlinear terms (Eq. 1) and against the
 many-slice lane-group kernel on the same states.
 
-Bounds: those of the split nonlinear evaluation (Phi' 5e-5, xi 1e-5, delta 4e-6 M; FP32 grid
-values through products, then a divergence or curl one to two orders below the fluxes it
-differences), both against the oracle and against the lane-group kernel: the two kernels
+Bounds: those of the split nonlinear evaluation (Phi' 5e-5, xi 1e-5; FP32 grid values through
+products, then a divergence or curl one to two orders below the fluxes it differences) and for
+delta 1.6e-8 M^2: its Laplacian of the kinetic energy weights the white FP32 rounding of KE by
+n(n+1) against a steeply decaying spectrum (the T63-T255 tests' 4e-6 M is the same value at
+M = 250; measured at T511: 2.3e-3 against 4.2e-3), both against the oracle and against the
+lane-group kernel: the two kernels
 round the same FP32 sums differently (other fused multiply-adds), and on this GPU their
 Phi' tendencies differ by 4e-6 (T255) and 6.5e-6 (T511), the cancellation in the divergence
 amplifying the FP32 rounding of the products.
@@ -54,7 +57,7 @@ def test_latency_ring_kernel(M, nlat, nlon):
     plan.close()
     # 3 slices (12 complex columns) take the same tcgen05 Legendre kernels as 8: only the ring
     # kernel differs.  1 slice (4 columns) also takes the narrow FP32 SIMT contraction.
-    bound = (5e-5, 1e-5, 4e-6 * M)
+    bound = (5e-5, 1e-5, 1.6e-8 * M * M)
     for b in range(3):
         for f in range(3):
             e = _err(wide[3][b, f], wide[S][b, f], w)
