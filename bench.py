@@ -1008,7 +1008,7 @@ def run_bumps(args):
     return 0
 
 
-# Parareal configurations of the other BASELINE workloads: (truncation, grid, slices, horizon,
+# Parareal workloads at T127 and T511: (truncation, grid, slices, horizon,
 # fine steps per slice, coarse plan, coarse steps per slice, coarse hyperviscosity candidates;
 # the first is the configured one, the next is taken if the iteration goes non-finite)
 PARA_CONFIGS = {
@@ -1017,12 +1017,12 @@ PARA_CONFIGS = {
     # (1e15, 1e16, 1e17 m^4/s) while the iteration goes non-finite: at 900 s the explicit Heun
     # advection of the coarse step has |lambda dt| ~ 1.4 at n = 127 for 80 m/s winds, a growth
     # of ~1.4 per step that only the larger coefficients damp
-    "config2": dict(workload="t127_parareal_s64", M=127, grid=(192, 384), S=64, days=2, nf=45, Mc=127,
+    "t127_parareal_s64": dict(workload="t127_parareal_s64", M=127, grid=(192, 384), S=64, days=2, nf=45, Mc=127,
                     cgrid=(192, 384), nc=3, q=4, nus=(1.0e14, 1.0e15, 1.0e16, 1.0e17), bump=False, iters=4,
                     fp64_iters=4, fp64_serial=True, seed=2),
     # T511, 256 slices over 3 days, fine ~29.78 s (34 per slice), coarse on T255 with 12 steps
     # per slice and hyperviscosity scaled from the T255 workload's coarse level, plus a 120 m bump
-    "config4": dict(workload="t511_parareal_s256", M=511, grid=(768, 1536), S=256, days=3, nf=34, Mc=255,
+    "t511_parareal_s256": dict(workload="t511_parareal_s256", M=511, grid=(768, 1536), S=256, days=3, nf=34, Mc=255,
                     cgrid=(384, 768), nc=12, q=4, nus=(1.0e16 * (127.0 / 255.0) ** 4,), bump=True, iters=4,
                     fp64_iters=1, fp64_serial=False, seed=4),
 }
@@ -1143,7 +1143,7 @@ def _para_run(cfg, prec_name, nu, U0, local):
 
 
 def run_parareal_config(args):
-    """--workload config2 | config4: Parareal at the configuration's size, split precision and
+    """--workload t127_parareal_s64 | t511_parareal_s256: Parareal at the configuration's size, split precision and
     FP64 plain on the same GPU; slice-steps/s, E_{Phi,32} and the area-weighted L2 error of the
     last slice boundary against each precision's serial fine solution after every iteration, and
     the per-field error of the split-precision iterates against the FP64 ones.  At T511 the FP64
@@ -1215,8 +1215,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["fp64", "mixed"])
-    ap.add_argument("--workload", default="mgrit", choices=["mgrit", "parareal", "serve", "ncu-case", "bumps", "config2",
-                                                              "config4"])
+    ap.add_argument("--workload", default="mgrit", choices=["mgrit", "parareal", "serve", "ncu-case", "bumps",
+                                                              "t127_parareal_s64", "t511_parareal_s256"])
     ap.add_argument("--bumps-iters", type=int, default=10, help="MGRIT iterations per bumps configuration")
     ap.add_argument("--S", type=int, default=32, help="states of the ncu case")
     ap.add_argument("--case-steps", type=int, default=1, help="IMEX steps of the ncu case")
