@@ -1175,6 +1175,9 @@ struct SplitTables {
         float ms_persist, ms_tile;
     };
     std::vector<Tune> tune[2];                // [0] inverse, [1] forward
+    // batches of at most 8 complex columns: 1 the FP32 SIMT kernel, 2 the tensor-core path
+    // (ms_persist: SIMT time, ms_tile: tensor-core time)
+    std::vector<Tune> narrow[2];
     unsigned char* inv = nullptr;
     unsigned char* fwd = nullptr;
     long long* inv_off = nullptr;
@@ -1554,6 +1557,49 @@ swe_status wait_selftest_launch(const swe_plan* p, long long polls, cudaStream_t
     return SWE_OK;
 }
 
+// Batches of at most 8 complex columns (the serial chains) can take the FP32 SIMT contraction
+// or the tensor-core path: which is faster depends on the truncation (the SIMT kernel wins at
+// T255, the tensor cores at T511).  The first call per direction and column count outside
+// stream capture runs both twice on its own operands, times the second run of each and keeps
+// the faster; a call under capture before that takes the SIMT kernel.
+swe_status leg_narrow_choice(const swe_plan* p, int dir, int C, const void* in, void* out, cudaStream_t st,
+                             int* choice) {
+    *choice = 1;
+    SplitTables* t = (SplitTables*)p->Pbf;
+    if (!t) return SWE_OK;
+    for (const auto& e : t->narrow[dir])
+        if (e.ncol == 2 * C) {
+            *choice = e.choice;
+            return SWE_OK;
+        }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    SWE_CHECK_CUDA(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return SWE_OK;
+    cudaEvent_t e0, e1;
+    SWE_CHECK_CUDA(cudaEventCreate(&e0));
+    SWE_CHECK_CUDA(cudaEventCreate(&e1));
+    float ms[2] = {0.f, 0.f};
+    swe_status r = SWE_OK;
+    for (int v = 0; v < 2 && r == SWE_OK; ++v)
+        for (int rep = 0; rep < 2 && r == SWE_OK; ++rep) {
+            cudaEventRecord(e0, st);
+            if (dir == 0)
+                r = v == 0 ? leg_inverse_small(p, (const float*)in, (float*)out, C, st)
+                           : leg_inverse_split(p, (const float2*)in, (float2*)out, C, st);
+            else
+                r = v == 0 ? leg_forward_small(p, (const float*)in, (float*)out, C, st)
+                           : leg_forward_split(p, (const float2*)in, (float2*)out, C, st);
+            cudaEventRecord(e1, st);
+            if (r == SWE_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms[v], e0, e1);
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    SWE_CHECK(r);
+    *choice = ms[0] <= ms[1] ? 1 : 2;
+    t->narrow[dir].push_back(SplitTables::Tune{2 * C, *choice, ms[0], ms[1]});
+    return SWE_OK;
+}
+
 // ----------------------------------------------------------------------------- C ABI: tuning
 extern "C" swe_status swe_plan_set_legendre_mode(swe_plan_t p, int mode) {
     if (!p || mode < SWE_LEGENDRE_AUTO || mode > SWE_LEGENDRE_PER_TILE) {
@@ -1582,6 +1628,13 @@ extern "C" swe_status swe_plan_tuning(swe_plan_t p, char* buf, size_t len) {
             for (const auto& e : t->tune[dir]) {
                 snprintf(tmp, sizeof tmp, "; %s ncol %d: %s (persistent %.3f ms, per tile %.3f ms)",
                          dir == 0 ? "inverse" : "forward", e.ncol, e.choice == 1 ? "persistent" : "per tile",
+                         e.ms_persist, e.ms_tile);
+                out += tmp;
+            }
+        for (int dir = 0; dir < 2; ++dir)
+            for (const auto& e : t->narrow[dir]) {
+                snprintf(tmp, sizeof tmp, "; %s ncol %d: %s (SIMT %.3f ms, tensor cores %.3f ms)",
+                         dir == 0 ? "inverse" : "forward", e.ncol, e.choice == 1 ? "SIMT" : "tensor cores",
                          e.ms_persist, e.ms_tile);
                 out += tmp;
             }

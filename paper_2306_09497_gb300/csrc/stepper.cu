@@ -7,20 +7,26 @@ static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 swe_status leg_inverse_f64(const swe_plan* p, const double2* X, double2* F, int C, cudaStream_t st);
 swe_status leg_forward_f64(const swe_plan* p, const double2* F, double2* Y, int C, cudaStream_t st);
-swe_status leg_inverse_split(const swe_plan* p, const float2* X, float2* F, int C, cudaStream_t st);
-swe_status leg_forward_split(const swe_plan* p, const float2* F, float2* Y, int C, cudaStream_t st);
 
 // The transform operands X (into the inverse contraction) and Y (out of the forward one) hold
 // complex128 on FP64 plans and complex64 on split-precision plans (the same buffers, half used).
 swe_status leg_inverse(const swe_plan* p, const double2* X, void* F, int C, cudaStream_t st) {
     if (p->prec == SWE_FP64) return leg_inverse_f64(p, X, (double2*)F, C, st);
-    if (leg_small_ok(p, C)) return leg_inverse_small(p, reinterpret_cast<const float*>(X), (float*)F, C, st);
+    if (leg_small_ok(p, C)) {
+        int choice = 1;
+        SWE_CHECK(leg_narrow_choice(p, 0, C, X, F, st, &choice));
+        if (choice == 1) return leg_inverse_small(p, reinterpret_cast<const float*>(X), (float*)F, C, st);
+    }
     return leg_inverse_split(p, reinterpret_cast<const float2*>(X), (float2*)F, C, st);
 }
 
 swe_status leg_forward(const swe_plan* p, const void* F, double2* Y, int C, cudaStream_t st) {
     if (p->prec == SWE_FP64) return leg_forward_f64(p, (const double2*)F, Y, C, st);
-    if (leg_small_ok(p, C)) return leg_forward_small(p, (const float*)F, reinterpret_cast<float*>(Y), C, st);
+    if (leg_small_ok(p, C)) {
+        int choice = 1;
+        SWE_CHECK(leg_narrow_choice(p, 1, C, F, Y, st, &choice));
+        if (choice == 1) return leg_forward_small(p, (const float*)F, reinterpret_cast<float*>(Y), C, st);
+    }
     return leg_forward_split(p, (const float2*)F, reinterpret_cast<float2*>(Y), C, st);
 }
 

@@ -172,6 +172,12 @@ swe_status plan_flags_status(int bits, const char* where, int iter);
 swe_status small_tables_build(swe_plan* p);
 void small_tables_free(swe_plan* p);
 bool leg_small_ok(const swe_plan* p, int C);
+// narrow batches: 1 FP32 SIMT kernel, 2 tensor-core path (measured on the first call per
+// direction (0 inverse, 1 forward) and column count outside stream capture)
+swe_status leg_narrow_choice(const swe_plan* p, int dir, int C, const void* in, void* out, cudaStream_t st,
+                             int* choice);
+swe_status leg_inverse_split(const swe_plan* p, const float2* X, float2* F, int C, cudaStream_t st);
+swe_status leg_forward_split(const swe_plan* p, const float2* F, float2* Y, int C, cudaStream_t st);
 swe_status leg_inverse_small(const swe_plan* p, const float* X, float* F, int C, cudaStream_t st);
 swe_status leg_forward_small(const swe_plan* p, const float* F, float* Y, int C, cudaStream_t st);
 
