@@ -132,9 +132,10 @@ swe_status swe_plan_set_nphi_form(swe_plan_t plan, int form);
 typedef enum { SWE_LEGENDRE_AUTO = 0, SWE_LEGENDRE_PERSISTENT = 1, SWE_LEGENDRE_PER_TILE = 2 } swe_legendre_mode;
 swe_status swe_plan_set_legendre_mode(swe_plan_t plan, int mode);
 
-/* Launch configurations the plan has chosen so far (fused ring kernel, Legendre variant per
- * direction and column count with the measured times), as a NUL-terminated text in the HOST
- * buffer buf of len bytes (truncated to fit).  SWE_EINVAL for a null plan or buffer. */
+/* Launch configurations the plan has chosen so far (fused ring kernel; per direction and
+ * column count the tensor-core Legendre variant, and for batches of at most 8 complex columns
+ * the SIMT or tensor-core contraction, each with the measured times), as a NUL-terminated text
+ * in the HOST buffer buf of len bytes (truncated to fit).  SWE_EINVAL for a null plan or buffer. */
 swe_status swe_plan_tuning(swe_plan_t plan, char* buf, size_t len);
 
 /* Copies the Gauss-Legendre nodes mu_j (north to south) and weights w_j into
