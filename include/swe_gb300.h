@@ -315,11 +315,13 @@ swe_status swe_pint_load(swe_pint_t p, const double* U, const double* Gold, void
 swe_status swe_pint_save(swe_pint_t p, double* U, double* Gold, void* stream);
 
 /* Inverse scalar transform for callers that cannot allocate device memory at
- * call time -- for example code that runs while a stream is being captured
- * into a CUDA graph (cudaMalloc cannot be captured), real-time loops that
- * forbid allocator calls, or applications whose device memory belongs to
- * their own pool.  Same arguments, layouts and result as sht_inverse (the
- * paper has no counterpart: this is a library-usage variant).
+ * call time -- for example real-time loops that forbid allocator calls (an
+ * allocation can block and synchronise the device), or applications whose
+ * device memory belongs entirely to their own pool allocator, so that a
+ * library allocation would fail or break their accounting.  Same arguments,
+ * layouts and result as sht_inverse (the paper has no counterpart: this is a
+ * library-usage variant).  Like sht_inverse, the first call at a new batch
+ * width may time the plan's kernel variants once, synchronising `stream`.
  * Scratch comes from a fixed static device array of SWE_NOALLOC_SCRATCH_BYTES
  * (64 MiB) that every GPU which loads the library holds until the process
  * exits; nothing is allocated or freed by the call.  The scratch needed is

@@ -2,10 +2,10 @@
 //
 // sht_inverse() takes its scratch (the transform operands and the Fourier
 // coefficients) from the plan's workspace arena, which grows with cudaMalloc on
-// demand.  Some callers cannot allocate device memory at call time: code running
-// while a stream is being captured into a CUDA graph (cudaMalloc is not
-// capturable), real-time loops that forbid allocator calls, and applications
-// whose device memory is fully owned by their own pool allocator.  For them
+// demand.  Some callers cannot allocate device memory at call time: real-time
+// loops that forbid allocator calls (an allocation can block and synchronise the
+// device), and applications whose device memory is fully owned by their own pool
+// allocator, where a library allocation would fail or escape their accounting.  For them
 // sht_inverse_noalloc() uses a fixed scratch array that lives in this file as a
 // static __device__ variable: SWE_NOALLOC_SCRATCH_BYTES (64 MiB) on every GPU
 // that loads the library, held until the process exits.

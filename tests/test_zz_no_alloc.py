@@ -1,7 +1,7 @@
 """sht_inverse_noalloc: the inverse transform for callers that cannot allocate device memory.
 
-Such callers (code inside a CUDA-graph stream capture, real-time loops, or
-applications whose device memory belongs to their own pool) get the same
+Such callers (real-time loops that forbid allocator calls, or applications
+whose device memory belongs to their own pool) get the same
 result as sht_inverse while the library draws its scratch from a fixed 64 MiB
 static device array instead of cudaMalloc.  The checks, on FP64 and on
 split-precision plans: two calls in a row agree with sht_inverse within the
