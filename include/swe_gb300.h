@@ -24,7 +24,10 @@
  *   the comment says "host".  The library owns its tables and workspace.
  * Streams: every call is asynchronous on the given stream (NULL = legacy
  *   default stream) unless its comment says it synchronises.  Calls on one
- *   plan must not overlap in time (the plan's workspace is shared).
+ *   plan must not overlap in time (the plan's workspace is shared).  On
+ *   split-precision plans the first call that runs a Legendre contraction at a
+ *   new batch width outside stream capture times the kernel variants once and
+ *   synchronises its stream (swe_plan_set_legendre_mode).
  * Errors: functions return a swe_status; SWE_OK is 0.  swe_last_error()
  *   returns a thread-local message describing the last failure.  No C++
  *   exception crosses this boundary.
