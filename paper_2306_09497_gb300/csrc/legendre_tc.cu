@@ -703,13 +703,13 @@ __global__ void __launch_bounds__(NTH, 1) k_leg_fwd_tc(const float* __restrict__
 // longest come first).  The K chunks of all its items form one continuous pipeline:
 //   converter warps 0-15: as in the per-tile kernels, chunk after chunk across items;
 //   control warp 16, one lane: raw TMA tiles NR chunks ahead and table tiles NB - 2 chunks
-//     ahead across item boundaries; the MMAs of item i go to accumulator set i mod 2 (TMEM
-//     columns 256 (i mod 2) ..), after "acc_empty" of that set shows the epilogue of item
-//     i - 2 done; after the item's last chunk it commits to "acc_full" of the set;
+//     ahead across item boundaries; the MMAs of item i go to accumulator set i mod nsets
+//     (see below), after "acc_empty" of that set shows the epilogue of the item that used it
+//     last done; after the item's last chunk it commits to "acc_full" of the set;
 //   epilogue warps 17-20 (TMEM lane quarter = warp mod 4): wait "acc_full" of item i, read
 //     the accumulators, write the result, fence, arrive on "acc_empty".
-// So the epilogue of one item and the set-up of the next overlap the MMAs of the next, and the
-// CTA's prologue (barriers, TMEM allocation, first copies) is paid once per SM.  Every wait is
+// So (with two sets) the epilogue of one item overlaps the MMAs of the next, and the CTA's
+// prologue (barriers, TMEM allocation, first copies) is paid once per SM.  Every wait is
 // bounded as in the per-tile kernels.
 constexpr int NEPI = 4;                       // epilogue warps
 constexpr int NTHP = NCV + 32 + 32 * NEPI;    // 672 threads
